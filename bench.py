@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 Kino-PAX+ planner (valid expansions/s).
+
+A step is one planning run of the whole hot path on one synthetic problem:
+kpx_reset + kpx_iterate(I) (I = the configuration's iteration count), i.e.
+I passes of Propagate -> winner select -> UpdateTree append -> PruneNodes with
+the active-set compaction.  Every step of a run is the same deterministic
+problem, so each step does identical work.
+
+Default workload: 6D Dubins airplane, forest of 300 seeded columns
+(half-width U[0.01, 0.03]), RK4 h = 0.02, 16^3 x 4 regions, tree cap 2^20,
+lambda = 64, 200 iterations.
+
+Printed (rank 0, one JSON line): value = valid expansions/s over the timed
+device region (inputs resident in HBM, L2 flushed between steps), e2e = the
+same metric through the C ABI with host buffers (kpx_create from host arrays,
+iterate, kpx_best_trajectory to host, destroy), the roofline of the dominant
+kernel (propagate, bound by FP32/ALU issue), the FP64 oracle timed on the
+host cores, and SM clocks sampled during the timed region.
+
+--impl reference times the FP64 oracle (the CPU reference of this project) on
+the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import math
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2602_02846_gb300 import scenes  # noqa: E402
+
+METRIC = "valid expansions/s"
+UNIT = "valid expansions/s"
+
+# Algorithmic FP32 work of one integration step (dynamics + integrator + cost
+# + state/workspace checks; an FMA counts 2, sin/cos 1 each) and of one
+# point-in-box test (6 comparisons).
+OPS_PER_STEP = {scenes.DI6: 22.0, scenes.DUBINS6: 96.0, scenes.QUAD12: 270.0}
+OPS_PER_BOX_TEST = 6.0
+SM_COUNT_FALLBACK = 152
+FP32_LANES_PER_SM = 128
+
+WORKLOADS = {
+    "dubins6_forest300": dict(make=lambda seed: scenes.dubins_scene(seed),
+                              desc="6D Dubins airplane, 300-column forest, RK4 h=0.02, 16^3x4 regions, "
+                                   "cap 2^20, lambda 64"),
+    "di6_boxes20": dict(make=lambda seed: scenes.di_scene(seed),
+                        desc="6D double integrator, 20 boxes, Euler h=0.01, 8^3x2^3 regions, cap 32768, lambda 16"),
+    "quad12_building1000": dict(make=lambda seed: scenes.quad_scene(seed),
+                                desc="12D quadcopter, 1,000-box building, RK4 h=0.005, 16^3x4^3 regions, "
+                                     "cap 2^22, lambda 128"),
+}
+DEFAULT_WORKLOAD = "dubins6_forest300"
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("kpx", "reference"), default="kpx")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--iters", type=int, default=0, help="planner iterations per step (0 = the config's)")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed set-up (one process per GPU; replicas of independent problems)
+# ---------------------------------------------------------------------------
+def dist_setup(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def allreduce(x, op, device):
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized():
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op={"max": dist.ReduceOp.MAX, "sum": dist.ReduceOp.SUM}[op])
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        exe = shutil.which("nvidia-smi")
+        if exe is None:
+            return
+        fd, self.path = tempfile.mkstemp(prefix="kpx_clocks_", suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen([exe, "-i", str(gpu_index), "--query-gpu=" + self.FIELDS,
+                                      "--format=csv,noheader,nounits", "-lms", "200"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the same problem, bounded in time
+# ---------------------------------------------------------------------------
+def oracle_sample(prob, iters, budget_s):
+    import oracle
+    oracle.build()
+    pl = oracle.Planner(prob)
+    t0 = time.perf_counter()
+    done = 0
+    while done < iters:
+        pl.iterate(1)
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    st = pl.state()
+    return dict(valid=int(st["total_valid"]), candidates=int(st["total_candidates"]), iters=done, seconds=dt)
+
+
+def run_reference(args):
+    world, rank, local = dist_setup("gloo")
+    if rank != 0:
+        return 0
+    spec = WORKLOADS[args.workload]
+    prob = spec["make"](args.seed)
+    iters = args.iters or prob.iterations
+    per_step_iters = min(iters, 40)
+    for _ in range(args.warmup):
+        oracle_sample(prob, min(per_step_iters, 5), 1e9)
+    vals, secs = 0, 0.0
+    for _ in range(args.steps):
+        r = oracle_sample(prob, per_step_iters, 1e9)
+        vals += r["valid"]
+        secs += r["seconds"]
+    value = vals / secs if secs > 0 else 0.0
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "iterations_per_step": per_step_iters,
+                   "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "first %d iterations of the workload per step, single-threaded FP64 C oracle"
+                                   % per_step_iters},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_kpx(args):
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2602_02846_gb300 as kpx
+    kpx.load()
+    spec = WORKLOADS[args.workload]
+    prob = spec["make"](args.seed + rank)
+    iters = args.iters or prob.iterations
+    stream = torch.cuda.current_stream(dev)
+    pl = kpx.Planner(prob, device=dev, stream=stream)
+    launches_per_step = 1 + 7 * iters
+
+    # one step to learn the (deterministic) work of a step
+    pl.reset()
+    st = pl.iterate(iters, stats=True)
+    valid_per_step = int(st["total_valid"])
+    steps_per_step = int(st["total_steps"])
+    tests_per_step = int(st["total_box_tests"])
+    cand_per_step = int(st["total_candidates"])
+    iters_done = int(st["iter"])
+    for _ in range(max(0, args.warmup - 1)):
+        pl.reset()
+        pl.iterate(iters)
+    torch.cuda.synchronize(dev)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        pl.reset()
+        pl.iterate(iters)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    st2 = pl.iterate(0, stats=True)
+    assert int(st2["total_valid"]) == valid_per_step, "steps are not identical"
+
+    ms_max = allreduce(ms, "max", dev)
+    valid_all = allreduce(valid_per_step * args.steps, "sum", dev)
+    value = valid_all / (ms_max / 1e3)
+
+    # per-phase device time over one step (same launches, CUDA events on the planner's stream)
+    phase_ms = [0.0] * 7
+    pl.reset()
+    flush.zero_()
+    evs = []
+    for _ in range(iters):
+        for ph in range(7):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            pl.debug_step(ph)
+            b.record(stream)
+            evs.append((ph, a, b))
+    torch.cuda.synchronize(dev)
+    for ph, a, b in evs:
+        phase_ms[ph] += a.elapsed_time(b)
+    prop_ms = phase_ms[1]
+    prop_launch_ms = prop_ms / max(1, iters_done)
+    ops_step = OPS_PER_STEP[prob.dyn] * steps_per_step + OPS_PER_BOX_TEST * tests_per_step
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
+    peak_mhz = 2070.0
+    peak = sms * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12  # TFLOP/s
+    achieved = (ops_step / max(1, iters_done)) / (prop_launch_ms / 1e3) / 1e12 if prop_ms > 0 else 0.0
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ws = pl.workspace
+        pl.close()
+        h2d = int(np.asarray(prob.obstacles).shape[0]) * 32 + 4 * prob.n
+        d2h = 0
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            p2 = kpx.Planner(prob, device=dev, stream=stream, workspace=ws)
+            p2.iterate(iters)
+            tr = p2.best_trajectory()
+            hdr = ctypes.sizeof(kpx.kpx_device_header)
+            d2h = hdr + ((len(tr["steps"]) + 1) * (prob.n + prob.m + 1) * 4 if tr is not None else 0)
+            p2.close()
+        torch.cuda.synchronize(dev)
+        barrier()
+        wall = time.perf_counter() - t0
+        wall_max = allreduce(wall, "max", dev)
+        e2e = {"value": valid_all / wall_max, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    else:
+        pl.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(prob, iters, args.cpu_seconds)
+        cpu = {"value": r["valid"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d of %d iterations of the same problem (%d valid rollouts, %.1f s), "
+                         "single-threaded FP64 C oracle" % (r["iters"], iters, r["valid"], r["seconds"])}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": spec["desc"], "iterations_per_step": iters,
+                       "iterations_run": iters_done, "seed": args.seed, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": "replicas (one independent problem per GPU)" if world > 1 else "single GPU",
+                       "valid_per_step": valid_per_step, "candidates_per_step": cand_per_step,
+                       "integration_steps_per_step": steps_per_step, "box_tests_per_step": tests_per_step,
+                       "tree_nodes": int(st["n_nodes"]), "solution_cost": (None if math.isinf(st["best_cost"])
+                                                                          else float(st["best_cost"]))},
+            "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0, "traffic": None,
+                         "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
+                                       % (sms, FP32_LANES_PER_SM, peak_mhz),
+                         "launch_ms": prop_launch_ms,
+                         "phase_share": {n: round(t / sum(phase_ms), 4) for n, t in zip(kpx.PHASES, phase_ms)}},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps,
+        }
+        print(json.dumps(line))
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_kpx(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,304 @@
+/*
+ * kpx.h -- C ABI of the GB300 (sm_103a) Kino-PAX+ planning library.
+ *
+ * The library runs the per-iteration hot path of Kino-PAX+ (Alg. 1: the
+ * Propagate / PruneNodes / UpdateTree loop) entirely on one GPU:
+ *   - Propagate (Alg. 2): lambda Philox-sampled (control, duration) pairs per
+ *     active node, Euler or RK4 integration in FP32, a validity check after
+ *     every integration step, region map, and a packed 64-bit (cost | id)
+ *     atomic minimum per region;
+ *   - the V_U filter and UpdateTree (Alg. 4): winners are the candidates
+ *     still holding their region's key; they are appended in slot order and
+ *     the best goal-reaching node is tracked;
+ *   - PruneNodes (Alg. 3) over the whole tree, fused with the compaction of
+ *     the next active set (Alg. 5, exclusiveScan + GraphSearch).
+ *
+ * Conventions shared by every entry point:
+ *   - No function throws; every one returns a kpx_status.
+ *   - Host inputs are read during the call and copied; the caller keeps
+ *     ownership of every pointer it passes.
+ *   - Device memory: the library allocates none.  The caller provides one
+ *     device buffer ("workspace") of kpx_workspace_size() bytes, aligned to
+ *     256 bytes, that must stay valid until kpx_destroy().  The opaque
+ *     planner handle itself lives in host memory (malloc).
+ *   - Work is enqueued on the caller's CUDA stream (a cudaStream_t passed as
+ *     void*; NULL = the legacy default stream).  kpx_iterate() does not wait
+ *     for the GPU unless statistics are requested.
+ *   - Errors: invalid arguments return KPX_E_INVALID with a message in
+ *     kpx_last_error(); a CUDA runtime failure returns KPX_E_CUDA with the
+ *     CUDA message.  KPX_TREE_FULL is sticky: once the tree capacity is
+ *     reached every further iteration is a no-op, but the best solution
+ *     stays readable.
+ *   - Thread safety: one planner must not be used from two host threads at
+ *     once; distinct planners are independent.
+ */
+#ifndef KPX_H
+#define KPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    KPX_OK = 0,
+    KPX_E_INVALID = 1,     /* bad argument (message in kpx_last_error) */
+    KPX_E_NOMEM = 2,       /* workspace too small */
+    KPX_E_CUDA = 3,        /* CUDA runtime error */
+    KPX_TREE_FULL = 4,     /* tree capacity t_e reached (sticky; not an error) */
+    KPX_NO_SOLUTION = 5,   /* no goal-reaching node yet */
+    KPX_E_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    KPX_E_INTERNAL = 7     /* a device-side consistency check failed */
+} kpx_status;
+
+/* The three systems of Sec. V (6D double integrator, 6D Dubins airplane,
+ * 12D quadcopter).  State / control layouts:
+ *   KPX_DI6      x = (p_x, p_y, p_z, v_x, v_y, v_z), u = (a_x, a_y, a_z)
+ *   KPX_DUBINS6  x = (x, y, z, yaw, pitch, speed), u = (yaw rate, pitch rate, accel)
+ *   KPX_QUAD12   x = (p, roll, pitch, yaw (ZYX), v, body rates), u = (thrust, tau_x, tau_y, tau_z)
+ */
+typedef enum { KPX_DI6 = 0, KPX_DUBINS6 = 1, KPX_QUAD12 = 2 } kpx_dyn_kind;
+typedef enum { KPX_EULER = 0, KPX_RK4 = 1 } kpx_integrator;
+/* Edge costs satisfying Assumption 1 (additive, monotone). */
+typedef enum {
+    KPX_COST_PATH_LENGTH = 0,     /* sum of |p_k - p_{k-1}| over the checked points */
+    KPX_COST_DURATION = 1,        /* K h */
+    KPX_COST_EFFORT_DURATION = 2  /* K h (1 + w e(u)), e = ((T-mg)/mg)^2 + sum (tau_i/tau_max)^2 */
+} kpx_cost_kind;
+
+/* Dynamics x' = f(x, u) (Sec. III) with the compact control box U and the
+ * state constraints that, with the workspace and obstacles, define X_valid.
+ * A segment has K steps of length h, K uniform in [k_min, k_max]
+ * ("duration dt in (0, T_prop]" of Sec. IV with dt = K h).
+ * Unconstrained state components use x_lo = -inf, x_hi = +inf.
+ * param (quadcopter): mass, g, Jx, Jy, Jz, tau_max. */
+typedef struct {
+    int32_t kind;          /* kpx_dyn_kind */
+    int32_t integ;         /* kpx_integrator */
+    float h;               /* integration step (s), > 0 */
+    int32_t k_min, k_max;  /* 1 <= k_min <= k_max <= 4096 */
+    float u_lo[8], u_hi[8];
+    float x_lo[16], x_hi[16];
+    float param[8];
+} kpx_dynamics;
+
+/* Workspace W (Sec. III): a closed box; the robot's position must stay in it. */
+typedef struct {
+    float lo[3], hi[3];
+} kpx_workspace;
+
+/* Obstacle set O: count closed axis-aligned boxes, aabb = host float[count][6]
+ * (lo x, y, z, hi x, y, z).  Copied at create. */
+typedef struct {
+    const float* aabb;
+    int32_t count;
+} kpx_obstacles;
+
+/* Goal set X_goal: closed ball on the position. */
+typedef struct {
+    float center[3];
+    float radius;
+} kpx_goal;
+
+typedef struct {
+    int32_t kind;          /* kpx_cost_kind */
+    float w_effort;
+} kpx_cost;
+
+/* One axis of the region decomposition R (hyper-cubes of Sec. IV): state
+ * component, bin count and range; wrap != 0 maps an angle into [-pi, pi)
+ * first.  Region ids are mixed radix in axis order. */
+typedef struct {
+    int32_t state_dim;
+    int32_t bins;
+    float lo, hi;
+    int32_t wrap;
+} kpx_region_axis;
+
+enum {
+    /* Reject a candidate whose key cannot win its region before checking
+     * obstacles (the collision-after-cost remark of the appendix).  Results
+     * are identical; only the "valid" statistic then counts fewer rollouts. */
+    KPX_FLAG_EARLY_REJECT = 1
+};
+
+/* Planner hyperparameters (appendix "Hyperparameters"): tree capacity t_e,
+ * branching factor lambda (0 = adaptive lambda = floor(t_e / |V_A|)),
+ * region grid, inactivity threshold I_max (0..254), Philox seed. */
+typedef struct {
+    int32_t tree_cap;
+    int32_t samples_per_node;
+    int32_t n_axes;
+    kpx_region_axis axis[8];
+    int32_t i_max;
+    uint64_t seed;
+    int32_t flags;         /* KPX_FLAG_* */
+} kpx_config;
+
+/* Counters after the last completed iteration. */
+typedef struct {
+    int32_t status;              /* kpx_status held by the planner */
+    int32_t iter;                /* iterations completed */
+    int32_t n_nodes;             /* |T| */
+    int32_t n_active;            /* |V_A| for the next iteration */
+    int32_t n_inactive, n_terminal;
+    int32_t lambda;              /* branching factor of the last iteration */
+    int32_t first_solution_iter; /* -1 until a goal node exists */
+    int64_t candidates, valid, winners;            /* last iteration */
+    int64_t total_candidates, total_valid, total_winners;
+    float best_cost;             /* +inf without a solution */
+    float pad;
+    uint64_t first_solution_ns;  /* device clock: first solution - first iterate launch, 0 if none */
+    uint64_t elapsed_ns;         /* device clock: last iteration end - first iterate launch */
+    uint64_t total_steps;        /* integration steps executed by Propagate */
+    uint64_t total_box_tests;    /* point-in-box tests executed by Propagate */
+} kpx_iter_stats;
+
+typedef struct kpx_planner kpx_planner;
+
+/* Bytes of device workspace kpx_create needs for this problem size
+ * (0 if the arguments are invalid). */
+size_t kpx_workspace_size(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obstacles);
+
+/* Problem statement of Sec. III + Alg. 1 initialisation: root node x_init,
+ * V_A = {root}, every region at infinite cost except the root's region,
+ * which holds the root's key; no solution (unless x_init is already in the
+ * goal).  start = host float[n] with n the state dimension of dyn->kind; it
+ * must lie in X_valid.  device_workspace: caller-owned device memory of at
+ * least kpx_workspace_size() bytes, 256-byte aligned.  cuda_stream: the
+ * stream all work of this planner is enqueued on.  On success *out receives
+ * the planner.  Errors: KPX_E_INVALID (inconsistent or non-finite inputs,
+ * start not valid, sizes out of range), KPX_E_NOMEM (workspace too small),
+ * KPX_E_CUDA. */
+kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                      const float* start, const kpx_goal* goal, const kpx_cost* cost,
+                      const kpx_config* cfg, void* device_workspace, size_t workspace_bytes,
+                      void* cuda_stream, kpx_planner** out);
+
+/* Runs n_iters iterations of Alg. 1's loop body (Propagate, PruneNodes,
+ * UpdateTree) asynchronously on the planner's stream.  If out_last is not
+ * NULL the call waits for the stream and fills it; the return value is then
+ * the planner's status (KPX_OK or KPX_TREE_FULL or a device error).
+ * Without out_last the call returns KPX_OK once the work is enqueued (or a
+ * launch error). */
+kpx_status kpx_iterate(kpx_planner* p, int32_t n_iters, kpx_iter_stats* out_last);
+
+/* The best solution trajectory (Alg. 1 returns it): root-to-goal node
+ * states, the control and step count of each segment.  Host outputs of
+ * capacity segments: states float[capacity+1][n], controls float[capacity][m],
+ * steps int32[capacity].  Waits for the planner's stream.  Returns
+ * KPX_NO_SOLUTION when no goal node exists (*out_len = 0), KPX_E_INVALID with
+ * *out_len = required segments when capacity is too small. */
+kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, float* controls,
+                               int32_t* steps, int32_t* out_len, float* out_cost);
+
+/* Re-initialises the planner to its kpx_create state on the device (same
+ * problem, same workspace), without host copies.  Asynchronous. */
+kpx_status kpx_reset(kpx_planner* p);
+
+/* Waits for the planner's stream and releases the host handle; the device
+ * workspace is the caller's to free afterwards. */
+kpx_status kpx_destroy(kpx_planner* p);
+
+const char* kpx_status_str(kpx_status s);
+/* Message of the last failing call on this planner ("" if none); with
+ * p == NULL the message of the last failing kpx_create in this thread. */
+const char* kpx_last_error(const kpx_planner* p);
+
+/* ------------------------------------------------------------------------
+ * Introspection and step-by-step API (tests, debugging, checkpointing).
+ * ---------------------------------------------------------------------- */
+
+/* Device-resident counters at the head of the workspace. */
+typedef struct {
+    int32_t status, active, iter, n_nodes;
+    int32_t count_A, lambda, va_sel, first_solution_iter;
+    int64_t n_slots;
+    uint64_t goal_key;
+    int32_t n_win, n_kept, count_A_next, epoch;
+    uint64_t prop_ticket;
+    uint32_t win_ticket, prune_ticket;
+    int32_t n_active, n_inactive, n_terminal, pad0;
+    uint64_t last_candidates, last_valid, last_winners;
+    uint64_t total_candidates, total_valid, total_winners;
+    uint64_t t_start_ns, t_first_solution_ns, t_last_ns;
+    int32_t traj_len, pad1;
+    uint64_t total_steps;      /* integration steps executed by Propagate since create/reset */
+    uint64_t total_box_tests;  /* point-in-box tests executed by Propagate since create/reset */
+    uint32_t err_info[4];
+} kpx_device_header;
+
+/* Device addresses of the planner's arrays inside the workspace (SoA):
+ * x: float[n][N] (component d of node i at x[d*N + i]), u: float[m][N],
+ * K: uint16[N], parent: int32[N] (root: -1), key: uint64[N] ((FP32 cost
+ * bits << 32) | id), region: int32[N], set: uint8[N] (bits 0-1: 1 = V_A,
+ * 2 = V_I, 3 = V_T; bit 2: a strict ancestor is dominated), icount: uint8[N],
+ * region_key: uint64[R], region_snap: uint64[R], va[2]: int32[va_cap] each
+ * (the current V_A list is va[header.va_sel]), win_slot: int32[R],
+ * win_mask: uint32[mask_words], obstacles: float[M][8] (lo x, y, z, 0,
+ * hi x, y, z, 0). */
+typedef struct {
+    kpx_device_header* header;
+    float* x;
+    float* u;
+    uint16_t* K;
+    int32_t* parent;
+    uint64_t* key;
+    int32_t* region;
+    uint8_t* set;
+    uint8_t* icount;
+    uint64_t* region_key;
+    uint64_t* region_snap;
+    int32_t* va[2];
+    int32_t* win_slot;
+    uint32_t* win_mask;
+    float* obstacles;
+    int32_t n, m, N, R;
+    int32_t va_cap, n_obstacles;
+    int64_t slot_cap;
+    int64_t mask_words;
+    size_t workspace_bytes;
+} kpx_layout;
+
+kpx_status kpx_get_layout(const kpx_planner* p, kpx_layout* out);
+
+/* Phases of one iteration, in launch order. */
+typedef enum {
+    KPX_PHASE_BEGIN = 0,      /* lambda, |V_A| lambda slots, region snapshot */
+    KPX_PHASE_PROPAGATE = 1,  /* Alg. 2 */
+    KPX_PHASE_MARK = 2,       /* V_U filter: regions holding a candidate key mark its slot */
+    KPX_PHASE_SCAN = 3,       /* winners ranked in slot order */
+    KPX_PHASE_APPEND = 4,     /* UpdateTree: winners written to T (capacity rule) */
+    KPX_PHASE_PRUNE = 5,      /* Alg. 3 + compaction of the next V_A */
+    KPX_PHASE_END = 6         /* counters */
+} kpx_phase;
+
+/* Per-slot record of PROPAGATE for parity checks (device arrays of
+ * capacity slots): valid uint8, region int32, key uint64, K int32,
+ * x_end float[n][capacity], u float[m][capacity]. */
+typedef struct {
+    uint8_t* valid;
+    int32_t* region;
+    uint64_t* key;
+    int32_t* K;
+    float* x;
+    float* u;
+    int64_t capacity;
+} kpx_debug_records;
+
+/* Launches one phase of the current iteration (records: PROPAGATE only,
+ * nullable; with records every slot is checked in full and recorded). */
+kpx_status kpx_debug_step(kpx_planner* p, int32_t phase, const kpx_debug_records* records);
+
+/* Copies the whole workspace (every array and counter) to / from dst/src,
+ * host or device memory of layout.workspace_bytes bytes.  Waits for the
+ * planner's stream.  A restored planner continues bit-identically. */
+kpx_status kpx_snapshot(kpx_planner* p, void* dst);
+kpx_status kpx_restore(kpx_planner* p, const void* src);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KPX_H */

@@ -123,7 +123,7 @@ def _declare(L):
     L.kpo_pack_key.argtypes = [C.c_float, C.c_uint32]
     L.kpo_pack_key.restype = C.c_uint64
     L.kpo_propagate.argtypes = [C.POINTER(Problem), C.c_uint32, C.c_int32, vp, vp, vp, C.c_int32,
-                                C.c_int64, vp] + [vp] * 12
+                                C.c_int64, vp] + [vp] * 11
     L.kpo_select_winners.argtypes = [C.c_int32, vp, vp, C.c_int64, vp, vp, vp, C.c_int32, C.c_int32,
                                      vp, vp, vp]
     L.kpo_select_winners.restype = C.c_int32

@@ -1,0 +1,388 @@
+"""Python binding of libkpx.so, the GB300 Kino-PAX+ planning library.
+
+Thin argument marshalling over the C ABI of include/kpx.h (ctypes): the
+functions below carry the C names and every step of the planning iteration
+runs in the library's CUDA kernels.  PyTorch provides the device workspace
+(a uint8 tensor owned by the ``Planner``) and the CUDA stream.
+
+The library is loaded on first use; if it has not been built, or cannot be
+loaded, a RuntimeError is raised.  There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import scenes  # noqa: F401  (re-exported for convenience)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkpx.so")
+_lock = threading.Lock()
+_lib = None
+
+# status codes (kpx_status)
+KPX_OK, KPX_E_INVALID, KPX_E_NOMEM, KPX_E_CUDA = 0, 1, 2, 3
+KPX_TREE_FULL, KPX_NO_SOLUTION, KPX_E_TIMEOUT, KPX_E_INTERNAL = 4, 5, 6, 7
+KPX_FLAG_EARLY_REJECT = 1
+PHASES = ("begin", "propagate", "mark", "scan", "append", "prune", "end")
+KEY_INF = 0xFFFFFFFFFFFFFFFF
+
+EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_trajectory", "kpx_reset",
+            "kpx_destroy", "kpx_status_str", "kpx_last_error", "kpx_get_layout", "kpx_debug_step",
+            "kpx_snapshot", "kpx_restore")
+
+
+class kpx_dynamics(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("integ", C.c_int32), ("h", C.c_float), ("k_min", C.c_int32),
+                ("k_max", C.c_int32), ("u_lo", C.c_float * 8), ("u_hi", C.c_float * 8),
+                ("x_lo", C.c_float * 16), ("x_hi", C.c_float * 16), ("param", C.c_float * 8)]
+
+
+class kpx_workspace(C.Structure):
+    _fields_ = [("lo", C.c_float * 3), ("hi", C.c_float * 3)]
+
+
+class kpx_obstacles(C.Structure):
+    _fields_ = [("aabb", C.POINTER(C.c_float)), ("count", C.c_int32)]
+
+
+class kpx_goal(C.Structure):
+    _fields_ = [("center", C.c_float * 3), ("radius", C.c_float)]
+
+
+class kpx_cost(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("w_effort", C.c_float)]
+
+
+class kpx_region_axis(C.Structure):
+    _fields_ = [("state_dim", C.c_int32), ("bins", C.c_int32), ("lo", C.c_float), ("hi", C.c_float),
+                ("wrap", C.c_int32)]
+
+
+class kpx_config(C.Structure):
+    _fields_ = [("tree_cap", C.c_int32), ("samples_per_node", C.c_int32), ("n_axes", C.c_int32),
+                ("axis", kpx_region_axis * 8), ("i_max", C.c_int32), ("seed", C.c_uint64),
+                ("flags", C.c_int32)]
+
+
+class kpx_iter_stats(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iter", C.c_int32), ("n_nodes", C.c_int32), ("n_active", C.c_int32),
+                ("n_inactive", C.c_int32), ("n_terminal", C.c_int32), ("lam", C.c_int32),
+                ("first_solution_iter", C.c_int32), ("candidates", C.c_int64), ("valid", C.c_int64),
+                ("winners", C.c_int64), ("total_candidates", C.c_int64), ("total_valid", C.c_int64),
+                ("total_winners", C.c_int64), ("best_cost", C.c_float), ("pad", C.c_float),
+                ("first_solution_ns", C.c_uint64), ("elapsed_ns", C.c_uint64),
+                ("total_steps", C.c_uint64), ("total_box_tests", C.c_uint64)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "pad"}
+
+
+class kpx_device_header(C.Structure):
+    _fields_ = [("status", C.c_int32), ("active", C.c_int32), ("iter", C.c_int32), ("n_nodes", C.c_int32),
+                ("count_A", C.c_int32), ("lam", C.c_int32), ("va_sel", C.c_int32),
+                ("first_solution_iter", C.c_int32), ("n_slots", C.c_int64), ("goal_key", C.c_uint64),
+                ("n_win", C.c_int32), ("n_kept", C.c_int32), ("count_A_next", C.c_int32), ("epoch", C.c_int32),
+                ("prop_ticket", C.c_uint64), ("win_ticket", C.c_uint32), ("prune_ticket", C.c_uint32),
+                ("n_active", C.c_int32), ("n_inactive", C.c_int32), ("n_terminal", C.c_int32), ("pad0", C.c_int32),
+                ("last_candidates", C.c_uint64), ("last_valid", C.c_uint64), ("last_winners", C.c_uint64),
+                ("total_candidates", C.c_uint64), ("total_valid", C.c_uint64), ("total_winners", C.c_uint64),
+                ("t_start_ns", C.c_uint64), ("t_first_solution_ns", C.c_uint64), ("t_last_ns", C.c_uint64),
+                ("traj_len", C.c_int32), ("pad1", C.c_int32), ("total_steps", C.c_uint64),
+                ("total_box_tests", C.c_uint64), ("err_info", C.c_uint32 * 4)]
+
+
+class kpx_layout(C.Structure):
+    _fields_ = [("header", C.c_void_p), ("x", C.c_void_p), ("u", C.c_void_p), ("K", C.c_void_p),
+                ("parent", C.c_void_p), ("key", C.c_void_p), ("region", C.c_void_p), ("set", C.c_void_p),
+                ("icount", C.c_void_p), ("region_key", C.c_void_p), ("region_snap", C.c_void_p),
+                ("va", C.c_void_p * 2), ("win_slot", C.c_void_p), ("win_mask", C.c_void_p),
+                ("obstacles", C.c_void_p), ("n", C.c_int32), ("m", C.c_int32), ("N", C.c_int32),
+                ("R", C.c_int32), ("va_cap", C.c_int32), ("n_obstacles", C.c_int32), ("slot_cap", C.c_int64),
+                ("mask_words", C.c_int64), ("workspace_bytes", C.c_size_t)]
+
+
+class kpx_debug_records(C.Structure):
+    _fields_ = [("valid", C.c_void_p), ("region", C.c_void_p), ("key", C.c_void_p), ("K", C.c_void_p),
+                ("x", C.c_void_p), ("u", C.c_void_p), ("capacity", C.c_int64)]
+
+
+def load(path: Optional[str] = None):
+    """Load libkpx.so (built by __graft_entry__.build() or ``python -m
+    paper_2602_02846_gb300.build``).  Raises RuntimeError if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError("libkpx.so is not built (%s); run __graft_entry__.build() first" % p)
+        try:
+            L = C.CDLL(p)
+        except OSError as e:
+            raise RuntimeError("cannot load libkpx.so: %s" % e) from e
+        vp = C.c_void_p
+        L.kpx_workspace_size.argtypes = [C.POINTER(kpx_dynamics), C.POINTER(kpx_config), C.c_int32]
+        L.kpx_workspace_size.restype = C.c_size_t
+        L.kpx_create.argtypes = [C.POINTER(kpx_dynamics), C.POINTER(kpx_workspace), C.POINTER(kpx_obstacles),
+                                 C.POINTER(C.c_float), C.POINTER(kpx_goal), C.POINTER(kpx_cost),
+                                 C.POINTER(kpx_config), vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.kpx_create.restype = C.c_int
+        L.kpx_iterate.argtypes = [vp, C.c_int32, C.POINTER(kpx_iter_stats)]
+        L.kpx_iterate.restype = C.c_int
+        L.kpx_best_trajectory.argtypes = [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                          C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_float)]
+        L.kpx_best_trajectory.restype = C.c_int
+        L.kpx_reset.argtypes = [vp]
+        L.kpx_reset.restype = C.c_int
+        L.kpx_destroy.argtypes = [vp]
+        L.kpx_destroy.restype = C.c_int
+        L.kpx_status_str.argtypes = [C.c_int]
+        L.kpx_status_str.restype = C.c_char_p
+        L.kpx_last_error.argtypes = [vp]
+        L.kpx_last_error.restype = C.c_char_p
+        L.kpx_get_layout.argtypes = [vp, C.POINTER(kpx_layout)]
+        L.kpx_get_layout.restype = C.c_int
+        L.kpx_debug_step.argtypes = [vp, C.c_int32, C.POINTER(kpx_debug_records)]
+        L.kpx_debug_step.restype = C.c_int
+        L.kpx_snapshot.argtypes = [vp, vp]
+        L.kpx_snapshot.restype = C.c_int
+        L.kpx_restore.argtypes = [vp, vp]
+        L.kpx_restore.restype = C.c_int
+        _lib = L
+        return L
+
+
+class KpxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("kpx status %d (%s): %s" % (status, _status_name(status), msg))
+        self.status = status
+
+
+def _status_name(s):
+    try:
+        return load().kpx_status_str(int(s)).decode()
+    except Exception:
+        return "?"
+
+
+# ---------------------------------------------------------------------------
+# marshalling of a scene description (scenes.Problem) into the C structs
+# ---------------------------------------------------------------------------
+def problem_structs(prob, flags: int = 0):
+    d = kpx_dynamics()
+    d.kind, d.integ, d.h = int(prob.dyn), int(prob.integ), float(prob.h)
+    d.k_min, d.k_max = int(prob.k_min), int(prob.k_max)
+    for i in range(prob.m):
+        d.u_lo[i], d.u_hi[i] = prob.u_lo[i], prob.u_hi[i]
+    for i in range(prob.n):
+        d.x_lo[i], d.x_hi[i] = prob.x_lo[i], prob.x_hi[i]
+    for i, v in enumerate(prob.param):
+        d.param[i] = v
+    w = kpx_workspace()
+    for a in range(3):
+        w.lo[a], w.hi[a] = prob.ws_lo[a], prob.ws_hi[a]
+    g = kpx_goal()
+    for a in range(3):
+        g.center[a] = prob.goal_c[a]
+    g.radius = prob.goal_r
+    c = kpx_cost()
+    c.kind, c.w_effort = int(prob.cost_kind), float(prob.w_effort)
+    cfg = kpx_config()
+    cfg.tree_cap, cfg.samples_per_node, cfg.n_axes = int(prob.tree_cap), int(prob.lam), len(prob.axes)
+    for i, ax in enumerate(prob.axes):
+        cfg.axis[i].state_dim, cfg.axis[i].bins = ax.state_dim, ax.bins
+        cfg.axis[i].lo, cfg.axis[i].hi, cfg.axis[i].wrap = ax.lo, ax.hi, int(bool(ax.wrap))
+    cfg.i_max = int(prob.i_max)
+    cfg.seed = int(prob.seed) & 0xFFFFFFFFFFFFFFFF
+    cfg.flags = int(flags)
+    obs = np.ascontiguousarray(np.asarray(prob.obstacles, dtype=np.float32).reshape(-1, 6))
+    o = kpx_obstacles()
+    o.aabb = obs.ctypes.data_as(C.POINTER(C.c_float))
+    o.count = obs.shape[0]
+    start = np.ascontiguousarray(np.asarray(prob.start, dtype=np.float32))
+    return d, w, o, g, c, cfg, obs, start
+
+
+def kpx_workspace_size(prob, flags: int = 0) -> int:
+    """Device bytes kpx_create needs for ``prob`` (0 if the problem is invalid)."""
+    d, w, o, g, c, cfg, obs, start = problem_structs(prob, flags)
+    return int(load().kpx_workspace_size(C.byref(d), C.byref(cfg), o.count))
+
+
+class Planner:
+    """One planning problem on one GPU (kpx_create ... kpx_destroy).
+
+    The device workspace is a torch uint8 tensor owned by this object; work
+    runs on ``stream`` (default: the current torch stream of ``device``).
+    """
+
+    def __init__(self, prob, device=None, stream=None, flags: int = 0, workspace=None):
+        import torch
+        L = load()
+        self.prob = prob
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        d, w, o, g, c, cfg, obs, start = problem_structs(prob, flags)
+        self._structs = (d, w, o, g, c, cfg, obs, start)
+        size = int(L.kpx_workspace_size(C.byref(d), C.byref(cfg), o.count))
+        if size == 0:
+            raise KpxError(KPX_E_INVALID, "problem rejected by kpx_workspace_size")
+        if workspace is not None:
+            if workspace.dtype != torch.uint8 or workspace.numel() < size + 256 or not workspace.is_cuda:
+                raise KpxError(KPX_E_NOMEM, "workspace tensor must be CUDA uint8 of >= %d bytes" % (size + 256))
+            self.workspace = workspace
+        else:
+            self.workspace = torch.empty(size + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._off = (-base) % 256
+        self.ws_ptr = base + self._off
+        self.ws_bytes = size
+        h = C.c_void_p()
+        st = L.kpx_create(C.byref(d), C.byref(w), C.byref(o), start.ctypes.data_as(C.POINTER(C.c_float)),
+                          C.byref(g), C.byref(c), C.byref(cfg), C.c_void_p(self.ws_ptr), C.c_size_t(size),
+                          C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != KPX_OK:
+            raise KpxError(st, L.kpx_last_error(None).decode())
+        self.h = h
+        self.n, self.m = prob.n, prob.m
+
+    # -- C ABI calls ----------------------------------------------------------
+    def _check(self, st, ok=(KPX_OK,)):
+        if st not in ok:
+            raise KpxError(st, load().kpx_last_error(self.h).decode())
+        return st
+
+    def iterate(self, n_iters: int = 1, stats: bool = False):
+        """kpx_iterate: asynchronous unless stats are requested."""
+        L = load()
+        if stats:
+            s = kpx_iter_stats()
+            st = L.kpx_iterate(self.h, int(n_iters), C.byref(s))
+            self._check(st, (KPX_OK, KPX_TREE_FULL))
+            return s.as_dict()
+        self._check(L.kpx_iterate(self.h, int(n_iters), None))
+        return None
+
+    def best_trajectory(self, capacity: Optional[int] = None):
+        """kpx_best_trajectory: dict(states, controls, steps, cost) or None."""
+        L = load()
+        cap = int(capacity if capacity is not None else 1024)
+        while True:
+            states = np.zeros((cap + 1, self.n), np.float32)
+            controls = np.zeros((cap, self.m), np.float32)
+            steps = np.zeros(cap, np.int32)
+            ln = C.c_int32(0)
+            cost = C.c_float(0)
+            st = L.kpx_best_trajectory(self.h, cap, states.ctypes.data_as(C.POINTER(C.c_float)),
+                                       controls.ctypes.data_as(C.POINTER(C.c_float)),
+                                       steps.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ln), C.byref(cost))
+            if st == KPX_NO_SOLUTION:
+                return None
+            if st == KPX_E_INVALID and ln.value > cap and capacity is None:
+                cap = ln.value
+                continue
+            self._check(st)
+            k = ln.value
+            return dict(states=states[:k + 1], controls=controls[:k], steps=steps[:k], cost=float(cost.value))
+
+    def reset(self):
+        self._check(load().kpx_reset(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().kpx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layout(self) -> kpx_layout:
+        lay = kpx_layout()
+        self._check(load().kpx_get_layout(self.h, C.byref(lay)))
+        return lay
+
+    def debug_step(self, phase, records: Optional[dict] = None):
+        """kpx_debug_step for one phase (name or index); records: dict of
+        torch tensors from ``make_records``."""
+        ph = PHASES.index(phase) if isinstance(phase, str) else int(phase)
+        rp = None
+        if records is not None:
+            r = kpx_debug_records()
+            r.valid, r.region, r.key = records["valid"].data_ptr(), records["region"].data_ptr(), records["key"].data_ptr()
+            r.K, r.x, r.u = records["K"].data_ptr(), records["x"].data_ptr(), records["u"].data_ptr()
+            r.capacity = records["capacity"]
+            rp = C.byref(r)
+        self._check(load().kpx_debug_step(self.h, ph, rp))
+
+    def make_records(self):
+        import torch
+        cap = int(self.layout().slot_cap)
+        dev = self.device
+        return dict(valid=torch.zeros(cap, dtype=torch.uint8, device=dev),
+                    region=torch.zeros(cap, dtype=torch.int32, device=dev),
+                    key=torch.zeros(cap, dtype=torch.int64, device=dev),
+                    K=torch.zeros(cap, dtype=torch.int32, device=dev),
+                    x=torch.zeros(self.n * cap, dtype=torch.float32, device=dev),
+                    u=torch.zeros(self.m * cap, dtype=torch.float32, device=dev),
+                    capacity=cap)
+
+    def snapshot(self):
+        """kpx_snapshot into a device tensor (a full copy of the workspace)."""
+        import torch
+        buf = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self._check(load().kpx_snapshot(self.h, C.c_void_p(buf.data_ptr())))
+        return buf
+
+    def restore(self, buf):
+        self._check(load().kpx_restore(self.h, C.c_void_p(buf.data_ptr())))
+
+    # -- read-only views of the device arrays (for tests and inspection) -----
+    def _view(self, ptr, nbytes, dtype):
+        off = int(ptr) - self.ws_ptr + self._off
+        return self.workspace[off:off + nbytes].view(dtype)
+
+    def header(self) -> kpx_device_header:
+        lay = self.layout()
+        self.stream.synchronize()
+        raw = self._view(lay.header, C.sizeof(kpx_device_header), __import__("torch").uint8).cpu().numpy()
+        return kpx_device_header.from_buffer_copy(raw.tobytes())
+
+    def arrays(self, n_nodes: Optional[int] = None) -> dict:
+        """Host copies of the tree arrays (first n_nodes rows) and region keys."""
+        import torch
+        lay = self.layout()
+        h = self.header()
+        nn = h.n_nodes if n_nodes is None else n_nodes
+        N, R = lay.N, lay.R
+        x = self._view(lay.x, 4 * self.n * N, torch.float32).view(self.n, N)[:, :nn].T.cpu().numpy()
+        u = self._view(lay.u, 4 * self.m * N, torch.float32).view(self.m, N)[:, :nn].T.cpu().numpy()
+        K = self._view(lay.K, 2 * N, torch.int16)[:nn].cpu().numpy().astype(np.int32) & 0xFFFF
+        parent = self._view(lay.parent, 4 * N, torch.int32)[:nn].cpu().numpy()
+        key = self._view(lay.key, 8 * N, torch.int64)[:nn].cpu().numpy().view(np.uint64)
+        region = self._view(lay.region, 4 * N, torch.int32)[:nn].cpu().numpy()
+        setb = self._view(lay.set, N, torch.uint8)[:nn].cpu().numpy()
+        icount = self._view(lay.icount, N, torch.uint8)[:nn].cpu().numpy()
+        rk = self._view(lay.region_key, 8 * R, torch.int64).cpu().numpy().view(np.uint64)
+        snap = self._view(lay.region_snap, 8 * R, torch.int64).cpu().numpy().view(np.uint64)
+        va_ptr = lay.va[h.va_sel]
+        va = self._view(va_ptr, 4 * lay.va_cap, torch.int32)[:h.count_A].cpu().numpy()
+        return dict(header=h, x=x, u=u, K=K, parent=parent, key=key, region=region, set=setb & 3,
+                    set_raw=setb, icount=icount, region_key=rk, region_snap=snap, VA=va,
+                    n_nodes=h.n_nodes, count_A=h.count_A, iter=h.iter, goal_key=int(h.goal_key))
+
+    def win_slots(self, count: int) -> np.ndarray:
+        import torch
+        lay = self.layout()
+        return self._view(lay.win_slot, 4 * lay.R, torch.int32)[:count].cpu().numpy()
+
+
+def status_str(s: int) -> str:
+    return load().kpx_status_str(int(s)).decode()

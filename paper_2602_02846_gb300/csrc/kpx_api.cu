@@ -1,0 +1,513 @@
+// kpx_api.cu -- host side of the C ABI declared in include/kpx.h.
+//
+// Validates the problem, lays the planner's arrays out in the caller's
+// device workspace, and enqueues the per-phase kernels on the caller's
+// stream.  Allocates no device memory.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kpx_internal.h"
+
+using namespace kpx;
+
+struct kpx_planner {
+    DevParams P;
+    Layout L;
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr int kStateDim[3] = {6, 6, 12};
+constexpr int kControlDim[3] = {3, 3, 4};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool finite(float v) { return std::isfinite(v); }
+
+// Validates the scalar configuration; returns an empty string when valid.
+std::string check_config(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs) {
+    if (!dyn || !cfg) return "null dynamics or config";
+    if (dyn->kind < 0 || dyn->kind > 2) return "unknown dynamics kind";
+    if (dyn->integ != KPX_EULER && dyn->integ != KPX_RK4) return "unknown integrator";
+    if (!(dyn->h > 0.0f) || !finite(dyn->h)) return "integration step h must be positive and finite";
+    if (dyn->k_min < 1 || dyn->k_max < dyn->k_min || dyn->k_max > 4096) return "need 1 <= k_min <= k_max <= 4096";
+    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
+    for (int i = 0; i < m; ++i)
+        if (!finite(dyn->u_lo[i]) || !finite(dyn->u_hi[i]) || dyn->u_lo[i] > dyn->u_hi[i])
+            return "control bounds must be finite with lo <= hi";
+    for (int i = 0; i < n; ++i)
+        if (std::isnan(dyn->x_lo[i]) || std::isnan(dyn->x_hi[i]) || dyn->x_lo[i] > dyn->x_hi[i])
+            return "state bounds must satisfy lo <= hi";
+    if (dyn->kind == KPX_QUAD12) {
+        for (int i = 0; i < 6; ++i)
+            if (!finite(dyn->param[i])) return "quadcopter parameters must be finite";
+        if (!(dyn->param[0] > 0.0f) || !(dyn->param[2] > 0.0f) || !(dyn->param[3] > 0.0f) ||
+            !(dyn->param[4] > 0.0f) || !(dyn->param[5] > 0.0f))
+            return "quadcopter mass, inertia and tau_max must be positive";
+    }
+    if (cfg->tree_cap < 1 || cfg->tree_cap > (1 << 28)) return "tree_cap must be in [1, 2^28]";
+    if (cfg->samples_per_node < 0 || cfg->samples_per_node > 65536) return "samples_per_node must be in [0, 65536]";
+    if (cfg->n_axes < 1 || cfg->n_axes > 8) return "n_axes must be in [1, 8]";
+    int64_t R = 1;
+    for (int a = 0; a < cfg->n_axes; ++a) {
+        const kpx_region_axis& ax = cfg->axis[a];
+        if (ax.state_dim < 0 || ax.state_dim >= n) return "region axis state_dim out of range";
+        if (ax.bins < 1 || ax.bins > (1 << 20)) return "region axis bins out of range";
+        if (!finite(ax.lo) || !finite(ax.hi) || !(ax.hi > ax.lo)) return "region axis needs finite lo < hi";
+        R *= ax.bins;
+        if (R > (1 << 28)) return "too many regions (> 2^28)";
+    }
+    if (cfg->i_max < 0 || cfg->i_max > 254) return "i_max must be in [0, 254]";
+    if (n_obs < 0 || n_obs > 6000) return "obstacle count must be in [0, 6000]";
+    return "";
+}
+
+Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs) {
+    Layout L{};
+    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
+    const int64_t N = cfg->tree_cap;
+    int64_t R = 1;
+    for (int a = 0; a < cfg->n_axes; ++a) R *= cfg->axis[a].bins;
+    L.va_cap = (int32_t)(N < R ? N : R);
+    L.slot_cap = cfg->samples_per_node > 0 ? (int64_t)L.va_cap * cfg->samples_per_node : N;
+    L.mask_words = (L.slot_cap + 31) / 32;
+    L.n_win_tiles = (int32_t)((L.mask_words + WIN_TILE_WORDS - 1) / WIN_TILE_WORDS);
+    L.n_prune_tiles = (int32_t)((N + PRUNE_TILE - 1) / PRUNE_TILE);
+    L.traj_rows = (int32_t)(N < TRAJ_STAGE_ROWS ? N + 1 : TRAJ_STAGE_ROWS);
+    size_t off = 0;
+    auto seg = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    L.hdr = seg(sizeof(kpx_device_header));
+    L.obs = seg((size_t)(n_obs > 0 ? n_obs : 1) * 2 * sizeof(float4));
+    L.x = seg((size_t)n * N * sizeof(float));
+    L.u = seg((size_t)m * N * sizeof(float));
+    L.K = seg((size_t)N * sizeof(uint16_t));
+    L.parent = seg((size_t)N * sizeof(int32_t));
+    L.key = seg((size_t)N * sizeof(uint64_t));
+    L.region = seg((size_t)N * sizeof(int32_t));
+    L.set = seg((size_t)N);
+    L.icount = seg((size_t)N);
+    L.region_key = seg((size_t)R * sizeof(uint64_t));
+    L.region_snap = seg((size_t)R * sizeof(uint64_t));
+    L.va0 = seg((size_t)L.va_cap * sizeof(int32_t));
+    L.va1 = seg((size_t)L.va_cap * sizeof(int32_t));
+    L.win_slot = seg((size_t)R * sizeof(int32_t));
+    L.win_mask = seg((size_t)L.mask_words * sizeof(uint32_t));
+    L.win_tiles = seg((size_t)L.n_win_tiles * sizeof(uint64_t));
+    L.prune_tiles = seg((size_t)L.n_prune_tiles * sizeof(uint64_t));
+    L.path = seg((size_t)N * sizeof(int32_t));
+    L.traj = seg((size_t)L.traj_rows * (n + m + 1) * sizeof(float));
+    L.total = off;
+    return L;
+}
+
+// FP32 membership of x in X_valid, with the same comparisons as the kernels.
+bool host_point_valid(const DevParams& P, const float* x, const float* obs, int n_obs) {
+    for (int d = 0; d < P.n; ++d)
+        if (!(x[d] >= P.x_lo[d] && x[d] <= P.x_hi[d])) return false;
+    for (int a = 0; a < 3; ++a)
+        if (!(x[a] >= P.ws_lo[a] && x[a] <= P.ws_hi[a])) return false;
+    for (int b = 0; b < n_obs; ++b) {
+        const float* o = obs + 6 * b;
+        if (x[0] >= o[0] && x[0] <= o[3] && x[1] >= o[1] && x[1] <= o[4] && x[2] >= o[2] && x[2] <= o[5])
+            return false;
+    }
+    return true;
+}
+
+kpx_status fail(kpx_planner* p, kpx_status st, const std::string& msg) {
+    if (p) p->err = msg;
+    return st;
+}
+
+kpx_status cuda_fail(kpx_planner* p, cudaError_t e, const char* where) {
+    std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+    if (p) p->err = msg;
+    return KPX_E_CUDA;
+}
+
+void bind_pointers(kpx_planner* p) {
+    char* b = p->ws;
+    const Layout& L = p->L;
+    DevParams& P = p->P;
+    P.hdr = reinterpret_cast<kpx_device_header*>(b + L.hdr);
+    P.obs = reinterpret_cast<float4*>(b + L.obs);
+    P.x = reinterpret_cast<float*>(b + L.x);
+    P.u = reinterpret_cast<float*>(b + L.u);
+    P.K = reinterpret_cast<uint16_t*>(b + L.K);
+    P.parent = reinterpret_cast<int32_t*>(b + L.parent);
+    P.key = reinterpret_cast<uint64_t*>(b + L.key);
+    P.region = reinterpret_cast<int32_t*>(b + L.region);
+    P.set = reinterpret_cast<uint8_t*>(b + L.set);
+    P.icount = reinterpret_cast<uint8_t*>(b + L.icount);
+    P.region_key = reinterpret_cast<uint64_t*>(b + L.region_key);
+    P.region_snap = reinterpret_cast<uint64_t*>(b + L.region_snap);
+    P.va0 = reinterpret_cast<int32_t*>(b + L.va0);
+    P.va1 = reinterpret_cast<int32_t*>(b + L.va1);
+    P.win_slot = reinterpret_cast<int32_t*>(b + L.win_slot);
+    P.win_mask = reinterpret_cast<uint32_t*>(b + L.win_mask);
+    P.win_tiles = reinterpret_cast<uint64_t*>(b + L.win_tiles);
+    P.prune_tiles = reinterpret_cast<uint64_t*>(b + L.prune_tiles);
+    P.path = reinterpret_cast<int32_t*>(b + L.path);
+    P.traj = reinterpret_cast<float*>(b + L.traj);
+}
+
+kpx_status read_header(kpx_planner* p, kpx_device_header* h) {
+    cudaError_t e = cudaMemcpyAsync(h, p->P.hdr, sizeof(*h), cudaMemcpyDeviceToHost, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "reading planner counters");
+    return KPX_OK;
+}
+
+kpx_status run_phase(kpx_planner* p, int phase, const kpx_debug_records* rec) {
+    cudaError_t e = cudaSuccess;
+    switch (phase) {
+        case KPX_PHASE_BEGIN: e = launch_begin(p->P, p->stream); break;
+        case KPX_PHASE_PROPAGATE: e = launch_propagate(p->P, rec, p->stream); break;
+        case KPX_PHASE_MARK: e = launch_mark(p->P, p->stream); break;
+        case KPX_PHASE_SCAN: e = launch_scan(p->P, p->stream); break;
+        case KPX_PHASE_APPEND: e = launch_append(p->P, p->stream); break;
+        case KPX_PHASE_PRUNE: e = launch_prune(p->P, p->stream); break;
+        case KPX_PHASE_END: e = launch_end(p->P, p->stream); break;
+        default: return fail(p, KPX_E_INVALID, "unknown phase");
+    }
+    if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
+    return KPX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kpx_workspace_size(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obstacles) {
+    if (!check_config(dyn, cfg, n_obstacles).empty()) return 0;
+    return make_layout(dyn, cfg, n_obstacles).total;
+}
+
+kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                      const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                      void* device_workspace, size_t workspace_bytes, void* cuda_stream, kpx_planner** out) {
+    g_create_error.clear();
+    auto reject = [&](kpx_status st, const std::string& msg) {
+        g_create_error = msg;
+        return st;
+    };
+    if (!out) return reject(KPX_E_INVALID, "out is null");
+    *out = nullptr;
+    if (!ws || !obs || !start || !goal || !cost) return reject(KPX_E_INVALID, "null argument");
+    const int32_t n_obs = obs->count;
+    std::string msg = check_config(dyn, cfg, n_obs);
+    if (!msg.empty()) return reject(KPX_E_INVALID, msg);
+    if (n_obs > 0 && !obs->aabb) return reject(KPX_E_INVALID, "obstacle array is null");
+    if (!device_workspace) return reject(KPX_E_INVALID, "device workspace is null");
+    if (reinterpret_cast<uintptr_t>(device_workspace) % 256 != 0)
+        return reject(KPX_E_INVALID, "device workspace must be 256-byte aligned");
+    for (int a = 0; a < 3; ++a)
+        if (!finite(ws->lo[a]) || !finite(ws->hi[a]) || !(ws->hi[a] >= ws->lo[a]))
+            return reject(KPX_E_INVALID, "workspace box needs finite lo <= hi");
+    for (int i = 0; i < 6 * n_obs; ++i)
+        if (!finite(obs->aabb[i])) return reject(KPX_E_INVALID, "obstacle coordinates must be finite");
+    for (int b = 0; b < n_obs; ++b)
+        for (int a = 0; a < 3; ++a)
+            if (obs->aabb[6 * b + a] > obs->aabb[6 * b + 3 + a]) return reject(KPX_E_INVALID, "obstacle box with lo > hi");
+    for (int a = 0; a < 3; ++a)
+        if (!finite(goal->center[a])) return reject(KPX_E_INVALID, "goal centre must be finite");
+    if (!finite(goal->radius) || goal->radius < 0.0f) return reject(KPX_E_INVALID, "goal radius must be >= 0");
+    if (cost->kind < 0 || cost->kind > 2) return reject(KPX_E_INVALID, "unknown cost kind");
+    if (!finite(cost->w_effort) || cost->w_effort < 0.0f) return reject(KPX_E_INVALID, "w_effort must be >= 0");
+    if (cost->kind == KPX_COST_EFFORT_DURATION && dyn->kind != KPX_QUAD12)
+        return reject(KPX_E_INVALID, "effort+duration cost needs the quadcopter");
+    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
+    for (int i = 0; i < n; ++i)
+        if (!finite(start[i])) return reject(KPX_E_INVALID, "start state must be finite");
+
+    Layout L = make_layout(dyn, cfg, n_obs);
+    if (workspace_bytes < L.total) return reject(KPX_E_NOMEM, "device workspace smaller than kpx_workspace_size()");
+    if ((uint64_t)cfg->tree_cap + (uint64_t)L.slot_cap >= 0xFFFFFFFFull)
+        return reject(KPX_E_INVALID, "tree_cap + candidate slots must stay below 2^32");
+
+    kpx_planner* p = new (std::nothrow) kpx_planner();
+    if (!p) return reject(KPX_E_NOMEM, "host allocation failed");
+    p->L = L;
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    p->ws = reinterpret_cast<char*>(device_workspace);
+    p->ws_bytes = workspace_bytes;
+    DevParams& P = p->P;
+    memset(&P, 0, sizeof(P));
+    P.dyn = dyn->kind;
+    P.integ = dyn->integ;
+    P.n = n;
+    P.m = m;
+    P.h = dyn->h;
+    P.k_min = dyn->k_min;
+    P.k_max = dyn->k_max;
+    for (int i = 0; i < 8; ++i) {
+        P.u_lo[i] = i < m ? dyn->u_lo[i] : 0.0f;
+        P.u_hi[i] = i < m ? dyn->u_hi[i] : 0.0f;
+        P.param[i] = dyn->param[i];
+    }
+    for (int i = 0; i < 16; ++i) {
+        P.x_lo[i] = i < n ? dyn->x_lo[i] : -INFINITY;
+        P.x_hi[i] = i < n ? dyn->x_hi[i] : INFINITY;
+        P.start[i] = i < n ? start[i] : 0.0f;
+    }
+    for (int a = 0; a < 3; ++a) {
+        P.ws_lo[a] = ws->lo[a];
+        P.ws_hi[a] = ws->hi[a];
+        P.goal_c[a] = goal->center[a];
+    }
+    P.goal_r2 = goal->radius * goal->radius;
+    P.cost_kind = cost->kind;
+    P.w_effort = cost->w_effort;
+    if (dyn->kind == KPX_QUAD12) {
+        P.mg = dyn->param[0] * dyn->param[1];
+        P.inv_mg = 1.0f / P.mg;
+        P.inv_mass = 1.0f / dyn->param[0];
+        P.inv_tau_max = 1.0f / dyn->param[5];
+        for (int i = 0; i < 3; ++i) {
+            P.J[i] = dyn->param[2 + i];
+            P.inv_J[i] = 1.0f / dyn->param[2 + i];
+        }
+    }
+    P.n_axes = cfg->n_axes;
+    for (int a = 0; a < cfg->n_axes; ++a) {
+        const kpx_region_axis& ax = cfg->axis[a];
+        P.ax_dim[a] = ax.state_dim;
+        P.ax_bins[a] = ax.bins;
+        P.ax_wrap[a] = ax.wrap ? 1 : 0;
+        P.ax_lo[a] = ax.lo;
+        const float width = ax.hi - ax.lo;
+        P.ax_scale[a] = (float)ax.bins / width;
+    }
+    int64_t R = 1;
+    for (int a = 0; a < cfg->n_axes; ++a) R *= cfg->axis[a].bins;
+    P.N = cfg->tree_cap;
+    P.R = (int32_t)R;
+    P.lambda_fixed = cfg->samples_per_node;
+    P.i_max = cfg->i_max;
+    P.seed_lo = (uint32_t)(cfg->seed & 0xFFFFFFFFull);
+    P.seed_hi = (uint32_t)(cfg->seed >> 32);
+    P.flags = cfg->flags;
+    P.n_obs = n_obs;
+    P.va_cap = L.va_cap;
+    P.slot_cap = L.slot_cap;
+    P.mask_words = L.mask_words;
+    P.n_win_tiles = L.n_win_tiles;
+    P.n_prune_tiles = L.n_prune_tiles;
+    bind_pointers(p);
+
+    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) {
+        delete p;
+        return reject(KPX_E_INVALID, "start state is not in X_valid");
+    }
+    std::vector<float4> ob((size_t)2 * (n_obs > 0 ? n_obs : 1));
+    for (int b = 0; b < n_obs; ++b) {
+        const float* o = obs->aabb + 6 * b;
+        ob[2 * b] = make_float4(o[0], o[1], o[2], 0.0f);
+        ob[2 * b + 1] = make_float4(o[3], o[4], o[5], 0.0f);
+    }
+    cudaError_t e = cudaSuccess;
+    if (n_obs > 0)
+        e = cudaMemcpyAsync(P.obs, ob.data(), (size_t)2 * n_obs * sizeof(float4), cudaMemcpyHostToDevice, p->stream);
+    if (e == cudaSuccess) e = launch_init(P, true, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // the host copy buffer is local
+    if (e != cudaSuccess) {
+        g_create_error = std::string("kpx_create: ") + cudaGetErrorString(e);
+        delete p;
+        return KPX_E_CUDA;
+    }
+    *out = p;
+    return KPX_OK;
+}
+
+kpx_status kpx_iterate(kpx_planner* p, int32_t n_iters, kpx_iter_stats* out_last) {
+    if (!p) return KPX_E_INVALID;
+    if (n_iters < 0) return fail(p, KPX_E_INVALID, "n_iters must be >= 0");
+    for (int32_t it = 0; it < n_iters; ++it) {
+        for (int ph = KPX_PHASE_BEGIN; ph <= KPX_PHASE_END; ++ph) {
+            kpx_status st = run_phase(p, ph, nullptr);
+            if (st != KPX_OK) return st;
+        }
+    }
+    if (!out_last) return KPX_OK;
+    kpx_device_header h;
+    kpx_status st = read_header(p, &h);
+    if (st != KPX_OK) return st;
+    memset(out_last, 0, sizeof(*out_last));
+    out_last->status = h.status;
+    out_last->iter = h.iter;
+    out_last->n_nodes = h.n_nodes;
+    out_last->n_active = h.count_A;
+    out_last->n_inactive = h.n_inactive;
+    out_last->n_terminal = h.n_terminal;
+    out_last->lambda = h.lambda;
+    out_last->first_solution_iter = h.first_solution_iter;
+    out_last->candidates = (int64_t)h.last_candidates;
+    out_last->valid = (int64_t)h.last_valid;
+    out_last->winners = (int64_t)h.last_winners;
+    out_last->total_candidates = (int64_t)h.total_candidates;
+    out_last->total_valid = (int64_t)h.total_valid;
+    out_last->total_winners = (int64_t)h.total_winners;
+    if (h.goal_key == KEY_INF) {
+        out_last->best_cost = INFINITY;
+    } else {
+        uint32_t bits = (uint32_t)(h.goal_key >> 32);
+        float c;
+        memcpy(&c, &bits, sizeof c);
+        out_last->best_cost = c;
+    }
+    out_last->first_solution_ns =
+        (h.first_solution_iter >= 0 && h.t_first_solution_ns > h.t_start_ns) ? h.t_first_solution_ns - h.t_start_ns : 0;
+    out_last->elapsed_ns = h.t_last_ns > h.t_start_ns ? h.t_last_ns - h.t_start_ns : 0;
+    out_last->total_steps = h.total_steps;
+    out_last->total_box_tests = h.total_box_tests;
+    if (h.status == KPX_E_TIMEOUT || h.status == KPX_E_INTERNAL) {
+        char buf[128];
+        snprintf(buf, sizeof buf, "device status %d (info %08x %08x)", h.status, h.err_info[0], h.err_info[1]);
+        p->err = buf;
+    }
+    return (kpx_status)h.status;
+}
+
+kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, float* controls, int32_t* steps,
+                               int32_t* out_len, float* out_cost) {
+    if (!p || !out_len) return KPX_E_INVALID;
+    *out_len = 0;
+    cudaError_t e = launch_path(p->P, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "path kernel");
+    kpx_device_header h;
+    kpx_status st = read_header(p, &h);
+    if (st != KPX_OK) return st;
+    if (h.traj_len < 0) return KPX_NO_SOLUTION;
+    const int len = h.traj_len;
+    *out_len = len;
+    if (len > capacity) return fail(p, KPX_E_INVALID, "trajectory capacity too small (see *out_len)");
+    if (!states || (len > 0 && (!controls || !steps))) return fail(p, KPX_E_INVALID, "null output array");
+    const int n = p->P.n, m = p->P.m, w = n + m + 1;
+    std::vector<float> buf((size_t)p->L.traj_rows * w);
+    for (int first = 0; first <= len; first += p->L.traj_rows) {
+        const int rows = (len + 1 - first) < p->L.traj_rows ? (len + 1 - first) : p->L.traj_rows;
+        e = launch_gather(p->P, first, rows, p->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(buf.data(), p->P.traj, (size_t)rows * w * sizeof(float), cudaMemcpyDeviceToHost,
+                                p->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "trajectory gather");
+        for (int r = 0; r < rows; ++r) {
+            const int g = first + r;
+            const float* row = buf.data() + (size_t)r * w;
+            memcpy(states + (size_t)g * n, row, n * sizeof(float));
+            if (g >= 1) {
+                memcpy(controls + (size_t)(g - 1) * m, row + n, m * sizeof(float));
+                int k;
+                memcpy(&k, row + n + m, sizeof k);
+                steps[g - 1] = k;
+            }
+        }
+    }
+    if (out_cost) {
+        uint32_t bits = (uint32_t)(h.goal_key >> 32);
+        memcpy(out_cost, &bits, sizeof(float));
+    }
+    return KPX_OK;
+}
+
+kpx_status kpx_reset(kpx_planner* p) {
+    if (!p) return KPX_E_INVALID;
+    cudaError_t e = launch_init(p->P, false, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "reset");
+    return KPX_OK;
+}
+
+kpx_status kpx_destroy(kpx_planner* p) {
+    if (!p) return KPX_OK;
+    cudaError_t e = cudaStreamSynchronize(p->stream);
+    delete p;
+    return e == cudaSuccess ? KPX_OK : KPX_E_CUDA;
+}
+
+const char* kpx_status_str(kpx_status s) {
+    switch (s) {
+        case KPX_OK: return "ok";
+        case KPX_E_INVALID: return "invalid argument";
+        case KPX_E_NOMEM: return "workspace too small";
+        case KPX_E_CUDA: return "CUDA error";
+        case KPX_TREE_FULL: return "tree full";
+        case KPX_NO_SOLUTION: return "no solution";
+        case KPX_E_TIMEOUT: return "device wait timed out";
+        case KPX_E_INTERNAL: return "internal consistency check failed";
+    }
+    return "unknown status";
+}
+
+const char* kpx_last_error(const kpx_planner* p) { return p ? p->err.c_str() : g_create_error.c_str(); }
+
+kpx_status kpx_get_layout(const kpx_planner* p, kpx_layout* out) {
+    if (!p || !out) return KPX_E_INVALID;
+    const DevParams& P = p->P;
+    memset(out, 0, sizeof(*out));
+    out->header = P.hdr;
+    out->x = P.x;
+    out->u = P.u;
+    out->K = P.K;
+    out->parent = P.parent;
+    out->key = P.key;
+    out->region = P.region;
+    out->set = P.set;
+    out->icount = P.icount;
+    out->region_key = P.region_key;
+    out->region_snap = P.region_snap;
+    out->va[0] = P.va0;
+    out->va[1] = P.va1;
+    out->win_slot = P.win_slot;
+    out->win_mask = P.win_mask;
+    out->obstacles = reinterpret_cast<float*>(P.obs);
+    out->n = P.n;
+    out->m = P.m;
+    out->N = P.N;
+    out->R = P.R;
+    out->va_cap = P.va_cap;
+    out->n_obstacles = P.n_obs;
+    out->slot_cap = P.slot_cap;
+    out->mask_words = P.mask_words;
+    out->workspace_bytes = p->L.total;
+    return KPX_OK;
+}
+
+kpx_status kpx_debug_step(kpx_planner* p, int32_t phase, const kpx_debug_records* records) {
+    if (!p) return KPX_E_INVALID;
+    if (records && records->valid && records->capacity < p->P.slot_cap)
+        return fail(p, KPX_E_INVALID, "debug record capacity below the slot capacity");
+    return run_phase(p, phase, phase == KPX_PHASE_PROPAGATE ? records : nullptr);
+}
+
+kpx_status kpx_snapshot(kpx_planner* p, void* dst) {
+    if (!p || !dst) return KPX_E_INVALID;
+    cudaError_t e = cudaMemcpyAsync(dst, p->ws, p->L.total, cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return e == cudaSuccess ? KPX_OK : cuda_fail(p, e, "snapshot");
+}
+
+kpx_status kpx_restore(kpx_planner* p, const void* src) {
+    if (!p || !src) return KPX_E_INVALID;
+    cudaError_t e = cudaMemcpyAsync(p->ws, src, p->L.total, cudaMemcpyDefault, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    return e == cudaSuccess ? KPX_OK : cuda_fail(p, e, "restore");
+}
+
+}  // extern "C"

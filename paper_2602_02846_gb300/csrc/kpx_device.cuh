@@ -1,0 +1,322 @@
+// kpx_device.cuh -- device-side arithmetic of one Kino-PAX+ rollout.
+//
+// Compiled with -fmad=false: every FP32 operation rounds once, and fused
+// multiply-adds appear only where written as fmaf().  The propagate kernel
+// and the append kernel inline the same functions, so a winner's rollout is
+// re-materialised bit-identically from (seed, iteration, node, sample).
+#pragma once
+
+#include <cstdint>
+
+#include "kpx_internal.h"
+
+namespace kpx {
+
+// --------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 products per 4-word counter, key bumped by the Weyl constants.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// "Randomly sample u and dt" (Alg. 2): counter (iteration, node, sample,
+// block), key = seed words.  u_i = lo + (hi - lo) * f, f = (w >> 8) 2^-24,
+// one FP32 rounding per operation; K from word m (block 1 word 0 when m = 4).
+template <int M>
+__device__ __forceinline__ void sample_control(const DevParams& P, uint32_t iter, uint32_t node, uint32_t s,
+                                               float (&u)[M], int& K) {
+    const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
+    const uint4 w0 = philox4x32_10(make_uint4(iter, node, s, 0u), key);
+    const uint32_t w[4] = {w0.x, w0.y, w0.z, w0.w};
+    uint32_t wk;
+    if (M == 4) {
+        const uint4 w1 = philox4x32_10(make_uint4(iter, node, s, 1u), key);
+        wk = w1.x;
+    } else {
+        wk = w[M];
+    }
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        const float f = __fmul_rn(__uint2float_rn(w[i] >> 8), 0x1p-24f);
+        u[i] = __fadd_rn(P.u_lo[i], __fmul_rn(__fsub_rn(P.u_hi[i], P.u_lo[i]), f));
+    }
+    const uint64_t range = (uint64_t)(P.k_max - P.k_min + 1);
+    K = P.k_min + (int)(((uint64_t)wk * range) >> 32);
+}
+
+// --------------------------------------------------------------------------
+// Dynamics (the three systems of Sec. V; textbook equations).
+// --------------------------------------------------------------------------
+template <int DYN>
+struct Dims;
+template <>
+struct Dims<KPX_DI6> {
+    static constexpr int n = 6, m = 3;
+};
+template <>
+struct Dims<KPX_DUBINS6> {
+    static constexpr int n = 6, m = 3;
+};
+template <>
+struct Dims<KPX_QUAD12> {
+    static constexpr int n = 12, m = 4;
+};
+
+template <int DYN>
+__device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<DYN>::n],
+                                      const float (&u)[Dims<DYN>::m], float (&dx)[Dims<DYN>::n]) {
+    if constexpr (DYN == KPX_DI6) {
+        // p' = v, v' = a
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            dx[i] = x[3 + i];
+            dx[3 + i] = u[i];
+        }
+    } else if constexpr (DYN == KPX_DUBINS6) {
+        // (x, y, z)' = v (cos psi cos gamma, sin psi cos gamma, sin gamma); angles and speed follow u
+        float sp, cp, sg, cg;
+        sincosf(x[3], &sp, &cp);
+        sincosf(x[4], &sg, &cg);
+        const float vc = x[5] * cg;
+        dx[0] = vc * cp;
+        dx[1] = vc * sp;
+        dx[2] = x[5] * sg;
+        dx[3] = u[0];
+        dx[4] = u[1];
+        dx[5] = u[2];
+    } else {
+        // p' = v; v' = (T/m) R(phi,theta,psi) e3 - g e3 (R = Rz Ry Rx);
+        // (phi,theta,psi)' = W(phi,theta) omega; omega' = J^-1 (tau - omega x J omega)
+        float sph, cph, sth, cth, sps, cps;
+        sincosf(x[3], &sph, &cph);
+        sincosf(x[4], &sth, &cth);
+        sincosf(x[5], &sps, &cps);
+        const float inv_cth = 1.0f / cth;
+        const float tth = sth * inv_cth;
+        const float p = x[9], q = x[10], r = x[11];
+        const float a = u[0] * P.inv_mass;
+        const float sthcph = sth * cph;
+        const float r13 = fmaf(cps, sthcph, sps * sph);
+        const float r23 = fmaf(sps, sthcph, -(cps * sph));
+        const float r33 = cth * cph;
+        dx[0] = x[6];
+        dx[1] = x[7];
+        dx[2] = x[8];
+        const float t1 = fmaf(sph, q, cph * r);
+        dx[3] = fmaf(tth, t1, p);
+        dx[4] = fmaf(cph, q, -(sph * r));
+        dx[5] = t1 * inv_cth;
+        dx[6] = a * r13;
+        dx[7] = a * r23;
+        dx[8] = fmaf(a, r33, -P.param[1]);
+        dx[9] = fmaf(-(P.J[2] - P.J[1]) * q, r, u[1]) * P.inv_J[0];
+        dx[10] = fmaf(-(P.J[0] - P.J[2]) * r, p, u[2]) * P.inv_J[1];
+        dx[11] = fmaf(-(P.J[1] - P.J[0]) * p, q, u[3]) * P.inv_J[2];
+    }
+}
+
+// One PropagateODE step: forward Euler or classic RK4, control held constant.
+template <int DYN, int INTEG>
+__device__ __forceinline__ void step(const DevParams& P, float (&x)[Dims<DYN>::n], const float (&u)[Dims<DYN>::m]) {
+    constexpr int n = Dims<DYN>::n;
+    const float h = P.h;
+    float k1[n];
+    deriv<DYN>(P, x, u, k1);
+    if constexpr (INTEG == KPX_EULER) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) x[i] = fmaf(h, k1[i], x[i]);
+    } else {
+        const float hh = 0.5f * h;
+        const float h6 = h * (1.0f / 6.0f);
+        float xt[n], k2[n], k3[n], k4[n];
+#pragma unroll
+        for (int i = 0; i < n; ++i) xt[i] = fmaf(hh, k1[i], x[i]);
+        deriv<DYN>(P, xt, u, k2);
+#pragma unroll
+        for (int i = 0; i < n; ++i) xt[i] = fmaf(hh, k2[i], x[i]);
+        deriv<DYN>(P, xt, u, k3);
+#pragma unroll
+        for (int i = 0; i < n; ++i) xt[i] = fmaf(h, k3[i], x[i]);
+        deriv<DYN>(P, xt, u, k4);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const float s = fmaf(2.0f, k2[i] + k3[i], k1[i] + k4[i]);
+            x[i] = fmaf(h6, s, x[i]);
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Validity of one checked point (X_valid of Sec. III): state bounds, the
+// closed workspace box, and no closed obstacle box containing the position.
+// NaN fails every comparison and is therefore invalid.
+// --------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ bool bounds_ok(const DevParams& P, const float (&x)[N]) {
+    bool ok = true;
+#pragma unroll
+    for (int d = 0; d < N; ++d) ok &= (x[d] >= P.x_lo[d]) & (x[d] <= P.x_hi[d]);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ok &= (x[a] >= P.ws_lo[a]) & (x[a] <= P.ws_hi[a]);
+    return ok;
+}
+
+// Tests the point against the boxes in order; returns true on the first box
+// containing it.  `tests` accumulates the number of boxes examined.
+__device__ __forceinline__ bool hits_obstacle(const float4* __restrict__ s_obs, int n_obs, float px, float py,
+                                              float pz, uint32_t& tests) {
+    for (int b = 0; b < n_obs; ++b) {
+        const float4 lo = s_obs[2 * b];
+        const float4 hi = s_obs[2 * b + 1];
+        const bool in = (px >= lo.x) & (px <= hi.x) & (py >= lo.y) & (py <= hi.y) & (pz >= lo.z) & (pz <= hi.z);
+        if (in) {
+            tests += (uint32_t)(b + 1);
+            return true;
+        }
+    }
+    tests += (uint32_t)n_obs;
+    return false;
+}
+
+// --------------------------------------------------------------------------
+// Edge cost (Assumption 1): path length accumulated per step, duration K h,
+// or effort+duration K h (1 + w e(u)).
+// --------------------------------------------------------------------------
+template <int M>
+__device__ __forceinline__ float edge_cost(const DevParams& P, int K, float path_len, const float (&u)[M]) {
+    if (P.cost_kind == KPX_COST_PATH_LENGTH) return path_len;
+    const float dur = __fmul_rn(__int2float_rn(K), P.h);
+    if (P.cost_kind == KPX_COST_DURATION || M < 4) return dur;
+    const float dt = (u[0] - P.mg) * P.inv_mg;
+    float e = dt * dt;
+#pragma unroll
+    for (int i = 1; i < M; ++i) {
+        const float t = u[i] * P.inv_tau_max;
+        e = fmaf(t, t, e);
+    }
+    return dur * fmaf(P.w_effort, e, 1.0f);
+}
+
+// PropagateODE over K steps.  CHECK = true tests every step's state (the
+// propagate kernel); CHECK = false reproduces the same arithmetic without
+// the checks (the append kernel re-materialises winners that passed them).
+template <int DYN, int INTEG, bool CHECK, bool OBST>
+__device__ __forceinline__ bool rollout(const DevParams& P, float (&x)[Dims<DYN>::n], const float (&u)[Dims<DYN>::m],
+                                        int K, float& path_len, const float4* __restrict__ s_obs, uint32_t& steps,
+                                        uint32_t& tests) {
+    float len = 0.0f;
+    const bool want_len = P.cost_kind == KPX_COST_PATH_LENGTH;
+    for (int k = 0; k < K; ++k) {
+        const float p0 = x[0], p1 = x[1], p2 = x[2];
+        step<DYN, INTEG>(P, x, u);
+        ++steps;
+        if (want_len) {
+            const float dx = x[0] - p0, dy = x[1] - p1, dz = x[2] - p2;
+            len = len + sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+        if constexpr (CHECK) {
+            if (!bounds_ok(P, x)) {
+                path_len = len;
+                return false;
+            }
+            if constexpr (OBST) {
+                if (hits_obstacle(s_obs, P.n_obs, x[0], x[1], x[2], tests)) {
+                    path_len = len;
+                    return false;
+                }
+            }
+        }
+    }
+    path_len = len;
+    return true;
+}
+
+// Obstacle pass alone over a re-integrated segment (used after an early cost
+// check; same integration arithmetic as rollout()).
+template <int DYN, int INTEG>
+__device__ __forceinline__ bool obstacle_pass(const DevParams& P, float (&x)[Dims<DYN>::n],
+                                              const float (&u)[Dims<DYN>::m], int K, const float4* __restrict__ s_obs,
+                                              uint32_t& steps, uint32_t& tests) {
+    for (int k = 0; k < K; ++k) {
+        step<DYN, INTEG>(P, x, u);
+        ++steps;
+        if (hits_obstacle(s_obs, P.n_obs, x[0], x[1], x[2], tests)) return false;
+    }
+    return true;
+}
+
+// --------------------------------------------------------------------------
+// Region map (decomposition R of Sec. IV): per axis
+// c = clamp(floor((x - lo) * scale), 0, bins - 1) in FP32, one rounding per
+// operation; a wrapped axis first maps psi -> psi - 2 pi floor((psi + pi) / 2 pi).
+// --------------------------------------------------------------------------
+template <int N>
+__device__ __forceinline__ int region_of(const DevParams& P, const float (&x)[N]) {
+    constexpr float PI_F = 3.14159265358979323846f;
+    constexpr float TWO_PI_F = 6.28318530717958647692f;
+    int id = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        if (a < P.n_axes) {
+            float xv = x[0];
+#pragma unroll
+            for (int d = 1; d < N; ++d)
+                if (P.ax_dim[a] == d) xv = x[d];
+            if (P.ax_wrap[a]) {
+                const float t = __fdiv_rn(__fadd_rn(xv, PI_F), TWO_PI_F);
+                xv = __fsub_rn(xv, __fmul_rn(TWO_PI_F, floorf(t)));
+            }
+            const float t = __fmul_rn(__fsub_rn(xv, P.ax_lo[a]), P.ax_scale[a]);
+            int c = (int)floorf(t);
+            c = c < 0 ? 0 : c;
+            c = c > P.ax_bins[a] - 1 ? P.ax_bins[a] - 1 : c;
+            id = id * P.ax_bins[a] + c;
+        }
+    }
+    return id;
+}
+
+__device__ __forceinline__ bool in_goal(const DevParams& P, float px, float py, float pz) {
+    const float dx = px - P.goal_c[0], dy = py - P.goal_c[1], dz = pz - P.goal_c[2];
+    return fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= P.goal_r2;
+}
+
+__device__ __forceinline__ uint64_t pack_key(float cost, uint32_t id) {
+    return ((uint64_t)__float_as_uint(cost) << 32) | (uint64_t)id;
+}
+
+__device__ __forceinline__ float key_cost(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// first device error wins; TREE_FULL only replaces OK
+__device__ __forceinline__ void set_status(kpx_device_header* h, int code) {
+    atomicCAS(&h->status, (int)KPX_OK, code);
+}
+
+}  // namespace kpx

@@ -1,0 +1,106 @@
+// kpx_internal.h -- private declarations shared by the kernels and the C ABI.
+//
+// Everything here is an implementation detail of libkpx.so: the kernel
+// parameter block, the workspace layout, and the launchers of the per-phase
+// kernels.  The public surface is include/kpx.h.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "kpx.h"
+
+namespace kpx {
+
+constexpr uint64_t KEY_INF = ~0ull;
+
+// node-set byte: bits 0-1 the set, bit 2 the memoised "a strict ancestor is
+// dominated" flag (monotone: once an ancestor is dominated it stays so).
+enum : uint8_t { SET_A = 1, SET_I = 2, SET_T = 3, SET_MASK = 3, SET_ANC = 4 };
+
+// work partitioning constants
+constexpr int PROP_THREADS = 256;
+constexpr int WIN_THREADS = 256;
+constexpr int WIN_WORDS_PER_THREAD = 8;
+constexpr int WIN_TILE_WORDS = WIN_THREADS * WIN_WORDS_PER_THREAD;   // 2048 words = 65536 slots
+constexpr int PRUNE_THREADS = 256;
+constexpr int PRUNE_PER_THREAD = 4;
+constexpr int PRUNE_TILE = PRUNE_THREADS * PRUNE_PER_THREAD;         // 1024 nodes
+constexpr int TRAJ_STAGE_ROWS = 65536;                               // trajectory gather chunk
+
+// Parameter block passed by value to every kernel.
+struct DevParams {
+    // problem (FP32 throughout, as given by the caller)
+    int32_t dyn, integ, n, m;
+    float h;
+    int32_t k_min, k_max;
+    float u_lo[8], u_hi[8];
+    float x_lo[16], x_hi[16];
+    float param[8];
+    float ws_lo[3], ws_hi[3];
+    float goal_c[3], goal_r2;
+    int32_t cost_kind;
+    float w_effort;
+    float mg, inv_mg, inv_tau_max, inv_mass;
+    float inv_J[3], J[3];
+    int32_t n_axes;
+    int32_t ax_dim[8], ax_bins[8], ax_wrap[8];
+    float ax_lo[8], ax_scale[8];
+    float start[16];
+    // planner
+    int32_t N, R, lambda_fixed, i_max;
+    uint32_t seed_lo, seed_hi;
+    int32_t flags, n_obs;
+    int32_t va_cap;
+    int32_t pad0;
+    int64_t slot_cap, mask_words;
+    int32_t n_win_tiles, n_prune_tiles;
+    // device arrays (inside the caller's workspace)
+    kpx_device_header* hdr;
+    float* x;
+    float* u;
+    uint16_t* K;
+    int32_t* parent;
+    uint64_t* key;
+    int32_t* region;
+    uint8_t* set;
+    uint8_t* icount;
+    uint64_t* region_key;
+    uint64_t* region_snap;
+    int32_t* va0;
+    int32_t* va1;
+    int32_t* win_slot;
+    uint32_t* win_mask;
+    uint64_t* win_tiles;
+    uint64_t* prune_tiles;
+    float4* obs;          // [2*n_obs]: lo (x,y,z,0), hi (x,y,z,0)
+    int32_t* path;        // [N] node ids root -> goal
+    float* traj;          // staging: states [(TRAJ_STAGE_ROWS+1) n], controls [TRAJ_STAGE_ROWS m], steps
+};
+
+// Workspace layout (byte offsets from the workspace base).
+struct Layout {
+    size_t hdr, obs, x, u, K, parent, key, region, set, icount;
+    size_t region_key, region_snap, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, path, traj;
+    size_t total;
+    int32_t va_cap;
+    int64_t slot_cap, mask_words;
+    int32_t n_win_tiles, n_prune_tiles;
+    int32_t traj_rows;
+};
+
+// launchers (kpx_kernels.cu); each returns the launch status
+cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s);
+cudaError_t launch_begin(const DevParams& P, cudaStream_t s);
+cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s);
+cudaError_t launch_mark(const DevParams& P, cudaStream_t s);
+cudaError_t launch_scan(const DevParams& P, cudaStream_t s);
+cudaError_t launch_append(const DevParams& P, cudaStream_t s);
+cudaError_t launch_prune(const DevParams& P, cudaStream_t s);
+cudaError_t launch_end(const DevParams& P, cudaStream_t s);
+cudaError_t launch_path(const DevParams& P, cudaStream_t s);
+cudaError_t launch_gather(const DevParams& P, int32_t first_row, int32_t rows, cudaStream_t s);
+
+}  // namespace kpx

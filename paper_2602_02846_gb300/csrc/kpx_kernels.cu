@@ -1,0 +1,687 @@
+// kpx_kernels.cu -- the sm_103a kernels of one Kino-PAX+ iteration.
+//
+// Launch order per iteration (all counts are read from device memory, so
+// the sequence has a fixed launch shape and can be captured in a graph):
+//   begin      lambda (fixed or floor(t_e/|V_A|)), slot count, tickets,
+//              region-key snapshot when the capacity rule could trigger
+//   propagate  Alg. 2: one thread per (active node, sample) slot
+//   mark       V_U filter: a region whose key holds a candidate id marks
+//              that candidate's slot in a bitmask
+//   scan       winners ranked in ascending slot order (decoupled look-back)
+//   append     UpdateTree (Alg. 4): winners re-materialised from Philox and
+//              appended at n_nodes + rank; capacity rule; solution update
+//   prune      PruneNodes (Alg. 3) over the pre-append tree, fused with the
+//              compaction of the next V_A list (Alg. 5)
+//   end        counters
+#include <cuda_runtime.h>
+
+#include "kpx_device.cuh"
+
+namespace kpx {
+
+namespace {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr uint32_t LOOKBACK_POLL_LIMIT = 1u << 20;
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one value per thread.
+// ---------------------------------------------------------------------------
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
+    total = s_warp[NW - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Single-pass chained scan across tiles ("decoupled look-back"): each tile
+// publishes its aggregate, then walks back over predecessors until it meets
+// an inclusive prefix.  Tile ids come from an atomic ticket, so every
+// predecessor of a waiting tile is already running.  Status word:
+// epoch (30 bits) << 34 | flag (1 aggregate, 2 prefix) << 32 | value.
+// The wait is bounded: after LOOKBACK_POLL_LIMIT polls the kernel records
+// KPX_E_TIMEOUT and continues with the partial prefix.
+__device__ uint32_t lookback(uint64_t* tiles, uint32_t tile, uint32_t agg, uint32_t epoch, kpx_device_header* H) {
+    const uint64_t E = (uint64_t)(epoch & 0x3FFFFFFFu);
+    if (tile == 0) {
+        st_relaxed_u64(&tiles[0], (E << 34) | (2ull << 32) | agg);
+        return 0u;
+    }
+    st_relaxed_u64(&tiles[tile], (E << 34) | (1ull << 32) | agg);
+    uint32_t excl = 0u;
+    int t = (int)tile - 1;
+    uint32_t polls = 0;
+    while (t >= 0) {
+        const uint64_t w = ld_relaxed_u64(&tiles[t]);
+        const uint32_t flag = (uint32_t)(w >> 32) & 3u;
+        if ((w >> 34) == E && flag != 0u) {
+            excl += (uint32_t)w;
+            if (flag == 2u) break;
+            --t;
+        } else {
+            if (++polls > LOOKBACK_POLL_LIMIT) {
+                set_status(H, KPX_E_TIMEOUT);
+                H->err_info[0] = 0x10000u | tile;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    st_relaxed_u64(&tiles[tile], (E << 34) | (2ull << 32) | (excl + agg));
+    return excl;
+}
+
+__device__ __forceinline__ const int32_t* va_current(const DevParams& P, const kpx_device_header* H) {
+    return H->va_sel ? P.va1 : P.va0;
+}
+
+// ---------------------------------------------------------------------------
+// init / reset: Alg. 1 initialisation.
+// ---------------------------------------------------------------------------
+template <int N>
+__global__ void k_init(DevParams P, int first_time) {
+    float xs[N];
+#pragma unroll
+    for (int d = 0; d < N; ++d) xs[d] = P.start[d];
+    const int root_region = region_of<N>(P, xs);
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const uint64_t root_key = pack_key(0.0f, 0u);
+    for (int64_t r = tid; r < P.R; r += stride) P.region_key[r] = (r == root_region) ? root_key : KEY_INF;
+    for (int64_t w = tid; w < P.mask_words; w += stride) P.win_mask[w] = 0u;
+    if (first_time) {
+        for (int64_t t = tid; t < P.n_win_tiles; t += stride) P.win_tiles[t] = 0ull;
+        for (int64_t t = tid; t < P.n_prune_tiles; t += stride) P.prune_tiles[t] = 0ull;
+    }
+    if (tid == 0) {
+        kpx_device_header* H = P.hdr;
+        const int32_t epoch = first_time ? 0 : H->epoch;
+        memset(H, 0, sizeof(kpx_device_header));
+        H->epoch = epoch;
+        H->status = KPX_OK;
+        H->n_nodes = 1;
+        H->count_A = 1;
+        H->first_solution_iter = -1;
+        H->goal_key = KEY_INF;
+        if (in_goal(P, xs[0], xs[1], xs[2])) {
+            H->goal_key = root_key;
+            H->first_solution_iter = 0;
+        }
+#pragma unroll
+        for (int d = 0; d < N; ++d) P.x[(int64_t)d * P.N] = xs[d];
+        for (int d = 0; d < P.m; ++d) P.u[(int64_t)d * P.N] = 0.0f;
+        P.K[0] = 0;
+        P.parent[0] = -1;
+        P.key[0] = root_key;
+        P.region[0] = root_region;
+        P.set[0] = SET_A;
+        P.icount[0] = 0;
+        P.va0[0] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// begin: branching factor, slot count, tickets; region snapshot for the
+// capacity rule (only when an overflow is possible this iteration).
+// ---------------------------------------------------------------------------
+__global__ void k_begin(DevParams P) {
+    kpx_device_header* H = P.hdr;
+    const bool active = H->status == KPX_OK;
+    const int count_A = H->count_A;
+    const int lam = P.lambda_fixed > 0 ? P.lambda_fixed : (count_A > 0 ? max(1, P.N / count_A) : 0);
+    const int64_t n_slots = active ? (int64_t)count_A * lam : 0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        H->active = active ? 1 : 0;
+        H->lambda = lam;
+        H->n_slots = n_slots;
+        H->prop_ticket = 0ull;
+        H->win_ticket = 0u;
+        H->prune_ticket = 0u;
+        H->n_win = 0;
+        H->n_kept = 0;
+        H->count_A_next = 0;
+        H->last_valid = 0ull;
+        H->n_active = H->n_inactive = H->n_terminal = 0;
+        if (active) {
+            H->epoch = (H->epoch + 1) & 0x3FFFFFFF;
+            if (H->epoch == 0) H->epoch = 1;
+            if (H->t_start_ns == 0ull) H->t_start_ns = globaltimer_ns();
+        }
+    }
+    if (!active) return;
+    const int64_t max_new = n_slots < P.R ? n_slots : P.R;
+    if ((int64_t)H->n_nodes + max_new <= P.N) return;  // capacity rule cannot trigger
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = tid; r < P.R; r += stride) P.region_snap[r] = P.region_key[r];
+}
+
+// ---------------------------------------------------------------------------
+// propagate (Alg. 2).  Warps take 32 consecutive slots at a time from an
+// atomic ticket (dynamic balance of variable-length rollouts).  Slot =
+// rank j of the parent in V_A times lambda plus sample s.
+// ---------------------------------------------------------------------------
+template <int DYN, int INTEG>
+__global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_debug_records rec, int rec_on) {
+    constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
+    extern __shared__ float4 s_obs[];
+    kpx_device_header* H = P.hdr;
+    for (int i = threadIdx.x; i < 2 * P.n_obs; i += blockDim.x) s_obs[i] = P.obs[i];
+    __syncthreads();
+    if (!H->active) return;
+    const int64_t n_slots = H->n_slots;
+    const int lam = H->lambda;
+    const uint32_t iter = (uint32_t)H->iter;
+    const int32_t* va = va_current(P, H);
+    const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) && !rec_on;
+    const int lane = threadIdx.x & 31;
+    const uint32_t cand_base = (uint32_t)P.N;
+    uint32_t steps = 0, tests = 0;
+    for (;;) {
+        unsigned long long base = 0ull;
+        if (lane == 0) base = atomicAdd((unsigned long long*)&H->prop_ticket, 32ull);
+        base = __shfl_sync(FULL, base, 0);
+        if ((int64_t)base >= n_slots) break;
+        const int64_t slot = (int64_t)base + lane;
+        bool valid = false;
+        if (slot < n_slots) {
+            const int j = (int)(slot / lam);
+            const int s = (int)(slot - (int64_t)j * lam);
+            const int node = va[j];
+            float x[n], u[m];
+#pragma unroll
+            for (int d = 0; d < n; ++d) x[d] = P.x[(int64_t)d * P.N + node];
+            const float cost0 = key_cost(P.key[node]);
+            int K;
+            sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
+            float len;
+            int r = -1;
+            uint64_t key = KEY_INF;
+            if (early) {
+                float x0[n];
+#pragma unroll
+                for (int d = 0; d < n; ++d) x0[d] = x[d];
+                bool ok = rollout<DYN, INTEG, true, false>(P, x, u, K, len, s_obs, steps, tests);
+                if (ok) {
+                    const float c = cost0 + edge_cost<m>(P, K, len, u);
+                    r = region_of<n>(P, x);
+                    key = pack_key(c, cand_base + (uint32_t)slot);
+                    ok = key < __ldcg(&P.region_key[r]);
+                    if (ok) ok = obstacle_pass<DYN, INTEG>(P, x0, u, K, s_obs, steps, tests);
+                }
+                valid = ok;
+            } else {
+                valid = rollout<DYN, INTEG, true, true>(P, x, u, K, len, s_obs, steps, tests);
+                if (valid) {
+                    const float c = cost0 + edge_cost<m>(P, K, len, u);
+                    r = region_of<n>(P, x);
+                    key = pack_key(c, cand_base + (uint32_t)slot);
+                }
+            }
+            if (valid && key < __ldcg(&P.region_key[r]))
+                atomicMin((unsigned long long*)&P.region_key[r], (unsigned long long)key);
+            if (rec_on && slot < rec.capacity) {
+                rec.valid[slot] = valid ? 1 : 0;
+                rec.region[slot] = valid ? r : -1;
+                rec.key[slot] = valid ? key : KEY_INF;
+                rec.K[slot] = K;
+#pragma unroll
+                for (int d = 0; d < n; ++d) rec.x[(int64_t)d * rec.capacity + slot] = x[d];
+#pragma unroll
+                for (int d = 0; d < m; ++d) rec.u[(int64_t)d * rec.capacity + slot] = u[d];
+            }
+        }
+        const uint32_t vb = __ballot_sync(FULL, valid);
+        if (lane == 0 && vb) atomicAdd((unsigned long long*)&H->last_valid, (unsigned long long)__popc(vb));
+    }
+    // work counters (one atomic per warp per launch)
+    unsigned long long st = steps, te = tests;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st += __shfl_down_sync(FULL, st, o);
+        te += __shfl_down_sync(FULL, te, o);
+    }
+    if (lane == 0 && st) {
+        atomicAdd((unsigned long long*)&H->total_steps, st);
+        atomicAdd((unsigned long long*)&H->total_box_tests, te);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mark: a region whose key carries a candidate id (>= N) names the slot of
+// the winner of that region (the V_U filter: "cost(x) = cost(R_i)").
+// ---------------------------------------------------------------------------
+__global__ void k_mark(DevParams P) {
+    const kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= P.R) return;
+    const uint64_t k = P.region_key[r];
+    if (k == KEY_INF) return;
+    const uint32_t id = (uint32_t)k;
+    if (id < (uint32_t)P.N) return;
+    const uint32_t slot = id - (uint32_t)P.N;
+    if ((int64_t)slot >= P.slot_cap) {  // a stale candidate id: cannot happen in a consistent state
+        set_status(P.hdr, KPX_E_INTERNAL);
+        return;
+    }
+    atomicOr(&P.win_mask[slot >> 5], 1u << (slot & 31));
+}
+
+// ---------------------------------------------------------------------------
+// scan: ranks of the marked slots in ascending slot order -> win_slot[rank];
+// clears the mask for the next iteration.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(WIN_THREADS) k_scan(DevParams P) {
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[WIN_THREADS / 32];
+    kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&H->win_ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t live_words = (H->n_slots + 31) / 32;
+    const int64_t n_tiles = (live_words + WIN_TILE_WORDS - 1) / WIN_TILE_WORDS;
+    if ((int64_t)tile >= n_tiles) return;
+    const int64_t w0 = (int64_t)tile * WIN_TILE_WORDS + (int64_t)threadIdx.x * WIN_WORDS_PER_THREAD;
+    uint32_t w[WIN_WORDS_PER_THREAD];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
+        w[i] = (w0 + i < live_words) ? P.win_mask[w0 + i] : 0u;
+        cnt += __popc(w[i]);
+    }
+    uint32_t agg;
+    const uint32_t excl = block_exclusive_scan<WIN_THREADS>(cnt, agg, s_warp);
+    if (threadIdx.x == 0) {
+        s_prefix = lookback(P.win_tiles, tile, agg, (uint32_t)H->epoch, H);
+        if ((int64_t)tile == n_tiles - 1) H->n_win = (int32_t)(s_prefix + agg);
+    }
+    __syncthreads();
+    uint32_t rank = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
+        uint32_t word = w[i];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            if (rank < (uint32_t)P.R)
+                P.win_slot[rank] = (int32_t)((w0 + i) * 32 + b);
+            else
+                set_status(H, KPX_E_INTERNAL);
+            ++rank;
+        }
+        if (w[i]) P.win_mask[w0 + i] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// append (UpdateTree, Alg. 4): each winner's rollout is re-materialised from
+// (seed, iteration, node, sample) with the propagate kernel's arithmetic,
+// written to T at n_nodes + rank, and its region key rewritten with the new
+// id.  Winners beyond the capacity restore their region from the snapshot
+// and mark the planner KPX_TREE_FULL.  Goal nodes lower the solution key.
+// ---------------------------------------------------------------------------
+template <int DYN, int INTEG>
+__global__ void __launch_bounds__(128) k_append(DevParams P) {
+    constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
+    kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    const int W = H->n_win;
+    const int n_old = H->n_nodes;
+    const int room = P.N - n_old;
+    const int kept = W < room ? W : room;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        H->n_kept = kept;
+        if (W > kept) set_status(H, KPX_TREE_FULL);
+    }
+    const int lam = H->lambda;
+    const uint32_t iter = (uint32_t)H->iter;
+    const int32_t* va = va_current(P, H);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
+        const int slot = P.win_slot[w];
+        const int j = slot / lam;
+        const int s = slot - j * lam;
+        const int node = va[j];
+        float x[n], u[m];
+#pragma unroll
+        for (int d = 0; d < n; ++d) x[d] = P.x[(int64_t)d * P.N + node];
+        const float cost0 = key_cost(P.key[node]);
+        int K;
+        sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
+        float len;
+        uint32_t st_unused = 0, te_unused = 0;
+        rollout<DYN, INTEG, false, false>(P, x, u, K, len, nullptr, st_unused, te_unused);
+        const float c = cost0 + edge_cost<m>(P, K, len, u);
+        const int r = region_of<n>(P, x);
+        const uint64_t cand_key = pack_key(c, (uint32_t)P.N + (uint32_t)slot);
+        if (P.region_key[r] != cand_key) {
+            set_status(H, KPX_E_INTERNAL);
+            H->err_info[1] = (uint32_t)slot;
+            continue;
+        }
+        if (w < kept) {
+            const int id = n_old + w;
+#pragma unroll
+            for (int d = 0; d < n; ++d) P.x[(int64_t)d * P.N + id] = x[d];
+#pragma unroll
+            for (int d = 0; d < m; ++d) P.u[(int64_t)d * P.N + id] = u[d];
+            P.K[id] = (uint16_t)K;
+            P.parent[id] = node;
+            const uint64_t k = pack_key(c, (uint32_t)id);
+            P.key[id] = k;
+            P.region[id] = r;
+            P.set[id] = SET_A;
+            P.icount[id] = 0;
+            P.region_key[r] = k;
+            if (in_goal(P, x[0], x[1], x[2])) atomicMin((unsigned long long*)&H->goal_key, (unsigned long long)k);
+        } else {
+            P.region_key[r] = P.region_snap[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// prune (PruneNodes, Alg. 3) over nodes [0, n_nodes) in the literal rule
+// order, then the compaction of V_A (Alg. 5) over [0, n_nodes + kept): new
+// winners are active by Alg. 4.  A tile of PRUNE_TILE consecutive ids keeps
+// ascending order; tiles are chained by the look-back scan.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[PRUNE_THREADS / 32];
+    kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    if (threadIdx.x == 0) s_tile = atomicAdd(&H->prune_ticket, 1u);
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int n_old = H->n_nodes;
+    const int total = n_old + H->n_kept;
+    const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
+    if ((int)tile >= n_tiles) return;
+    const uint64_t* __restrict__ rk = P.region_key;
+    const int i_max = P.i_max;
+    const int base = (int)tile * PRUNE_TILE + threadIdx.x * PRUNE_PER_THREAD;
+    uint32_t amask = 0;
+    int cA = 0, cI = 0, cT = 0;
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+        const int i = base + q;
+        if (i >= total) break;
+        if (i >= n_old) {  // appended this iteration: in V_A
+            amask |= 1u << q;
+            ++cA;
+            continue;
+        }
+        const uint8_t sb = P.set[i];
+        const int st = sb & SET_MASK;
+        if (st == SET_T) {  // V_T is permanent
+            ++cT;
+            continue;
+        }
+        const uint64_t k = P.key[i];
+        const uint64_t rkv = rk[P.region[i]];
+        const bool best = k == rkv;
+        int ic = P.icount[i];
+        const int ic0 = ic;
+        int nst = st;
+        bool anc = (sb & SET_ANC) != 0;
+        bool done = false;
+        if (best && st == SET_I) {  // rule 1: region best while inactive
+            ++ic;
+            if (ic > i_max) {
+                nst = SET_A;
+                done = true;
+            }
+        }
+        if (!done && ic > i_max && best) done = true;  // rule 2
+        if (!done && k > rkv) {                         // rule 3: dominated
+            nst = SET_T;
+            done = true;
+        }
+        if (!done) {  // rule 4: any strict ancestor dominated
+            if (!anc) {
+                int p = P.parent[i];
+                while (p >= 0) {
+                    const uint8_t sp = *(volatile const uint8_t*)&P.set[p];
+                    if ((sp & SET_MASK) == SET_T || (sp & SET_ANC)) {
+                        anc = true;
+                        break;
+                    }
+                    if (P.key[p] != rk[P.region[p]]) {
+                        anc = true;
+                        break;
+                    }
+                    p = P.parent[p];
+                }
+            }
+            if (anc) nst = SET_I;
+        }
+        const uint8_t nb = (uint8_t)(nst | (anc ? SET_ANC : 0));
+        if (nb != sb) P.set[i] = nb;
+        if (ic != ic0) P.icount[i] = (uint8_t)ic;
+        if (nst == SET_A) {
+            amask |= 1u << q;
+            ++cA;
+        } else if (nst == SET_I) {
+            ++cI;
+        } else {
+            ++cT;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_exclusive_scan<PRUNE_THREADS>((uint32_t)__popc(amask), agg, s_warp);
+    if (threadIdx.x == 0) {
+        s_prefix = lookback(P.prune_tiles, tile, agg, (uint32_t)H->epoch, H);
+        if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
+    }
+    __syncthreads();
+    int32_t* va_next = H->va_sel ? P.va0 : P.va1;
+    uint32_t pos = s_prefix + excl;
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+        if (amask & (1u << q)) {
+            // at most one active node per region, so pos < min(N, R) = va_cap
+            if (pos < (uint32_t)P.va_cap)
+                va_next[pos] = base + q;
+            else
+                set_status(H, KPX_E_INTERNAL);
+            ++pos;
+        }
+    }
+    // set sizes for the statistics
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cA += __shfl_down_sync(FULL, cA, o);
+        cI += __shfl_down_sync(FULL, cI, o);
+        cT += __shfl_down_sync(FULL, cT, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cA) atomicAdd(&H->n_active, cA);
+        if (cI) atomicAdd(&H->n_inactive, cI);
+        if (cT) atomicAdd(&H->n_terminal, cT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// end: commit the counters of the iteration.
+// ---------------------------------------------------------------------------
+__global__ void k_end(DevParams P) {
+    kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    H->n_nodes += H->n_kept;
+    H->count_A = H->count_A_next;
+    H->va_sel ^= 1;
+    H->last_candidates = (uint64_t)H->n_slots;
+    H->last_winners = (uint64_t)H->n_kept;
+    H->total_candidates += (uint64_t)H->n_slots;
+    H->total_valid += H->last_valid;
+    H->total_winners += (uint64_t)H->n_kept;
+    const uint64_t now = globaltimer_ns();
+    if (H->goal_key != KEY_INF && H->first_solution_iter < 0) {
+        H->first_solution_iter = H->iter;
+        H->t_first_solution_ns = now;
+    }
+    H->iter += 1;
+    H->t_last_ns = now;
+}
+
+// ---------------------------------------------------------------------------
+// solution extraction: parent walk from the best goal node.
+// ---------------------------------------------------------------------------
+__global__ void k_path(DevParams P) {
+    kpx_device_header* H = P.hdr;
+    const uint64_t gk = H->goal_key;
+    if (gk == KEY_INF) {
+        H->traj_len = -1;
+        return;
+    }
+    const int id = (int)(uint32_t)gk;
+    int len = 0;
+    for (int p = id; P.parent[p] >= 0 && len < P.N; p = P.parent[p]) ++len;
+    H->traj_len = len;
+    int p = id;
+    for (int k = len; k >= 0; --k) {
+        P.path[k] = p;
+        p = P.parent[p];
+    }
+}
+
+__global__ void k_gather(DevParams P, int first, int rows) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int node = P.path[first + r];
+    const int w = P.n + P.m + 1;
+    float* row = P.traj + (int64_t)r * w;
+    for (int d = 0; d < P.n; ++d) row[d] = P.x[(int64_t)d * P.N + node];
+    for (int d = 0; d < P.m; ++d) row[P.n + d] = P.u[(int64_t)d * P.N + node];
+    row[P.n + P.m] = __int_as_float((int)P.K[node]);
+}
+
+template <int DYN, int INTEG>
+cudaError_t launch_propagate_t(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = (size_t)P.n_obs * 2 * sizeof(float4);
+    static bool attr_done[3][2] = {};
+    if (!attr_done[DYN][INTEG]) {
+        cudaFuncSetAttribute(k_propagate<DYN, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_done[DYN][INTEG] = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<DYN, INTEG>, PROP_THREADS, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t need = (P.slot_cap + PROP_THREADS - 1) / PROP_THREADS;
+    int64_t grid = (int64_t)sms * per_sm;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kpx_debug_records r{};
+    int on = 0;
+    if (rec && rec->valid) {
+        r = *rec;
+        on = 1;
+    }
+    k_propagate<DYN, INTEG><<<(unsigned)grid, PROP_THREADS, smem, s>>>(P, r, on);
+    return cudaGetLastError();
+}
+
+template <int DYN, int INTEG>
+cudaError_t launch_append_t(const DevParams& P, cudaStream_t s) {
+    int blocks = (P.R + 127) / 128;
+    if (blocks > 4096) blocks = 4096;
+    k_append<DYN, INTEG><<<blocks, 128, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+#define KPX_DISPATCH(FN, P, ...)                                                         \
+    switch ((P).dyn * 2 + (P).integ) {                                                  \
+        case KPX_DI6 * 2 + KPX_EULER: return FN<KPX_DI6, KPX_EULER>(P, __VA_ARGS__);         \
+        case KPX_DI6 * 2 + KPX_RK4: return FN<KPX_DI6, KPX_RK4>(P, __VA_ARGS__);             \
+        case KPX_DUBINS6 * 2 + KPX_EULER: return FN<KPX_DUBINS6, KPX_EULER>(P, __VA_ARGS__); \
+        case KPX_DUBINS6 * 2 + KPX_RK4: return FN<KPX_DUBINS6, KPX_RK4>(P, __VA_ARGS__);     \
+        case KPX_QUAD12 * 2 + KPX_EULER: return FN<KPX_QUAD12, KPX_EULER>(P, __VA_ARGS__);   \
+        case KPX_QUAD12 * 2 + KPX_RK4: return FN<KPX_QUAD12, KPX_RK4>(P, __VA_ARGS__);       \
+        default: return cudaErrorInvalidValue;                                          \
+    }
+
+cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s) {
+    int64_t work = P.R > P.mask_words ? P.R : P.mask_words;
+    int blocks = (int)((work + 255) / 256);
+    if (blocks > 2048) blocks = 2048;
+    if (blocks < 1) blocks = 1;
+    if (P.n == 12)
+        k_init<12><<<blocks, 256, 0, s>>>(P, first_time ? 1 : 0);
+    else
+        k_init<6><<<blocks, 256, 0, s>>>(P, first_time ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_begin(const DevParams& P, cudaStream_t s) {
+    int blocks = (P.R + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    k_begin<<<blocks, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s) {
+    KPX_DISPATCH(launch_propagate_t, P, rec, s);
+}
+
+cudaError_t launch_mark(const DevParams& P, cudaStream_t s) {
+    k_mark<<<(P.R + 255) / 256, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const DevParams& P, cudaStream_t s) {
+    k_scan<<<P.n_win_tiles, WIN_THREADS, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_append(const DevParams& P, cudaStream_t s) { KPX_DISPATCH(launch_append_t, P, s); }
+
+cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
+    k_prune<<<P.n_prune_tiles, PRUNE_THREADS, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_end(const DevParams& P, cudaStream_t s) {
+    k_end<<<1, 1, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_path(const DevParams& P, cudaStream_t s) {
+    k_path<<<1, 1, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const DevParams& P, int32_t first_row, int32_t rows, cudaStream_t s) {
+    if (rows <= 0) return cudaSuccess;
+    k_gather<<<(rows + 127) / 128, 128, 0, s>>>(P, first_row, rows);
+    return cudaGetLastError();
+}
+
+}  // namespace kpx

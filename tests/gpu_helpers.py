@@ -1,0 +1,161 @@
+"""Helpers for the GPU parity tests: run one iteration of the CUDA planner
+phase by phase and compare each phase with the FP64 oracle on the same
+inputs.
+
+Tolerances (stated once, used everywhere):
+  * decisions (regions, winners, node sets, ids, counts) are compared
+    bit-exactly when both sides see identical inputs; the oracle's winner
+    selection, append and prune are fed the GPU's candidate keys;
+  * propagated end states: |gpu - oracle| / max(1, |oracle|) <= 1e-4 per
+    component (FP32 integration against FP64, one segment);
+  * validity verdicts, region ids and goal tests must agree except where the
+    oracle finds a checked point within 1e-4 of a face, a bound or a cell
+    boundary; such slots are counted and reported.
+"""
+import numpy as np
+
+import oracle
+
+REL_TOL = 1e-4
+NEAR = 1e-4
+A, I, T = 1, 2, 3
+
+
+def rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b) / np.maximum(1.0, np.abs(b))
+
+
+def oracle_inputs(arr):
+    return arr["x"].astype(np.float64), oracle.key_cost(arr["key"]).astype(np.float64)
+
+
+def records_host(rec, n, m, ns):
+    return dict(
+        valid=rec["valid"][:ns].cpu().numpy(),
+        region=rec["region"][:ns].cpu().numpy(),
+        key=rec["key"][:ns].cpu().numpy().view(np.uint64),
+        K=rec["K"][:ns].cpu().numpy(),
+        x=rec["x"].view(n, -1)[:, :ns].T.cpu().numpy(),
+        u=rec["u"].view(m, -1)[:, :ns].T.cpu().numpy(),
+    )
+
+
+def compare_propagate(prob, g, o, slots=None):
+    """GPU records g vs oracle propagate o (same slots).  Returns a report."""
+    if slots is not None:
+        g = {k: v[slots] for k, v in g.items()}
+    assert np.array_equal(g["K"], o["K"]), "K differs"
+    assert np.array_equal(g["u"].view(np.uint32), o["u"].view(np.uint32)), "controls differ"
+    near_v = o["vmargin"] < NEAR
+    vmis = (g["valid"] != o["valid"])
+    assert np.all(~vmis | near_v), "validity differs away from any boundary: %s" % np.nonzero(vmis & ~near_v)[0][:10]
+    both = (g["valid"] == 1) & (o["valid"] == 1)
+    err = rel_err(g["x"][both], o["x_end"][both])
+    max_err = float(err.max()) if err.size else 0.0
+    assert max_err <= REL_TOL, "end state error %.3g" % max_err
+    near_r = o["rmargin"][both] < NEAR
+    rmis = g["region"][both] != o["region"][both]
+    assert np.all(~rmis | near_r), "region differs away from a cell boundary"
+    gcost = oracle.key_cost(g["key"][both]).astype(np.float64)
+    cerr = rel_err(gcost, o["cost"][both])
+    assert cerr.size == 0 or cerr.max() <= REL_TOL, "cost error %.3g" % cerr.max()
+    gid = (g["key"][both] & np.uint64(0xFFFFFFFF))
+    oid = (o["key"][both] & np.uint64(0xFFFFFFFF))
+    assert np.array_equal(gid, oid), "candidate ids differ"
+    return dict(slots=int(len(g["K"])), valid=int(g["valid"].sum()), both_valid=int(both.sum()),
+                validity_exempt=int((vmis & near_v).sum()), region_exempt=int((rmis & near_r).sum()),
+                max_state_err=max_err, max_cost_err=float(cerr.max()) if cerr.size else 0.0)
+
+
+def step_phases(pl, prob, check_append=True):
+    """Runs one iteration phase by phase on the GPU and checks every phase
+    against the oracle.  Returns the report dict."""
+    import torch
+    n, m = prob.n, prob.m
+    before = pl.arrays()
+    rec = pl.make_records()
+    pl.debug_step("begin")
+    pl.debug_step("propagate", rec)
+    h = pl.header()
+    ns, lam, it = int(h.n_slots), int(h.lam), int(h.iter)
+    N = pl.layout().N
+    g = records_host(rec, n, m, ns)
+    tx, tc = oracle_inputs(before)
+    o = oracle.propagate(prob, it, lam, tx, tc, before["VA"], h.count_A)
+    rep = compare_propagate(prob, g, o)
+    # region argmin: the GPU's region keys after propagate equal the min over
+    # its own candidate keys (atomicMin) -- bit-exact
+    mid = pl.arrays()
+    rk_ref, win, kept, full = oracle.select_winners(before["region_key"], before["region_key"], g["valid"],
+                                                    np.where(g["valid"] == 1, g["region"], 0), g["key"],
+                                                    before["n_nodes"], N)
+    # before the capacity restore, the oracle's region keys equal the GPU's
+    rk_pre, _, _, _ = oracle.select_winners(before["region_key"], before["region_key"], g["valid"],
+                                            np.where(g["valid"] == 1, g["region"], 0), g["key"], 0, 2 ** 31 - 1)
+    assert np.array_equal(mid["region_key"], rk_pre), "region argmin differs"
+    pl.debug_step("mark")
+    pl.debug_step("scan")
+    h = pl.header()
+    W = int(h.n_win)
+    gw = pl.win_slots(W)
+    assert W == len(win), "winner count differs: gpu %d oracle %d" % (W, len(win))
+    assert np.array_equal(gw, win.astype(np.int32)), "winner slots differ"
+    pl.debug_step("append")
+    after = pl.arrays(n_nodes=before["n_nodes"] + kept)
+    h = pl.header()
+    assert int(h.n_kept) == kept
+    assert (int(h.status) == 4) == full, "capacity rule differs"
+    assert np.array_equal(after["region_key"], rk_ref_with_ids(rk_ref, g, win, kept, before["n_nodes"], N))
+    if check_append and kept:
+        n0 = before["n_nodes"]
+        ids = np.arange(n0, n0 + kept)
+        ws = win[:kept]
+        assert np.array_equal(after["parent"][ids], before["VA"][ws // lam]), "parents differ"
+        assert np.array_equal(after["K"][ids], g["K"][ws]), "K differs"
+        assert np.array_equal(after["u"][ids].view(np.uint32), g["u"][ws].view(np.uint32)), "controls differ"
+        # re-materialised winners are bit-identical to the propagate records
+        assert np.array_equal(after["x"][ids].view(np.uint32), g["x"][ws].view(np.uint32)), "re-materialised state differs"
+        assert np.array_equal(after["key"][ids] >> np.uint64(32), g["key"][ws] >> np.uint64(32))
+        assert np.array_equal(after["key"][ids] & np.uint64(0xFFFFFFFF), ids.astype(np.uint64))
+        assert np.array_equal(after["region"][ids], g["region"][ws])
+        assert np.all(after["set"][ids] == A) and np.all(after["icount"][ids] == 0)
+        # solution: least key among appended goal nodes (oracle goal test in FP64)
+        gk = before["goal_key"]
+        amb = 0
+        for i in ids:
+            inside, margin = oracle.in_goal(prob, after["x"][i].astype(np.float64))
+            if margin < NEAR:
+                amb += 1
+            if inside:
+                gk = min(gk, int(after["key"][i]))
+        if amb == 0:
+            assert int(pl.header().goal_key) == gk, "solution key differs"
+        rep["goal_exempt"] = amb
+    # prune: oracle Alg. 3 on the same (pre-append) nodes and region keys
+    s_ref, ic_ref = oracle.prune(before["key"], before["region"], before["parent"], before["set"],
+                                 before["icount"], after["region_key"], prob.i_max)
+    pl.debug_step("prune")
+    pr = pl.arrays(n_nodes=before["n_nodes"] + kept)
+    n0 = before["n_nodes"]
+    assert np.array_equal(pr["set"][:n0], s_ref), "node sets differ after prune"
+    assert np.array_equal(pr["icount"][:n0], ic_ref), "inactivity counters differ after prune"
+    pl.debug_step("end")
+    fin = pl.arrays()
+    expect_va = np.nonzero(fin["set"] == A)[0].astype(np.int32)
+    assert fin["n_nodes"] == n0 + kept
+    assert np.array_equal(fin["VA"], expect_va), "next V_A differs from the ascending active ids"
+    assert fin["iter"] == it + 1
+    rep.update(winners=W, kept=kept, full=full, n_nodes=int(fin["n_nodes"]), count_A=int(fin["count_A"]))
+    return rep
+
+
+def rk_ref_with_ids(rk_ref, g, win, kept, n0, N):
+    """Oracle region keys after append: kept winners carry their new ids."""
+    rk = rk_ref.copy()
+    for rank in range(kept):
+        s = win[rank]
+        r = g["region"][s]
+        rk[r] = (g["key"][s] & np.uint64(0xFFFFFFFF00000000)) | np.uint64(n0 + rank)
+    return rk

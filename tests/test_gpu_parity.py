@@ -1,0 +1,223 @@
+"""GPU parity: every phase of the CUDA iteration against the FP64 oracle on
+the same inputs, through the C ABI (ctypes binding).
+
+Sizes: the DI and Dubins cases run every slot of an iteration (several warps,
+tiles and a ragged tail); the full-size quadcopter and Dubins configurations
+are checked on sampled slots that the oracle evaluates one by one, in the
+same launch configuration the benchmark uses.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2602_02846_gb300 import scenes  # noqa: E402
+
+from tests import gpu_helpers as gh  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def kpx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_02846_gb300 as k
+    k.load()
+    return k
+
+
+def _run_lockstep(kpx, prob, iters, flags=0):
+    pl = kpx.Planner(prob, flags=flags)
+    reports = []
+    for _ in range(iters):
+        if pl.header().status != 0:
+            break
+        reports.append(gh.step_phases(pl, prob))
+    return pl, reports
+
+
+CASES = {
+    "di_config": lambda: scenes.di_scene(0),
+    "di_16grid": lambda: scenes.di_scene(1, grid_pos=16, tree_cap=32768),
+    "di_adaptive": lambda: scenes.di_scene(2, grid_pos=15, tree_cap=100000, lam=0),
+    "di_empty": lambda: scenes.di_scene(3, n_obstacles=0, grid_pos=12, tree_cap=20000),
+    "dubins_forest": lambda: scenes.dubins_scene(0),
+    "dubins_open": lambda: scenes.dubins_scene(1, n_obstacles=0, tree_cap=1 << 16, lam=16),
+    "quad_small": lambda: scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_iteration_lockstep(kpx, case):
+    """Several consecutive iterations, each checked phase by phase."""
+    prob = CASES[case]()
+    iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "dubins_forest": 6,
+             "dubins_open": 8, "quad_small": 3}[case]
+    pl, reps = _run_lockstep(kpx, prob, iters)
+    assert reps, "no iteration ran"
+    tot = sum(r["slots"] for r in reps)
+    ex = sum(r["validity_exempt"] + r["region_exempt"] for r in reps)
+    print(case, "slots", tot, "exempt", ex, "max err", max(r["max_state_err"] for r in reps),
+          "nodes", reps[-1]["n_nodes"])
+    assert ex <= max(2, 0.002 * tot)
+    pl.close()
+
+
+def test_capacity_rule_lockstep(kpx):
+    """The iteration that overflows the tree is checked phase by phase; the
+    planner then stays KPX_TREE_FULL and further iterations change nothing."""
+    prob = scenes.di_scene(4, grid_pos=16, tree_cap=700)
+    pl = kpx.Planner(prob)
+    full_seen = False
+    for _ in range(30):
+        rep = gh.step_phases(pl, prob)
+        if rep["full"]:
+            full_seen = True
+            break
+    assert full_seen
+    a = pl.arrays()
+    assert a["n_nodes"] == 700
+    st = pl.iterate(3, stats=True)
+    assert st["status"] == kpx.KPX_TREE_FULL
+    b = pl.arrays()
+    assert b["iter"] == a["iter"]
+    assert np.array_equal(a["region_key"], b["region_key"])
+    pl.close()
+
+
+def _sampled_propagate(kpx, prob, warm_iters, n_samples, seed=0):
+    pl = kpx.Planner(prob)
+    pl.iterate(warm_iters)
+    before = pl.arrays()
+    rec = pl.make_records()
+    pl.debug_step("begin")
+    pl.debug_step("propagate", rec)
+    h = pl.header()
+    ns = int(h.n_slots)
+    rng = np.random.default_rng(seed)
+    slots = np.unique(np.concatenate([rng.integers(0, ns, size=min(n_samples, ns)), [0, ns - 1]]))
+    g = gh.records_host(rec, prob.n, prob.m, ns)
+    tx, tc = gh.oracle_inputs(before)
+    o = oracle.propagate(prob, int(h.iter), int(h.lam), tx, tc, before["VA"], int(h.count_A), slots=slots)
+    rep = gh.compare_propagate(prob, g, o, slots=slots)
+    rep["n_slots"] = ns
+    pl.close()
+    return rep
+
+
+def test_quad_full_config_sampled(kpx):
+    """12D quadcopter at its full configuration (2^22 nodes, 16^3 x 4^3
+    regions, lambda 128, 1,000 boxes): sampled slots against the oracle."""
+    prob = scenes.quad_scene(0)
+    rep = _sampled_propagate(kpx, prob, warm_iters=4, n_samples=3000)
+    print("quad", rep)
+    assert rep["n_slots"] > 10000
+    assert rep["validity_exempt"] + rep["region_exempt"] <= max(2, 0.002 * rep["slots"])
+
+
+def test_dubins_full_config_sampled(kpx):
+    prob = scenes.dubins_scene(0)
+    rep = _sampled_propagate(kpx, prob, warm_iters=10, n_samples=3000)
+    print("dubins", rep)
+    assert rep["validity_exempt"] + rep["region_exempt"] <= max(2, 0.002 * rep["slots"])
+
+
+def _all_arrays(pl):
+    a = pl.arrays()
+    return {k: v for k, v in a.items() if k != "header"}
+
+
+def _same(a, b):
+    for k in a:
+        if isinstance(a[k], np.ndarray):
+            assert np.array_equal(np.ascontiguousarray(a[k]).view(np.uint8),
+                                  np.ascontiguousarray(b[k]).view(np.uint8)), k
+        else:
+            assert a[k] == b[k], k
+
+
+def test_production_iteration_equals_phases_and_early_reject(kpx):
+    """kpx_iterate equals the phase-by-phase sequence bit for bit, and the
+    early cost rejection (collision-after-cost) leaves every result unchanged."""
+    prob = scenes.dubins_scene(2, n_obstacles=120, tree_cap=1 << 16, lam=32)
+    pl = kpx.Planner(prob)
+    pl.iterate(5)
+    snap = pl.snapshot()
+    pl.iterate(4)
+    ref = _all_arrays(pl)
+    pl.restore(snap)
+    for _ in range(4):
+        for ph in kpx.PHASES:
+            pl.debug_step(ph)
+    _same(ref, _all_arrays(pl))
+    pl.close()
+    pe = kpx.Planner(prob, flags=kpx.KPX_FLAG_EARLY_REJECT)
+    pe.iterate(9)
+    _same(ref, _all_arrays(pe))
+    pe.close()
+
+
+def test_determinism_and_reset(kpx):
+    prob = scenes.di_scene(5, grid_pos=16, tree_cap=1 << 15)
+    a = kpx.Planner(prob)
+    b = kpx.Planner(prob)
+    a.iterate(8)
+    b.iterate(8)
+    ra = _all_arrays(a)
+    _same(ra, _all_arrays(b))
+    b.iterate(3)
+    b.reset()
+    b.iterate(8)
+    _same(ra, _all_arrays(b))
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("case", ["di_16grid", "dubins_open", "quad_small"])
+def test_tree_invariants_fp64(kpx, case):
+    """Every GPU tree edge re-rolled by the oracle in FP64 from the stored
+    parent state: same end state (1e-4), valid, cost = parent + edge."""
+    prob = CASES[case]()
+    pl = kpx.Planner(prob)
+    pl.iterate({"di_16grid": 5, "dubins_open": 12, "quad_small": 4}[case])
+    a = pl.arrays()
+    n = a["n_nodes"]
+    assert n > 50
+    cost = oracle.key_cost(a["key"]).astype(np.float64)
+    worst = 0.0
+    for i in range(1, min(n, 4000)):
+        p = a["parent"][i]
+        assert p < i
+        r = oracle.rollout(prob, a["x"][p].astype(np.float64), a["u"][i], int(a["K"][i]))
+        assert r["valid"] or r["margin"] < gh.NEAR
+        worst = max(worst, float(gh.rel_err(a["x"][i], r["x_end"]).max()))
+        assert abs(cost[i] - (cost[p] + r["edge_cost"])) <= gh.REL_TOL * max(1.0, cost[i])
+    assert worst <= gh.REL_TOL
+    # region keys: one node per visited region, V_A nodes are region-best
+    rk = a["region_key"]
+    visited = np.nonzero(rk != np.uint64(oracle.KEY_INF))[0]
+    owners = {int(a["region"][i]) for i in range(n) if a["key"][i] == rk[a["region"][i]]}
+    assert owners == set(int(r) for r in visited)
+    act = np.nonzero(a["set"] == 1)[0]
+    assert np.all(a["key"][act] == rk[a["region"][act]])
+    pl.close()
+
+
+def test_solution_revalidated_fp64(kpx):
+    """The returned trajectory re-validates in FP64 segment by segment."""
+    prob = scenes.di_scene(6, grid_pos=16, tree_cap=32768)
+    pl = kpx.Planner(prob)
+    st = pl.iterate(40, stats=True)
+    tr = pl.best_trajectory()
+    assert tr is not None, st
+    rv = oracle.revalidate(prob, tr["states"].astype(np.float64), tr["controls"], tr["steps"])
+    print("revalidate", rv, "cost", tr["cost"])
+    assert rv["max_seg_err"] <= gh.REL_TOL
+    assert rv["min_clearance"] >= -1e-4
+    assert rv["goal_slack"] >= -1e-4
+    assert abs(rv["cost"] - tr["cost"]) <= gh.REL_TOL * max(1.0, tr["cost"])
+    assert np.allclose(tr["states"][0], prob.start)
+    assert st["best_cost"] == np.float32(tr["cost"])
+    pl.close()

@@ -172,3 +172,34 @@ def test_convergence_sanity_empty_world(oracle_mod):
         finals[gp] = float(np.median(vals))
     assert finals[12] < lb * 1.15
     assert finals[20] < lb * 1.15
+
+
+def test_step_functions_reproduce_the_planner(oracle_mod):
+    """The per-step entry points (propagate, select_winners, prune) used by
+    the GPU parity tests, chained by hand, reproduce the oracle planner's own
+    iterations exactly."""
+    o = oracle_mod
+    prob = scenes.di_scene(2, grid_pos=16, tree_cap=4096)
+    pl = o.Planner(prob)
+    for _ in range(4):
+        st = pl.state()
+        lam = prob.lam
+        rec = o.propagate(prob, st["iter"], lam, st["x"], st["cost"], st["VA"], st["count_A"])
+        rk, win, kept, full = o.select_winners(st["region_key"], st["region_key"], rec["valid"],
+                                               rec["region"], rec["key"], st["n_nodes"], prob.tree_cap)
+        s_new, ic_new = o.prune(st["key"], st["region"], st["parent"], st["set"], st["icount"], rk, prob.i_max)
+        pl.iterate(1)
+        nxt = pl.state()
+        n0 = st["n_nodes"]
+        assert nxt["n_nodes"] == n0 + kept
+        assert np.array_equal(nxt["set"][:n0], s_new)
+        assert np.array_equal(nxt["icount"][:n0], ic_new)
+        for rank, c in enumerate(win[:kept]):
+            i = n0 + rank
+            assert nxt["parent"][i] == st["VA"][rec["slot"][c] // lam]
+            assert np.array_equal(nxt["x"][i], rec["x_end"][c])
+            assert nxt["cost"][i] == rec["cost"][c]
+            assert nxt["region"][i] == rec["region"][c]
+            assert nxt["K"][i] == rec["K"][c]
+            assert (int(rec["key"][c]) >> 32) == (int(nxt["key"][i]) >> 32)
+            assert nxt["region_key"][rec["region"][c]] == nxt["key"][i]
