@@ -207,6 +207,40 @@ const char* kpx_status_str(kpx_status s);
  * p == NULL the message of the last failing kpx_create in this thread. */
 const char* kpx_last_error(const kpx_planner* p);
 
+/* One complete planning run that allocates nothing (the paper has no
+ * counterpart: this is a deployment convenience of this library).
+ *
+ * Some callers cannot call cudaMalloc: code that runs while its stream is
+ * being captured into a CUDA graph (allocation is not allowed during
+ * capture), real-time control loops that must never block on an allocator or
+ * meet an out-of-memory error mid-plan, and plugins whose host application
+ * already owns the device's memory pool.  This entry point plans with device
+ * memory reserved inside the library instead: a static device array of
+ * KPX_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
+ * process exits.  It runs kpx_create + kpx_iterate(n_iters) +
+ * kpx_best_trajectory in one call, synchronously on cuda_stream, with the
+ * same arguments and outputs as those calls (host inputs; host outputs of
+ * capacity segments).  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.
+ *
+ * Limits and caveats:
+ *   - problems whose kpx_workspace_size() exceeds KPX_STATIC_SCRATCH_BYTES
+ *     are rejected with KPX_E_NOMEM (message in kpx_last_error(NULL));
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture;
+ *   - every call, from any thread or stream, uses the same array, and the
+ *     array keeps the last call's contents (each call re-initialises what it
+ *     reads); calls that overlap on the GPU race and corrupt each other.
+ * Returns KPX_OK, KPX_NO_SOLUTION (*out_len = 0), KPX_E_INVALID (bad input,
+ * or capacity too small with *out_len = required segments), KPX_E_NOMEM,
+ * KPX_E_CUDA, or a device status (KPX_E_TIMEOUT / KPX_E_INTERNAL). */
+#define KPX_STATIC_SCRATCH_BYTES (16u << 20)
+kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                           const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                           int32_t n_iters, void* cuda_stream, int32_t capacity, float* states, float* controls,
+                           int32_t* steps, int32_t* out_len, float* out_cost);
+
 /* ------------------------------------------------------------------------
  * Introspection and step-by-step API (tests, debugging, checkpointing).
  * ---------------------------------------------------------------------- */

@@ -33,7 +33,7 @@ KEY_INF = 0xFFFFFFFFFFFFFFFF
 
 EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_trajectory", "kpx_reset",
             "kpx_destroy", "kpx_status_str", "kpx_last_error", "kpx_get_layout", "kpx_debug_step",
-            "kpx_snapshot", "kpx_restore")
+            "kpx_snapshot", "kpx_restore", "kpx_plan_static")
 
 
 class kpx_dynamics(C.Structure):
@@ -153,6 +153,12 @@ def load(path: Optional[str] = None):
         L.kpx_snapshot.restype = C.c_int
         L.kpx_restore.argtypes = [vp, vp]
         L.kpx_restore.restype = C.c_int
+        L.kpx_plan_static.argtypes = [C.POINTER(kpx_dynamics), C.POINTER(kpx_workspace), C.POINTER(kpx_obstacles),
+                                      C.POINTER(C.c_float), C.POINTER(kpx_goal), C.POINTER(kpx_cost),
+                                      C.POINTER(kpx_config), C.c_int32, vp, C.c_int32, C.POINTER(C.c_float),
+                                      C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_float)]
+        L.kpx_plan_static.restype = C.c_int
         _lib = L
         return L
 
@@ -382,6 +388,34 @@ class Planner:
         import torch
         lay = self.layout()
         return self._view(lay.win_slot, 4 * lay.R, torch.int32)[:count].cpu().numpy()
+
+
+def kpx_plan_static(prob, n_iters: int, stream=None, capacity: int = 4096, flags: int = 0):
+    """One planning run in the library's static device memory (no
+    allocation anywhere; see include/kpx.h).  ``stream``: a torch CUDA stream
+    or None for the legacy default stream.  Returns (status, trajectory dict
+    or None)."""
+    L = load()
+    d, w, o, g, c, cfg, obs, start = problem_structs(prob, flags)
+    states = np.zeros((capacity + 1, prob.n), np.float32)
+    controls = np.zeros((capacity, prob.m), np.float32)
+    steps = np.zeros(capacity, np.int32)
+    ln = C.c_int32(0)
+    cost = C.c_float(0)
+    sp = C.c_void_p(stream.cuda_stream) if stream is not None else None
+    st = L.kpx_plan_static(C.byref(d), C.byref(w), C.byref(o), start.ctypes.data_as(C.POINTER(C.c_float)),
+                           C.byref(g), C.byref(c), C.byref(cfg), int(n_iters), sp, int(capacity),
+                           states.ctypes.data_as(C.POINTER(C.c_float)), controls.ctypes.data_as(C.POINTER(C.c_float)),
+                           steps.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(ln), C.byref(cost))
+    if st != KPX_OK:
+        return int(st), None
+    k = ln.value
+    return int(st), dict(states=states[:k + 1], controls=controls[:k], steps=steps[:k], cost=float(cost.value))
+
+
+def last_create_error() -> str:
+    """Message of the last failing kpx_create / kpx_plan_static in this thread."""
+    return load().kpx_last_error(None).decode()
 
 
 def status_str(s: int) -> str:

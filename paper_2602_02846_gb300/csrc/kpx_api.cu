@@ -511,3 +511,235 @@ kpx_status kpx_restore(kpx_planner* p, const void* src) {
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// kpx_plan_static: one planning run without any allocation.
+//
+// For callers that may not allocate device memory: code running while a
+// stream is being captured into a CUDA graph (allocation calls are not
+// allowed during capture), real-time control loops that must never wait on
+// an allocator or see an out-of-memory error mid-flight, and plugins whose
+// host application owns the whole device memory pool.  Their device memory
+// is this file-scope array, reserved when the library is loaded and held by
+// every GPU that loads it until the process exits.  This path deliberately
+// duplicates the parameter set-up of kpx_create instead of sharing it, so
+// that the allocating path above stays exactly as it is.
+// ===========================================================================
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)KPX_STATIC_SCRATCH_BYTES;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, never a device
+// address).
+constexpr int kMaxDevices = 64;
+void* g_static_addr[kMaxDevices] = {};
+
+cudaError_t static_scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (!g_static_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = ptr;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                                      const float* start, const kpx_goal* goal, const kpx_cost* cost,
+                                      const kpx_config* cfg, int32_t n_iters, void* cuda_stream, int32_t capacity,
+                                      float* states, float* controls, int32_t* steps, int32_t* out_len,
+                                      float* out_cost) {
+    g_create_error.clear();
+    auto reject = [&](kpx_status st, const char* msg) {
+        g_create_error = msg;
+        return st;
+    };
+    if (!out_len) return reject(KPX_E_INVALID, "out_len is null");
+    *out_len = 0;
+    if (!ws || !obs || !start || !goal || !cost) return reject(KPX_E_INVALID, "null argument");
+    if (n_iters < 0) return reject(KPX_E_INVALID, "n_iters must be >= 0");
+    const int32_t n_obs = obs->count;
+    {
+        std::string msg = check_config(dyn, cfg, n_obs);
+        if (!msg.empty()) {
+            g_create_error = msg;
+            return KPX_E_INVALID;
+        }
+    }
+    if (n_obs > 0 && !obs->aabb) return reject(KPX_E_INVALID, "obstacle array is null");
+    for (int a = 0; a < 3; ++a)
+        if (!finite(ws->lo[a]) || !finite(ws->hi[a]) || !(ws->hi[a] >= ws->lo[a]))
+            return reject(KPX_E_INVALID, "workspace box needs finite lo <= hi");
+    for (int i = 0; i < 6 * n_obs; ++i)
+        if (!finite(obs->aabb[i])) return reject(KPX_E_INVALID, "obstacle coordinates must be finite");
+    for (int b = 0; b < n_obs; ++b)
+        for (int a = 0; a < 3; ++a)
+            if (obs->aabb[6 * b + a] > obs->aabb[6 * b + 3 + a]) return reject(KPX_E_INVALID, "obstacle box with lo > hi");
+    for (int a = 0; a < 3; ++a)
+        if (!finite(goal->center[a])) return reject(KPX_E_INVALID, "goal centre must be finite");
+    if (!finite(goal->radius) || goal->radius < 0.0f) return reject(KPX_E_INVALID, "goal radius must be >= 0");
+    if (cost->kind < 0 || cost->kind > 2) return reject(KPX_E_INVALID, "unknown cost kind");
+    if (!finite(cost->w_effort) || cost->w_effort < 0.0f) return reject(KPX_E_INVALID, "w_effort must be >= 0");
+    if (cost->kind == KPX_COST_EFFORT_DURATION && dyn->kind != KPX_QUAD12)
+        return reject(KPX_E_INVALID, "effort+duration cost needs the quadcopter");
+    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
+    for (int i = 0; i < n; ++i)
+        if (!finite(start[i])) return reject(KPX_E_INVALID, "start state must be finite");
+    const Layout L = make_layout(dyn, cfg, n_obs);
+    if (L.total > kStaticScratchBytes)
+        return reject(KPX_E_NOMEM, "problem needs more device memory than the static scratch of "
+                                   "kpx_plan_static (KPX_STATIC_SCRATCH_BYTES); use kpx_create with a workspace");
+    if ((uint64_t)cfg->tree_cap + (uint64_t)L.slot_cap >= 0xFFFFFFFFull)
+        return reject(KPX_E_INVALID, "tree_cap + candidate slots must stay below 2^32");
+
+    kpx_planner pl;  // host handle on the stack: nothing is allocated
+    pl.L = L;
+    pl.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    void* scratch = nullptr;
+    cudaError_t e = static_scratch_address(&scratch);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("kpx_plan_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    pl.ws = reinterpret_cast<char*>(scratch);
+    pl.ws_bytes = kStaticScratchBytes;
+    DevParams& P = pl.P;
+    memset(&P, 0, sizeof(P));
+    P.dyn = dyn->kind;
+    P.integ = dyn->integ;
+    P.n = n;
+    P.m = m;
+    P.h = dyn->h;
+    P.k_min = dyn->k_min;
+    P.k_max = dyn->k_max;
+    for (int i = 0; i < 8; ++i) {
+        P.u_lo[i] = i < m ? dyn->u_lo[i] : 0.0f;
+        P.u_hi[i] = i < m ? dyn->u_hi[i] : 0.0f;
+        P.param[i] = dyn->param[i];
+    }
+    for (int i = 0; i < 16; ++i) {
+        P.x_lo[i] = i < n ? dyn->x_lo[i] : -INFINITY;
+        P.x_hi[i] = i < n ? dyn->x_hi[i] : INFINITY;
+        P.start[i] = i < n ? start[i] : 0.0f;
+    }
+    for (int a = 0; a < 3; ++a) {
+        P.ws_lo[a] = ws->lo[a];
+        P.ws_hi[a] = ws->hi[a];
+        P.goal_c[a] = goal->center[a];
+    }
+    P.goal_r2 = goal->radius * goal->radius;
+    P.cost_kind = cost->kind;
+    P.w_effort = cost->w_effort;
+    if (dyn->kind == KPX_QUAD12) {
+        P.mg = dyn->param[0] * dyn->param[1];
+        P.inv_mg = 1.0f / P.mg;
+        P.inv_mass = 1.0f / dyn->param[0];
+        P.inv_tau_max = 1.0f / dyn->param[5];
+        for (int i = 0; i < 3; ++i) {
+            P.J[i] = dyn->param[2 + i];
+            P.inv_J[i] = 1.0f / dyn->param[2 + i];
+        }
+    }
+    P.n_axes = cfg->n_axes;
+    int64_t R = 1;
+    for (int a = 0; a < cfg->n_axes; ++a) {
+        const kpx_region_axis& ax = cfg->axis[a];
+        P.ax_dim[a] = ax.state_dim;
+        P.ax_bins[a] = ax.bins;
+        P.ax_wrap[a] = ax.wrap ? 1 : 0;
+        P.ax_lo[a] = ax.lo;
+        const float width = ax.hi - ax.lo;
+        P.ax_scale[a] = (float)ax.bins / width;
+        R *= ax.bins;
+    }
+    P.N = cfg->tree_cap;
+    P.R = (int32_t)R;
+    P.lambda_fixed = cfg->samples_per_node;
+    P.i_max = cfg->i_max;
+    P.seed_lo = (uint32_t)(cfg->seed & 0xFFFFFFFFull);
+    P.seed_hi = (uint32_t)(cfg->seed >> 32);
+    P.flags = cfg->flags;
+    P.n_obs = n_obs;
+    P.va_cap = L.va_cap;
+    P.slot_cap = L.slot_cap;
+    P.mask_words = L.mask_words;
+    P.n_win_tiles = L.n_win_tiles;
+    P.n_prune_tiles = L.n_prune_tiles;
+    bind_pointers(&pl);
+    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) return reject(KPX_E_INVALID, "start state is not in X_valid");
+
+    // obstacles: lo and hi corners copied straight from the caller's
+    // float[M][6] into the float4 pairs the kernels read (no staging buffer)
+    if (n_obs > 0) {
+        e = cudaMemcpy2DAsync(P.obs, 2 * sizeof(float4), obs->aabb, 6 * sizeof(float), 3 * sizeof(float), n_obs,
+                              cudaMemcpyHostToDevice, pl.stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(reinterpret_cast<char*>(P.obs) + sizeof(float4), 2 * sizeof(float4), obs->aabb + 3,
+                                  6 * sizeof(float), 3 * sizeof(float), n_obs, cudaMemcpyHostToDevice, pl.stream);
+    }
+    // every array that must start at zero is cleared by the first-time init
+    if (e == cudaSuccess) e = launch_init(P, true, pl.stream);
+    for (int32_t it = 0; e == cudaSuccess && it < n_iters; ++it) {
+        e = launch_begin(P, pl.stream);
+        if (e == cudaSuccess) e = launch_propagate(P, nullptr, pl.stream);
+        if (e == cudaSuccess) e = launch_mark(P, pl.stream);
+        if (e == cudaSuccess) e = launch_scan(P, pl.stream);
+        if (e == cudaSuccess) e = launch_append(P, pl.stream);
+        if (e == cudaSuccess) e = launch_prune(P, pl.stream);
+        if (e == cudaSuccess) e = launch_end(P, pl.stream);
+    }
+    if (e == cudaSuccess) e = launch_path(P, pl.stream);
+    kpx_device_header h;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, P.hdr, sizeof(h), cudaMemcpyDeviceToHost, pl.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(pl.stream);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("kpx_plan_static: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    if (h.status == KPX_E_TIMEOUT || h.status == KPX_E_INTERNAL) return reject((kpx_status)h.status, "device status");
+    if (h.traj_len < 0) return KPX_NO_SOLUTION;
+    const int len = h.traj_len;
+    *out_len = len;
+    if (len > capacity) return reject(KPX_E_INVALID, "trajectory capacity too small (see *out_len)");
+    if (!states || (len > 0 && (!controls || !steps))) return reject(KPX_E_INVALID, "null output array");
+    const size_t w = (size_t)(n + m + 1) * sizeof(float);
+    for (int first = 0; e == cudaSuccess && first <= len; first += L.traj_rows) {
+        const int rows = (len + 1 - first) < L.traj_rows ? (len + 1 - first) : L.traj_rows;
+        e = launch_gather(P, first, rows, pl.stream);
+        // staging row r holds node path[first + r]: its state, then the
+        // control and step count of the segment that ends at it
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(states + (size_t)first * n, n * sizeof(float), P.traj, w, n * sizeof(float), rows,
+                                  cudaMemcpyDeviceToHost, pl.stream);
+        const int skip = first == 0 ? 1 : 0;  // the root has no incoming segment
+        if (e == cudaSuccess && rows > skip) {
+            e = cudaMemcpy2DAsync(controls + (size_t)(first + skip - 1) * m, m * sizeof(float),
+                                  P.traj + (size_t)skip * (n + m + 1) + n, w, m * sizeof(float), rows - skip,
+                                  cudaMemcpyDeviceToHost, pl.stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(steps + (first + skip - 1), sizeof(int32_t),
+                                      P.traj + (size_t)skip * (n + m + 1) + n + m, w, sizeof(int32_t), rows - skip,
+                                      cudaMemcpyDeviceToHost, pl.stream);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(pl.stream);
+    }
+    if (e != cudaSuccess) {
+        g_create_error = std::string("kpx_plan_static: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    if (out_cost) {
+        uint32_t bits = (uint32_t)(h.goal_key >> 32);
+        memcpy(out_cost, &bits, sizeof(float));
+    }
+    return KPX_OK;
+}
