@@ -268,7 +268,8 @@ typedef struct {
  * x: float[n][N] (component d of node i at x[d*N + i]), u: float[m][N],
  * K: uint16[N], parent: int32[N] (root: -1), key: uint64[N] ((FP32 cost
  * bits << 32) | id), region: int32[N], set: uint8[N] (bits 0-1: 1 = V_A,
- * 2 = V_I, 3 = V_T; bit 2: a strict ancestor is dominated), icount: uint8[N],
+ * 2 = V_I, 3 = V_T; bit 2: a strict ancestor is dominated; bit 3: the node
+ * no longer holds its region's key), icount: uint8[N],
  * region_key: uint64[R], region_snap: uint64[R], va[2]: int32[va_cap] each
  * (the current V_A list is va[header.va_sel]), win_slot: int32[R],
  * win_mask: uint32[mask_words], obstacles: float[M][8] (lo x, y, z, 0,

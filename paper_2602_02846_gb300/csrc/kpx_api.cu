@@ -23,6 +23,11 @@ struct kpx_planner {
     char* ws;
     size_t ws_bytes;
     std::string err;
+    // iterations captured as CUDA graphs (built on first use; launched on `stream`)
+    int graph_state = 0;  // 0 not tried, 1 ready, -1 unavailable (plain launches)
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph_one = nullptr;
+    cudaGraphExec_t graph_many = nullptr;
 };
 
 namespace {
@@ -94,6 +99,9 @@ Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs
     };
     L.hdr = seg(sizeof(kpx_device_header));
     L.obs = seg((size_t)(n_obs > 0 ? n_obs : 1) * 2 * sizeof(float4));
+    L.box_cells = seg((size_t)(n_obs > 0 ? n_obs : 1) * 6 * sizeof(int32_t));
+    L.cell_start = seg((size_t)(GRID_MAX_CELLS + 1) * sizeof(int32_t));
+    L.cell_box = seg((size_t)grid_entry_budget(n_obs) * 2 * sizeof(float4));
     L.x = seg((size_t)n * N * sizeof(float));
     L.u = seg((size_t)m * N * sizeof(float));
     L.K = seg((size_t)N * sizeof(uint16_t));
@@ -104,6 +112,7 @@ Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs
     L.icount = seg((size_t)N);
     L.region_key = seg((size_t)R * sizeof(uint64_t));
     L.region_snap = seg((size_t)R * sizeof(uint64_t));
+    L.region_owner = seg((size_t)R * sizeof(int32_t));
     L.va0 = seg((size_t)L.va_cap * sizeof(int32_t));
     L.va1 = seg((size_t)L.va_cap * sizeof(int32_t));
     L.win_slot = seg((size_t)R * sizeof(int32_t));
@@ -130,6 +139,55 @@ bool host_point_valid(const DevParams& P, const float* x, const float* obs, int 
     return true;
 }
 
+// Resolution of the obstacle grid: cells about the mean box extent per axis
+// (at most GRID_MAX_AXIS per axis and GRID_MAX_CELLS in all), coarsened until
+// the cell lists fit the reserved entries.  Uses the same FP32 cell map as
+// the device, so the entry count here is the one the device build produces.
+void choose_grid(DevParams& P, const float* aabb, int n_obs) {
+    P.grid_cap = (int32_t)grid_entry_budget(n_obs);
+    int g[3] = {1, 1, 1};
+    float W[3];
+    for (int a = 0; a < 3; ++a) W[a] = P.ws_hi[a] - P.ws_lo[a];
+    if (n_obs > 0) {
+        for (int a = 0; a < 3; ++a) {
+            if (!(W[a] > 0.0f)) continue;
+            double sum = 0.0;
+            for (int b = 0; b < n_obs; ++b) {
+                double e = (double)aabb[6 * b + 3 + a] - (double)aabb[6 * b + a];
+                sum += e < (double)W[a] ? e : (double)W[a];
+            }
+            double mean = sum / n_obs;
+            if (mean < (double)W[a] / GRID_MAX_AXIS) mean = (double)W[a] / GRID_MAX_AXIS;
+            int ga = (int)((double)W[a] / mean);
+            g[a] = ga < 1 ? 1 : (ga > GRID_MAX_AXIS ? GRID_MAX_AXIS : ga);
+        }
+    }
+    for (;;) {
+        while ((int64_t)g[0] * g[1] * g[2] > GRID_MAX_CELLS) {
+            int big = g[0] >= g[1] && g[0] >= g[2] ? 0 : (g[1] >= g[2] ? 1 : 2);
+            g[big] = (g[big] + 1) / 2;
+        }
+        for (int a = 0; a < 3; ++a) {
+            P.grid_n[a] = g[a];
+            P.grid_inv[a] = W[a] > 0.0f ? (float)g[a] / W[a] : 0.0f;
+        }
+        int64_t entries = 0;
+        for (int b = 0; b < n_obs; ++b) {
+            int64_t cells = 1;
+            for (int a = 0; a < 3; ++a) {
+                const int c0 = grid_cell(aabb[6 * b + a], P.ws_lo[a], P.grid_inv[a], g[a]);
+                const int c1 = grid_cell(aabb[6 * b + 3 + a], P.ws_lo[a], P.grid_inv[a], g[a]);
+                cells *= (int64_t)(c1 - c0 + 1);
+            }
+            entries += cells;
+        }
+        if (entries <= P.grid_cap || (g[0] == 1 && g[1] == 1 && g[2] == 1)) break;
+        int big = g[0] >= g[1] && g[0] >= g[2] ? 0 : (g[1] >= g[2] ? 1 : 2);
+        g[big] = (g[big] + 1) / 2;
+    }
+    P.n_cells = g[0] * g[1] * g[2];
+}
+
 kpx_status fail(kpx_planner* p, kpx_status st, const std::string& msg) {
     if (p) p->err = msg;
     return st;
@@ -147,6 +205,9 @@ void bind_pointers(kpx_planner* p) {
     DevParams& P = p->P;
     P.hdr = reinterpret_cast<kpx_device_header*>(b + L.hdr);
     P.obs = reinterpret_cast<float4*>(b + L.obs);
+    P.box_cells = reinterpret_cast<int32_t*>(b + L.box_cells);
+    P.cell_start = reinterpret_cast<int32_t*>(b + L.cell_start);
+    P.cell_box = reinterpret_cast<float4*>(b + L.cell_box);
     P.x = reinterpret_cast<float*>(b + L.x);
     P.u = reinterpret_cast<float*>(b + L.u);
     P.K = reinterpret_cast<uint16_t*>(b + L.K);
@@ -157,6 +218,7 @@ void bind_pointers(kpx_planner* p) {
     P.icount = reinterpret_cast<uint8_t*>(b + L.icount);
     P.region_key = reinterpret_cast<uint64_t*>(b + L.region_key);
     P.region_snap = reinterpret_cast<uint64_t*>(b + L.region_snap);
+    P.region_owner = reinterpret_cast<int32_t*>(b + L.region_owner);
     P.va0 = reinterpret_cast<int32_t*>(b + L.va0);
     P.va1 = reinterpret_cast<int32_t*>(b + L.va1);
     P.win_slot = reinterpret_cast<int32_t*>(b + L.win_slot);
@@ -172,6 +234,51 @@ kpx_status read_header(kpx_planner* p, kpx_device_header* h) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "reading planner counters");
     return KPX_OK;
+}
+
+constexpr int kGraphIterations = 8;
+
+cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s) {
+    cudaError_t e = launch_begin(P, s);
+    if (e == cudaSuccess) e = launch_propagate(P, nullptr, s);
+    if (e == cudaSuccess) e = launch_mark(P, s);
+    if (e == cudaSuccess) e = launch_scan(P, s);
+    if (e == cudaSuccess) e = launch_append(P, s);
+    if (e == cudaSuccess) e = launch_prune(P, s);
+    if (e == cudaSuccess) e = launch_end(P, s);
+    return e;
+}
+
+cudaError_t capture_iterations(kpx_planner* p, int count, cudaGraphExec_t* exec) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < count && le == cudaSuccess; ++i) le = enqueue_iteration(p->P, p->capture_stream);
+    e = cudaStreamEndCapture(p->capture_stream, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+// Builds the two iteration graphs once; on any failure the planner keeps
+// using plain launches (same kernels, same order).
+void ensure_graphs(kpx_planner* p) {
+    if (p->graph_state != 0) return;
+    p->graph_state = -1;
+    prepare_launches(p->P);
+    if (cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        p->capture_stream = nullptr;
+        return;
+    }
+    if (capture_iterations(p, 1, &p->graph_one) == cudaSuccess &&
+        capture_iterations(p, kGraphIterations, &p->graph_many) == cudaSuccess) {
+        p->graph_state = 1;
+        return;
+    }
+    cudaGetLastError();
 }
 
 kpx_status run_phase(kpx_planner* p, int phase, const kpx_debug_records* rec) {
@@ -310,6 +417,7 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
     P.n_win_tiles = L.n_win_tiles;
     P.n_prune_tiles = L.n_prune_tiles;
     bind_pointers(p);
+    choose_grid(P, obs->aabb, n_obs);
 
     if (!host_point_valid(P, P.start, obs->aabb, n_obs)) {
         delete p;
@@ -325,6 +433,7 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
     if (n_obs > 0)
         e = cudaMemcpyAsync(P.obs, ob.data(), (size_t)2 * n_obs * sizeof(float4), cudaMemcpyHostToDevice, p->stream);
     if (e == cudaSuccess) e = launch_init(P, true, p->stream);
+    if (e == cudaSuccess) e = launch_grid_build(P, p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // the host copy buffer is local
     if (e != cudaSuccess) {
         g_create_error = std::string("kpx_create: ") + cudaGetErrorString(e);
@@ -338,11 +447,18 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
 kpx_status kpx_iterate(kpx_planner* p, int32_t n_iters, kpx_iter_stats* out_last) {
     if (!p) return KPX_E_INVALID;
     if (n_iters < 0) return fail(p, KPX_E_INVALID, "n_iters must be >= 0");
-    for (int32_t it = 0; it < n_iters; ++it) {
-        for (int ph = KPX_PHASE_BEGIN; ph <= KPX_PHASE_END; ++ph) {
-            kpx_status st = run_phase(p, ph, nullptr);
-            if (st != KPX_OK) return st;
-        }
+    if (n_iters > 0) ensure_graphs(p);
+    int32_t it = 0;
+    if (p->graph_state == 1) {
+        cudaError_t e = cudaSuccess;
+        for (; e == cudaSuccess && it + kGraphIterations <= n_iters; it += kGraphIterations)
+            e = cudaGraphLaunch(p->graph_many, p->stream);
+        for (; e == cudaSuccess && it < n_iters; ++it) e = cudaGraphLaunch(p->graph_one, p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+    }
+    for (; it < n_iters; ++it) {
+        cudaError_t e = enqueue_iteration(p->P, p->stream);
+        if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
     }
     if (!out_last) return KPX_OK;
     kpx_device_header h;
@@ -437,6 +553,9 @@ kpx_status kpx_reset(kpx_planner* p) {
 kpx_status kpx_destroy(kpx_planner* p) {
     if (!p) return KPX_OK;
     cudaError_t e = cudaStreamSynchronize(p->stream);
+    if (p->graph_one) cudaGraphExecDestroy(p->graph_one);
+    if (p->graph_many) cudaGraphExecDestroy(p->graph_many);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     delete p;
     return e == cudaSuccess ? KPX_OK : KPX_E_CUDA;
 }
@@ -676,6 +795,7 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     P.n_win_tiles = L.n_win_tiles;
     P.n_prune_tiles = L.n_prune_tiles;
     bind_pointers(&pl);
+    choose_grid(P, obs->aabb, n_obs);
     if (!host_point_valid(P, P.start, obs->aabb, n_obs)) return reject(KPX_E_INVALID, "start state is not in X_valid");
 
     // obstacles: lo and hi corners copied straight from the caller's
@@ -689,6 +809,7 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     }
     // every array that must start at zero is cleared by the first-time init
     if (e == cudaSuccess) e = launch_init(P, true, pl.stream);
+    if (e == cudaSuccess) e = launch_grid_build(P, pl.stream);
     for (int32_t it = 0; e == cudaSuccess && it < n_iters; ++it) {
         e = launch_begin(P, pl.stream);
         if (e == cudaSuccess) e = launch_propagate(P, nullptr, pl.stream);

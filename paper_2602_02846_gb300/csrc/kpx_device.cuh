@@ -73,6 +73,19 @@ struct Dims<KPX_QUAD12> {
     static constexpr int n = 12, m = 4;
 };
 
+// sin and cos through the special-function unit after a two-constant
+// Cody-Waite reduction of the angle to [-pi, pi] (the hardware sine and
+// cosine are accurate to about 4e-7 absolute on that interval).
+__device__ __forceinline__ void fast_sincos(float a, float& s, float& c) {
+    constexpr float INV_TWO_PI = 0.15915494309189535f;
+    constexpr float TWO_PI_HI = 6.28125f;                   // few significant bits: k * TWO_PI_HI is exact
+    constexpr float TWO_PI_LO = 1.9353071795864769e-3f;     // 2 pi - TWO_PI_HI
+    const float k = rintf(a * INV_TWO_PI);
+    float r = fmaf(-k, TWO_PI_HI, a);
+    r = fmaf(-k, TWO_PI_LO, r);
+    __sincosf(r, &s, &c);
+}
+
 template <int DYN>
 __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<DYN>::n],
                                       const float (&u)[Dims<DYN>::m], float (&dx)[Dims<DYN>::n]) {
@@ -86,8 +99,8 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
     } else if constexpr (DYN == KPX_DUBINS6) {
         // (x, y, z)' = v (cos psi cos gamma, sin psi cos gamma, sin gamma); angles and speed follow u
         float sp, cp, sg, cg;
-        sincosf(x[3], &sp, &cp);
-        sincosf(x[4], &sg, &cg);
+        fast_sincos(x[3], sp, cp);
+        fast_sincos(x[4], sg, cg);
         const float vc = x[5] * cg;
         dx[0] = vc * cp;
         dx[1] = vc * sp;
@@ -99,9 +112,9 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
         // p' = v; v' = (T/m) R(phi,theta,psi) e3 - g e3 (R = Rz Ry Rx);
         // (phi,theta,psi)' = W(phi,theta) omega; omega' = J^-1 (tau - omega x J omega)
         float sph, cph, sth, cth, sps, cps;
-        sincosf(x[3], &sph, &cph);
-        sincosf(x[4], &sth, &cth);
-        sincosf(x[5], &sps, &cps);
+        fast_sincos(x[3], sph, cph);
+        fast_sincos(x[4], sth, cth);
+        fast_sincos(x[5], sps, cps);
         const float inv_cth = 1.0f / cth;
         const float tth = sth * inv_cth;
         const float p = x[9], q = x[10], r = x[11];
@@ -172,20 +185,28 @@ __device__ __forceinline__ bool bounds_ok(const DevParams& P, const float (&x)[N
     return ok;
 }
 
-// Tests the point against the boxes in order; returns true on the first box
-// containing it.  `tests` accumulates the number of boxes examined.
-__device__ __forceinline__ bool hits_obstacle(const float4* __restrict__ s_obs, int n_obs, float px, float py,
-                                              float pz, uint32_t& tests) {
-    for (int b = 0; b < n_obs; ++b) {
-        const float4 lo = s_obs[2 * b];
-        const float4 hi = s_obs[2 * b + 1];
+// Obstacle test through the uniform grid: only the boxes listed for the
+// point's cell are tested (the list holds every box overlapping the cell,
+// so the verdict equals testing all boxes).  The point must lie in the
+// workspace box.  `tests` accumulates the number of boxes examined.
+__device__ __forceinline__ bool hits_obstacle(const DevParams& P, float px, float py, float pz, uint32_t& tests) {
+    if (P.n_obs == 0) return false;
+    const int cx = grid_cell(px, P.ws_lo[0], P.grid_inv[0], P.grid_n[0]);
+    const int cy = grid_cell(py, P.ws_lo[1], P.grid_inv[1], P.grid_n[1]);
+    const int cz = grid_cell(pz, P.ws_lo[2], P.grid_inv[2], P.grid_n[2]);
+    const int c = (cz * P.grid_n[1] + cy) * P.grid_n[0] + cx;
+    const int e0 = __ldg(P.cell_start + c);
+    const int e1 = min(__ldg(P.cell_start + c + 1), P.grid_cap);  // the build guarantees <= grid_cap
+    for (int e = e0; e < e1; ++e) {
+        const float4 lo = __ldg(P.cell_box + 2 * e);
+        const float4 hi = __ldg(P.cell_box + 2 * e + 1);
         const bool in = (px >= lo.x) & (px <= hi.x) & (py >= lo.y) & (py <= hi.y) & (pz >= lo.z) & (pz <= hi.z);
         if (in) {
-            tests += (uint32_t)(b + 1);
+            tests += (uint32_t)(e - e0 + 1);
             return true;
         }
     }
-    tests += (uint32_t)n_obs;
+    tests += (uint32_t)(e1 - e0);
     return false;
 }
 
@@ -208,18 +229,71 @@ __device__ __forceinline__ float edge_cost(const DevParams& P, int K, float path
     return dur * fmaf(P.w_effort, e, 1.0f);
 }
 
+// One integrator per (system, scheme).  The generic stepper applies step();
+// the Dubins RK4 stepper uses that yaw, pitch and speed move linearly under a
+// constant control: the two RK4 midpoint stages coincide (k2 = k3) and the
+// end-of-step angles are the next step's start angles, so one step needs two
+// new sine/cosine pairs instead of eight.
+template <int DYN, int INTEG>
+struct Stepper {
+    static constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
+    __device__ __forceinline__ void init(const DevParams&, const float (&)[n], const float (&)[m]) {}
+    __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
+        step<DYN, INTEG>(P, x, u);
+    }
+};
+
+template <>
+struct Stepper<KPX_DUBINS6, KPX_RK4> {
+    static constexpr int n = 6, m = 3;
+    float sp, cp, sg, cg;  // sin/cos of yaw and pitch at the current state
+    __device__ __forceinline__ void init(const DevParams&, const float (&x)[n], const float (&)[m]) {
+        fast_sincos(x[3], sp, cp);
+        fast_sincos(x[4], sg, cg);
+    }
+    __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
+        const float h = P.h;
+        const float hh = 0.5f * h;
+        const float h6 = h * (1.0f / 6.0f);
+        const float vs = x[5];
+        const float ym = fmaf(hh, u[0], x[3]), gm = fmaf(hh, u[1], x[4]), vm = fmaf(hh, u[2], x[5]);
+        const float ye = fmaf(h, u[0], x[3]), ge = fmaf(h, u[1], x[4]), ve = fmaf(h, u[2], x[5]);
+        float spm, cpm, sgm, cgm, spe, cpe, sge, cge;
+        fast_sincos(ym, spm, cpm);
+        fast_sincos(gm, sgm, cgm);
+        fast_sincos(ye, spe, cpe);
+        fast_sincos(ge, sge, cge);
+        // f = v (cos yaw cos pitch, sin yaw cos pitch, sin pitch) at start, mid, end
+        const float as = vs * cg, am = vm * cgm, ae = ve * cge;
+        const float fx = fmaf(4.0f, am * cpm, fmaf(as, cp, ae * cpe));
+        const float fy = fmaf(4.0f, am * spm, fmaf(as, sp, ae * spe));
+        const float fz = fmaf(4.0f, vm * sgm, fmaf(vs, sg, ve * sge));
+        x[0] = fmaf(h6, fx, x[0]);
+        x[1] = fmaf(h6, fy, x[1]);
+        x[2] = fmaf(h6, fz, x[2]);
+        x[3] = ye;
+        x[4] = ge;
+        x[5] = ve;
+        sp = spe;
+        cp = cpe;
+        sg = sge;
+        cg = cge;
+    }
+};
+
 // PropagateODE over K steps.  CHECK = true tests every step's state (the
 // propagate kernel); CHECK = false reproduces the same arithmetic without
 // the checks (the append kernel re-materialises winners that passed them).
 template <int DYN, int INTEG, bool CHECK, bool OBST>
 __device__ __forceinline__ bool rollout(const DevParams& P, float (&x)[Dims<DYN>::n], const float (&u)[Dims<DYN>::m],
-                                        int K, float& path_len, const float4* __restrict__ s_obs, uint32_t& steps,
-                                        uint32_t& tests) {
+                                        int K, float& path_len, uint32_t& steps, uint32_t& tests) {
+    Stepper<DYN, INTEG> st;
+    st.init(P, x, u);
     float len = 0.0f;
     const bool want_len = P.cost_kind == KPX_COST_PATH_LENGTH;
     for (int k = 0; k < K; ++k) {
         const float p0 = x[0], p1 = x[1], p2 = x[2];
-        step<DYN, INTEG>(P, x, u);
+        st.advance(P, x, u);
         ++steps;
         if (want_len) {
             const float dx = x[0] - p0, dy = x[1] - p1, dz = x[2] - p2;
@@ -231,7 +305,7 @@ __device__ __forceinline__ bool rollout(const DevParams& P, float (&x)[Dims<DYN>
                 return false;
             }
             if constexpr (OBST) {
-                if (hits_obstacle(s_obs, P.n_obs, x[0], x[1], x[2], tests)) {
+                if (hits_obstacle(P, x[0], x[1], x[2], tests)) {
                     path_len = len;
                     return false;
                 }
@@ -246,12 +320,14 @@ __device__ __forceinline__ bool rollout(const DevParams& P, float (&x)[Dims<DYN>
 // check; same integration arithmetic as rollout()).
 template <int DYN, int INTEG>
 __device__ __forceinline__ bool obstacle_pass(const DevParams& P, float (&x)[Dims<DYN>::n],
-                                              const float (&u)[Dims<DYN>::m], int K, const float4* __restrict__ s_obs,
-                                              uint32_t& steps, uint32_t& tests) {
+                                              const float (&u)[Dims<DYN>::m], int K, uint32_t& steps,
+                                              uint32_t& tests) {
+    Stepper<DYN, INTEG> st;
+    st.init(P, x, u);
     for (int k = 0; k < K; ++k) {
-        step<DYN, INTEG>(P, x, u);
+        st.advance(P, x, u);
         ++steps;
-        if (hits_obstacle(s_obs, P.n_obs, x[0], x[1], x[2], tests)) return false;
+        if (hits_obstacle(P, x[0], x[1], x[2], tests)) return false;
     }
     return true;
 }

@@ -16,9 +16,11 @@ namespace kpx {
 
 constexpr uint64_t KEY_INF = ~0ull;
 
-// node-set byte: bits 0-1 the set, bit 2 the memoised "a strict ancestor is
-// dominated" flag (monotone: once an ancestor is dominated it stays so).
-enum : uint8_t { SET_A = 1, SET_I = 2, SET_T = 3, SET_MASK = 3, SET_ANC = 4 };
+// node-set byte: bits 0-1 the set; bit 2 the memoised "a strict ancestor is
+// dominated" flag; bit 3 "dominated": the node no longer holds its region's
+// key (set by the append that replaces it as the region's owner).  Both flags
+// are monotone: region keys only decrease.
+enum : uint8_t { SET_A = 1, SET_I = 2, SET_T = 3, SET_MASK = 3, SET_ANC = 4, SET_DOM = 8 };
 
 // work partitioning constants
 constexpr int PROP_THREADS = 256;
@@ -29,6 +31,10 @@ constexpr int PRUNE_THREADS = 256;
 constexpr int PRUNE_PER_THREAD = 4;
 constexpr int PRUNE_TILE = PRUNE_THREADS * PRUNE_PER_THREAD;         // 1024 nodes
 constexpr int TRAJ_STAGE_ROWS = 65536;                               // trajectory gather chunk
+// obstacle broad phase: a uniform grid over the workspace box
+constexpr int GRID_MAX_CELLS = 65536;
+constexpr int GRID_MAX_AXIS = 64;
+inline int64_t grid_entry_budget(int32_t n_obs) { return 32 * (int64_t)n_obs + 4096; }
 
 // Parameter block passed by value to every kernel.
 struct DevParams {
@@ -57,6 +63,11 @@ struct DevParams {
     int32_t pad0;
     int64_t slot_cap, mask_words;
     int32_t n_win_tiles, n_prune_tiles;
+    // obstacle grid: cell(c, axis a) = clamp(floor((c - ws_lo[a]) * grid_inv[a]), 0, grid_n[a] - 1)
+    int32_t grid_n[3];
+    float grid_inv[3];
+    int32_t n_cells;
+    int32_t grid_cap;     // entries reserved in cell_box
     // device arrays (inside the caller's workspace)
     kpx_device_header* hdr;
     float* x;
@@ -69,6 +80,7 @@ struct DevParams {
     uint8_t* icount;
     uint64_t* region_key;
     uint64_t* region_snap;
+    int32_t* region_owner;  // [R]: tree id holding the region's key, -1 if none
     int32_t* va0;
     int32_t* va1;
     int32_t* win_slot;
@@ -76,14 +88,32 @@ struct DevParams {
     uint64_t* win_tiles;
     uint64_t* prune_tiles;
     float4* obs;          // [2*n_obs]: lo (x,y,z,0), hi (x,y,z,0)
+    int32_t* box_cells;   // [6*n_obs]: per box cell range lo x,y,z, hi x,y,z
+    int32_t* cell_start;  // [n_cells + 1]: CSR offsets into cell_box
+    float4* cell_box;     // [2*grid_cap]: boxes of each cell, in box order
     int32_t* path;        // [N] node ids root -> goal
     float* traj;          // staging: states [(TRAJ_STAGE_ROWS+1) n], controls [TRAJ_STAGE_ROWS m], steps
 };
 
+// FP32 cell index along one axis, identical on host and device (one
+// rounding per operation, no contraction).  Monotone in c, so a box that
+// contains a point always lists the point's cell.
+__host__ __device__ inline int grid_cell(float c, float lo, float inv, int n) {
+#ifdef __CUDA_ARCH__
+    const float t = __fmul_rn(__fsub_rn(c, lo), inv);
+#else
+    volatile float d = c - lo;
+    const float t = d * inv;
+#endif
+    int i = (int)floorf(t);
+    i = i < 0 ? 0 : i;
+    return i > n - 1 ? n - 1 : i;
+}
+
 // Workspace layout (byte offsets from the workspace base).
 struct Layout {
-    size_t hdr, obs, x, u, K, parent, key, region, set, icount;
-    size_t region_key, region_snap, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, path, traj;
+    size_t hdr, obs, box_cells, cell_start, cell_box, x, u, K, parent, key, region, set, icount;
+    size_t region_key, region_snap, region_owner, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, path, traj;
     size_t total;
     int32_t va_cap;
     int64_t slot_cap, mask_words;
@@ -93,6 +123,7 @@ struct Layout {
 
 // launchers (kpx_kernels.cu); each returns the launch status
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s);
+cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s);
 cudaError_t launch_begin(const DevParams& P, cudaStream_t s);
 cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s);
 cudaError_t launch_mark(const DevParams& P, cudaStream_t s);
@@ -102,5 +133,7 @@ cudaError_t launch_prune(const DevParams& P, cudaStream_t s);
 cudaError_t launch_end(const DevParams& P, cudaStream_t s);
 cudaError_t launch_path(const DevParams& P, cudaStream_t s);
 cudaError_t launch_gather(const DevParams& P, int32_t first_row, int32_t rows, cudaStream_t s);
+// computes the cached launch shapes (SM count, occupancy) outside any capture
+void prepare_launches(const DevParams& P);
 
 }  // namespace kpx

@@ -19,6 +19,17 @@
 
 namespace kpx {
 
+#define KPX_DISPATCH(FN, P, ...)                                                         \
+    switch ((P).dyn * 2 + (P).integ) {                                                  \
+        case KPX_DI6 * 2 + KPX_EULER: return FN<KPX_DI6, KPX_EULER>(P, __VA_ARGS__);         \
+        case KPX_DI6 * 2 + KPX_RK4: return FN<KPX_DI6, KPX_RK4>(P, __VA_ARGS__);             \
+        case KPX_DUBINS6 * 2 + KPX_EULER: return FN<KPX_DUBINS6, KPX_EULER>(P, __VA_ARGS__); \
+        case KPX_DUBINS6 * 2 + KPX_RK4: return FN<KPX_DUBINS6, KPX_RK4>(P, __VA_ARGS__);     \
+        case KPX_QUAD12 * 2 + KPX_EULER: return FN<KPX_QUAD12, KPX_EULER>(P, __VA_ARGS__);   \
+        case KPX_QUAD12 * 2 + KPX_RK4: return FN<KPX_QUAD12, KPX_RK4>(P, __VA_ARGS__);       \
+        default: return cudaErrorInvalidValue;                                          \
+    }
+
 namespace {
 
 constexpr uint32_t FULL = 0xFFFFFFFFu;
@@ -108,7 +119,10 @@ __global__ void k_init(DevParams P, int first_time) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const uint64_t root_key = pack_key(0.0f, 0u);
-    for (int64_t r = tid; r < P.R; r += stride) P.region_key[r] = (r == root_region) ? root_key : KEY_INF;
+    for (int64_t r = tid; r < P.R; r += stride) {
+        P.region_key[r] = (r == root_region) ? root_key : KEY_INF;
+        P.region_owner[r] = (r == root_region) ? 0 : -1;
+    }
     for (int64_t w = tid; w < P.mask_words; w += stride) P.win_mask[w] = 0u;
     if (first_time) {
         for (int64_t t = tid; t < P.n_win_tiles; t += stride) P.win_tiles[t] = 0ull;
@@ -138,6 +152,79 @@ __global__ void k_init(DevParams P, int first_time) {
         P.set[0] = SET_A;
         P.icount[0] = 0;
         P.va0[0] = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// obstacle grid (broad phase), built once per create: per-box cell ranges,
+// per-cell counts (one warp per cell, boxes in index order), a scan into CSR
+// offsets, then the fill.  Deterministic: each cell lists its boxes in
+// ascending box index.
+// ---------------------------------------------------------------------------
+__global__ void k_box_cells(DevParams P) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= P.n_obs) return;
+    const float4 lo = P.obs[2 * b], hi = P.obs[2 * b + 1];
+    const float l[3] = {lo.x, lo.y, lo.z}, h[3] = {hi.x, hi.y, hi.z};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        P.box_cells[6 * b + a] = grid_cell(l[a], P.ws_lo[a], P.grid_inv[a], P.grid_n[a]);
+        P.box_cells[6 * b + 3 + a] = grid_cell(h[a], P.ws_lo[a], P.grid_inv[a], P.grid_n[a]);
+    }
+}
+
+__device__ __forceinline__ bool box_overlaps_cell(const DevParams& P, int b, int cx, int cy, int cz) {
+    const int* bc = P.box_cells + 6 * b;
+    return cx >= bc[0] && cx <= bc[3] && cy >= bc[1] && cy <= bc[4] && cz >= bc[2] && cz <= bc[5];
+}
+
+template <bool FILL>
+__global__ void k_grid_cells(DevParams P) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < P.n_cells; c += warps) {
+        const int cx = c % P.grid_n[0];
+        const int cy = (c / P.grid_n[0]) % P.grid_n[1];
+        const int cz = c / (P.grid_n[0] * P.grid_n[1]);
+        int count = 0;
+        const int start = FILL ? P.cell_start[c] : 0;
+        for (int base = 0; base < P.n_obs; base += 32) {
+            const int b = base + lane;
+            const bool in = b < P.n_obs && box_overlaps_cell(P, b, cx, cy, cz);
+            const uint32_t bal = __ballot_sync(FULL, in);
+            if (FILL && in) {
+                const int pos = start + count + __popc(bal & ((1u << lane) - 1u));
+                if (pos < P.grid_cap) {
+                    P.cell_box[2 * pos] = P.obs[2 * b];
+                    P.cell_box[2 * pos + 1] = P.obs[2 * b + 1];
+                }
+            }
+            count += __popc(bal);
+        }
+        if (!FILL && lane == 0) P.cell_start[c + 1] = count;
+    }
+    if (!FILL && blockIdx.x == 0 && threadIdx.x == 0) P.cell_start[0] = 0;
+}
+
+// in-place inclusive scan of cell_start[1..n_cells] (one block)
+__global__ void __launch_bounds__(1024) k_grid_scan(DevParams P) {
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_carry;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < P.n_cells; base += 1024) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < P.n_cells ? (uint32_t)P.cell_start[i + 1] : 0u;
+        uint32_t agg;
+        const uint32_t excl = block_exclusive_scan<1024>(v, agg, s_warp);
+        if (i < P.n_cells) P.cell_start[i + 1] = (int32_t)(s_carry + excl + v);
+        __syncthreads();
+        if (threadIdx.x == 0) s_carry += agg;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && (int64_t)s_carry > (int64_t)P.grid_cap) {
+        set_status(P.hdr, KPX_E_INTERNAL);
+        P.hdr->err_info[2] = s_carry;
     }
 }
 
@@ -185,10 +272,7 @@ __global__ void k_begin(DevParams P) {
 template <int DYN, int INTEG>
 __global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_debug_records rec, int rec_on) {
     constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
-    extern __shared__ float4 s_obs[];
     kpx_device_header* H = P.hdr;
-    for (int i = threadIdx.x; i < 2 * P.n_obs; i += blockDim.x) s_obs[i] = P.obs[i];
-    __syncthreads();
     if (!H->active) return;
     const int64_t n_slots = H->n_slots;
     const int lam = H->lambda;
@@ -198,12 +282,15 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_deb
     const int lane = threadIdx.x & 31;
     const uint32_t cand_base = (uint32_t)P.N;
     uint32_t steps = 0, tests = 0;
+    // warp w first takes chunk w (no atomic); later chunks come from the
+    // ticket, offset by the number of warps in the grid
+    const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    // warp-major: consecutive chunks land on different blocks (SMs)
+    int64_t chunk = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     for (;;) {
-        unsigned long long base = 0ull;
-        if (lane == 0) base = atomicAdd((unsigned long long*)&H->prop_ticket, 32ull);
-        base = __shfl_sync(FULL, base, 0);
-        if ((int64_t)base >= n_slots) break;
-        const int64_t slot = (int64_t)base + lane;
+        const int64_t base = chunk * 32;
+        if (base >= n_slots) break;
+        const int64_t slot = base + lane;
         bool valid = false;
         if (slot < n_slots) {
             const int j = (int)(slot / lam);
@@ -222,17 +309,17 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_deb
                 float x0[n];
 #pragma unroll
                 for (int d = 0; d < n; ++d) x0[d] = x[d];
-                bool ok = rollout<DYN, INTEG, true, false>(P, x, u, K, len, s_obs, steps, tests);
+                bool ok = rollout<DYN, INTEG, true, false>(P, x, u, K, len, steps, tests);
                 if (ok) {
                     const float c = cost0 + edge_cost<m>(P, K, len, u);
                     r = region_of<n>(P, x);
                     key = pack_key(c, cand_base + (uint32_t)slot);
                     ok = key < __ldcg(&P.region_key[r]);
-                    if (ok) ok = obstacle_pass<DYN, INTEG>(P, x0, u, K, s_obs, steps, tests);
+                    if (ok) ok = obstacle_pass<DYN, INTEG>(P, x0, u, K, steps, tests);
                 }
                 valid = ok;
             } else {
-                valid = rollout<DYN, INTEG, true, true>(P, x, u, K, len, s_obs, steps, tests);
+                valid = rollout<DYN, INTEG, true, true>(P, x, u, K, len, steps, tests);
                 if (valid) {
                     const float c = cost0 + edge_cost<m>(P, K, len, u);
                     r = region_of<n>(P, x);
@@ -254,6 +341,9 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_deb
         }
         const uint32_t vb = __ballot_sync(FULL, valid);
         if (lane == 0 && vb) atomicAdd((unsigned long long*)&H->last_valid, (unsigned long long)__popc(vb));
+        unsigned long long t = 0ull;
+        if (lane == 0) t = atomicAdd((unsigned long long*)&H->prop_ticket, 1ull);
+        chunk = n_warps + (int64_t)__shfl_sync(FULL, t, 0);
     }
     // work counters (one atomic per warp per launch)
     unsigned long long st = steps, te = tests;
@@ -275,18 +365,18 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_deb
 __global__ void k_mark(DevParams P) {
     const kpx_device_header* H = P.hdr;
     if (!H->active) return;
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= P.R) return;
-    const uint64_t k = P.region_key[r];
-    if (k == KEY_INF) return;
-    const uint32_t id = (uint32_t)k;
-    if (id < (uint32_t)P.N) return;
-    const uint32_t slot = id - (uint32_t)P.N;
-    if ((int64_t)slot >= P.slot_cap) {  // a stale candidate id: cannot happen in a consistent state
-        set_status(P.hdr, KPX_E_INTERNAL);
-        return;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x) {
+        const uint64_t k = P.region_key[r];
+        if (k == KEY_INF) continue;
+        const uint32_t id = (uint32_t)k;
+        if (id < (uint32_t)P.N) continue;
+        const uint32_t slot = id - (uint32_t)P.N;
+        if ((int64_t)slot >= P.slot_cap) {  // a stale candidate id: cannot happen in a consistent state
+            set_status(P.hdr, KPX_E_INTERNAL);
+            continue;
+        }
+        atomicOr(&P.win_mask[slot >> 5], 1u << (slot & 31));
     }
-    atomicOr(&P.win_mask[slot >> 5], 1u << (slot & 31));
 }
 
 // ---------------------------------------------------------------------------
@@ -298,41 +388,45 @@ __global__ void __launch_bounds__(WIN_THREADS) k_scan(DevParams P) {
     __shared__ uint32_t s_warp[WIN_THREADS / 32];
     kpx_device_header* H = P.hdr;
     if (!H->active) return;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&H->win_ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
     const int64_t live_words = (H->n_slots + 31) / 32;
     const int64_t n_tiles = (live_words + WIN_TILE_WORDS - 1) / WIN_TILE_WORDS;
-    if ((int64_t)tile >= n_tiles) return;
-    const int64_t w0 = (int64_t)tile * WIN_TILE_WORDS + (int64_t)threadIdx.x * WIN_WORDS_PER_THREAD;
-    uint32_t w[WIN_WORDS_PER_THREAD];
-    uint32_t cnt = 0;
+    if ((int64_t)blockIdx.x >= n_tiles) return;  // the other blocks take every tile
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&H->win_ticket, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if ((int64_t)tile >= n_tiles) return;
+        const int64_t w0 = (int64_t)tile * WIN_TILE_WORDS + (int64_t)threadIdx.x * WIN_WORDS_PER_THREAD;
+        uint32_t w[WIN_WORDS_PER_THREAD];
+        uint32_t cnt = 0;
 #pragma unroll
-    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
-        w[i] = (w0 + i < live_words) ? P.win_mask[w0 + i] : 0u;
-        cnt += __popc(w[i]);
-    }
-    uint32_t agg;
-    const uint32_t excl = block_exclusive_scan<WIN_THREADS>(cnt, agg, s_warp);
-    if (threadIdx.x == 0) {
-        s_prefix = lookback(P.win_tiles, tile, agg, (uint32_t)H->epoch, H);
-        if ((int64_t)tile == n_tiles - 1) H->n_win = (int32_t)(s_prefix + agg);
-    }
-    __syncthreads();
-    uint32_t rank = s_prefix + excl;
-#pragma unroll
-    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
-        uint32_t word = w[i];
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            if (rank < (uint32_t)P.R)
-                P.win_slot[rank] = (int32_t)((w0 + i) * 32 + b);
-            else
-                set_status(H, KPX_E_INTERNAL);
-            ++rank;
+        for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
+            w[i] = (w0 + i < live_words) ? P.win_mask[w0 + i] : 0u;
+            cnt += __popc(w[i]);
         }
-        if (w[i]) P.win_mask[w0 + i] = 0u;
+        uint32_t agg;
+        const uint32_t excl = block_exclusive_scan<WIN_THREADS>(cnt, agg, s_warp);
+        if (threadIdx.x == 0) {
+            s_prefix = lookback(P.win_tiles, tile, agg, (uint32_t)H->epoch, H);
+            if ((int64_t)tile == n_tiles - 1) H->n_win = (int32_t)(s_prefix + agg);
+        }
+        __syncthreads();
+        uint32_t rank = s_prefix + excl;
+#pragma unroll
+        for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
+            uint32_t word = w[i];
+            while (word) {
+                const int b = __ffs(word) - 1;
+                word &= word - 1;
+                if (rank < (uint32_t)P.R)
+                    P.win_slot[rank] = (int32_t)((w0 + i) * 32 + b);
+                else
+                    set_status(H, KPX_E_INTERNAL);
+                ++rank;
+            }
+            if (w[i]) P.win_mask[w0 + i] = 0u;
+        }
     }
 }
 
@@ -372,7 +466,7 @@ __global__ void __launch_bounds__(128) k_append(DevParams P) {
         sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
         float len;
         uint32_t st_unused = 0, te_unused = 0;
-        rollout<DYN, INTEG, false, false>(P, x, u, K, len, nullptr, st_unused, te_unused);
+        rollout<DYN, INTEG, false, false>(P, x, u, K, len, st_unused, te_unused);
         const float c = cost0 + edge_cost<m>(P, K, len, u);
         const int r = region_of<n>(P, x);
         const uint64_t cand_key = pack_key(c, (uint32_t)P.N + (uint32_t)slot);
@@ -395,6 +489,11 @@ __global__ void __launch_bounds__(128) k_append(DevParams P) {
             P.set[id] = SET_A;
             P.icount[id] = 0;
             P.region_key[r] = k;
+            // the previous owner of r loses its region (one winner per region,
+            // so this thread is the only writer of that node's set byte)
+            const int old = P.region_owner[r];
+            if (old >= 0) P.set[old] = (uint8_t)(P.set[old] | SET_DOM);
+            P.region_owner[r] = id;
             if (in_goal(P, x[0], x[1], x[2])) atomicMin((unsigned long long*)&H->goal_key, (unsigned long long)k);
         } else {
             P.region_key[r] = P.region_snap[r];
@@ -411,104 +510,121 @@ __global__ void __launch_bounds__(128) k_append(DevParams P) {
 __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ uint32_t s_warp[PRUNE_THREADS / 32];
+    // the tile's parent ids and set bytes: ancestor walks that stay inside
+    // the tile read shared memory (parents precede children)
+    __shared__ int32_t s_parent[PRUNE_TILE];
+    __shared__ uint8_t s_set[PRUNE_TILE];
     kpx_device_header* H = P.hdr;
     if (!H->active) return;
-    if (threadIdx.x == 0) s_tile = atomicAdd(&H->prune_ticket, 1u);
-    __syncthreads();
-    const uint32_t tile = s_tile;
     const int n_old = H->n_nodes;
     const int total = n_old + H->n_kept;
     const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
-    if ((int)tile >= n_tiles) return;
-    const uint64_t* __restrict__ rk = P.region_key;
-    const int i_max = P.i_max;
-    const int base = (int)tile * PRUNE_TILE + threadIdx.x * PRUNE_PER_THREAD;
-    uint32_t amask = 0;
+    if ((int)blockIdx.x >= n_tiles) return;  // the other blocks take every tile
     int cA = 0, cI = 0, cT = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&H->prune_ticket, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        __syncthreads();
+        if ((int)tile >= n_tiles) break;
+        const int i_max = P.i_max;
+        const int tile0 = (int)tile * PRUNE_TILE;
+        for (int k = threadIdx.x; k < PRUNE_TILE; k += PRUNE_THREADS) {
+            const int i = tile0 + k;
+            s_parent[k] = i < n_old ? P.parent[i] : -1;
+            s_set[k] = i < n_old ? P.set[i] : 0;
+        }
+        __syncthreads();
+        const int base = tile0 + threadIdx.x * PRUNE_PER_THREAD;
+        uint32_t amask = 0;
 #pragma unroll
-    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
-        const int i = base + q;
-        if (i >= total) break;
-        if (i >= n_old) {  // appended this iteration: in V_A
-            amask |= 1u << q;
-            ++cA;
-            continue;
-        }
-        const uint8_t sb = P.set[i];
-        const int st = sb & SET_MASK;
-        if (st == SET_T) {  // V_T is permanent
-            ++cT;
-            continue;
-        }
-        const uint64_t k = P.key[i];
-        const uint64_t rkv = rk[P.region[i]];
-        const bool best = k == rkv;
-        int ic = P.icount[i];
-        const int ic0 = ic;
-        int nst = st;
-        bool anc = (sb & SET_ANC) != 0;
-        bool done = false;
-        if (best && st == SET_I) {  // rule 1: region best while inactive
-            ++ic;
-            if (ic > i_max) {
-                nst = SET_A;
-                done = true;
+        for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+            const int i = base + q;
+            if (i >= total) break;
+            if (i >= n_old) {  // appended this iteration: in V_A
+                amask |= 1u << q;
+                ++cA;
+                continue;
             }
-        }
-        if (!done && ic > i_max && best) done = true;  // rule 2
-        if (!done && k > rkv) {                         // rule 3: dominated
-            nst = SET_T;
-            done = true;
-        }
-        if (!done) {  // rule 4: any strict ancestor dominated
-            if (!anc) {
-                int p = P.parent[i];
-                while (p >= 0) {
-                    const uint8_t sp = *(volatile const uint8_t*)&P.set[p];
-                    if ((sp & SET_MASK) == SET_T || (sp & SET_ANC)) {
-                        anc = true;
-                        break;
-                    }
-                    if (P.key[p] != rk[P.region[p]]) {
-                        anc = true;
-                        break;
-                    }
-                    p = P.parent[p];
+            const uint8_t sb = P.set[i];
+            const int st = sb & SET_MASK;
+            if (st == SET_T) {  // V_T is permanent
+                ++cT;
+                continue;
+            }
+            // key(i) >= key(region(i)) always, with equality only for the
+            // region's owner: "best" is "not dominated"
+            const bool dominated = (sb & SET_DOM) != 0;
+            const bool best = !dominated;
+            int ic = P.icount[i];
+            const int ic0 = ic;
+            int nst = st;
+            bool anc = (sb & SET_ANC) != 0;
+            bool done = false;
+            if (best && st == SET_I) {  // rule 1: region best while inactive
+                ++ic;
+                if (ic > i_max) {
+                    nst = SET_A;
+                    done = true;
                 }
             }
-            if (anc) nst = SET_I;
+            if (!done && ic > i_max && best) done = true;  // rule 2
+            if (!done && dominated) {                       // rule 3: dominated
+                nst = SET_T;
+                done = true;
+            }
+            if (!done) {  // rule 4: any strict ancestor dominated
+                if (!anc) {
+                    int p = s_parent[i - tile0];
+                    while (p >= tile0) {  // inside the tile: shared memory (a stale
+                        // set byte only lacks a monotone flag, which the walk re-derives)
+                        const uint8_t sp = s_set[p - tile0];
+                        if (sp & (SET_DOM | SET_ANC)) {
+                            anc = true;
+                            break;
+                        }
+                        p = s_parent[p - tile0];
+                    }
+                    for (; !anc && p >= 0; p = P.parent[p]) {
+                        const uint8_t sp = *(volatile const uint8_t*)&P.set[p];
+                        if (sp & (SET_DOM | SET_ANC)) anc = true;
+                    }
+                }
+                if (anc) nst = SET_I;
+            }
+            const uint8_t nb = (uint8_t)(nst | (anc ? SET_ANC : 0) | (sb & SET_DOM));
+            if (nb != sb) P.set[i] = nb;
+            if (ic != ic0) P.icount[i] = (uint8_t)ic;
+            if (nst == SET_A) {
+                amask |= 1u << q;
+                ++cA;
+            } else if (nst == SET_I) {
+                ++cI;
+            } else {
+                ++cT;
+            }
         }
-        const uint8_t nb = (uint8_t)(nst | (anc ? SET_ANC : 0));
-        if (nb != sb) P.set[i] = nb;
-        if (ic != ic0) P.icount[i] = (uint8_t)ic;
-        if (nst == SET_A) {
-            amask |= 1u << q;
-            ++cA;
-        } else if (nst == SET_I) {
-            ++cI;
-        } else {
-            ++cT;
+        uint32_t agg;
+        const uint32_t excl = block_exclusive_scan<PRUNE_THREADS>((uint32_t)__popc(amask), agg, s_warp);
+        if (threadIdx.x == 0) {
+            s_prefix = lookback(P.prune_tiles, tile, agg, (uint32_t)H->epoch, H);
+            if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
         }
-    }
-    uint32_t agg;
-    const uint32_t excl = block_exclusive_scan<PRUNE_THREADS>((uint32_t)__popc(amask), agg, s_warp);
-    if (threadIdx.x == 0) {
-        s_prefix = lookback(P.prune_tiles, tile, agg, (uint32_t)H->epoch, H);
-        if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
-    }
-    __syncthreads();
-    int32_t* va_next = H->va_sel ? P.va0 : P.va1;
-    uint32_t pos = s_prefix + excl;
+        __syncthreads();
+        int32_t* va_next = H->va_sel ? P.va0 : P.va1;
+        uint32_t pos = s_prefix + excl;
 #pragma unroll
-    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
-        if (amask & (1u << q)) {
-            // at most one active node per region, so pos < min(N, R) = va_cap
-            if (pos < (uint32_t)P.va_cap)
-                va_next[pos] = base + q;
-            else
-                set_status(H, KPX_E_INTERNAL);
-            ++pos;
+        for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+            if (amask & (1u << q)) {
+                // at most one active node per region, so pos < min(N, R) = va_cap
+                if (pos < (uint32_t)P.va_cap)
+                    va_next[pos] = base + q;
+                else
+                    set_status(H, KPX_E_INTERNAL);
+                ++pos;
+            }
         }
+        __syncthreads();
     }
     // set sizes for the statistics
 #pragma unroll
@@ -579,54 +695,65 @@ __global__ void k_gather(DevParams P, int first, int rows) {
     row[P.n + P.m] = __int_as_float((int)P.K[node]);
 }
 
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) dev = 0;
+    if (!cached[dev]) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = sms > 0 ? sms : 1;
+    }
+    return cached[dev];
+}
+
+// a persistent grid: enough resident blocks to fill the GPU, never more than the work
+int persistent_blocks(int64_t work_blocks, int per_sm) {
+    int64_t g = (int64_t)sm_count() * per_sm;
+    if (g > work_blocks) g = work_blocks;
+    return (int)(g < 1 ? 1 : g);
+}
+
+template <int DYN, int INTEG>
+int propagate_blocks_per_sm() {
+    static int per_sm = 0;
+    if (!per_sm) {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_propagate<DYN, INTEG>, PROP_THREADS, 0);
+        per_sm = v < 1 ? 1 : v;
+    }
+    return per_sm;
+}
+
+template <int DYN, int INTEG>
+int propagate_occupancy_t(const DevParams&, int) {
+    return propagate_blocks_per_sm<DYN, INTEG>();
+}
+
+int propagate_occupancy(const DevParams& P) { KPX_DISPATCH(propagate_occupancy_t, P, 0); }
+
 template <int DYN, int INTEG>
 cudaError_t launch_propagate_t(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = (size_t)P.n_obs * 2 * sizeof(float4);
-    static bool attr_done[3][2] = {};
-    if (!attr_done[DYN][INTEG]) {
-        cudaFuncSetAttribute(k_propagate<DYN, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_done[DYN][INTEG] = true;
-    }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_propagate<DYN, INTEG>, PROP_THREADS, smem);
-    if (per_sm < 1) per_sm = 1;
-    const int64_t need = (P.slot_cap + PROP_THREADS - 1) / PROP_THREADS;
-    int64_t grid = (int64_t)sms * per_sm;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
+    const int per_sm = propagate_blocks_per_sm<DYN, INTEG>();
+    const int grid = persistent_blocks((P.slot_cap + PROP_THREADS - 1) / PROP_THREADS, per_sm);
     kpx_debug_records r{};
     int on = 0;
     if (rec && rec->valid) {
         r = *rec;
         on = 1;
     }
-    k_propagate<DYN, INTEG><<<(unsigned)grid, PROP_THREADS, smem, s>>>(P, r, on);
+    k_propagate<DYN, INTEG><<<grid, PROP_THREADS, 0, s>>>(P, r, on);
     return cudaGetLastError();
 }
 
 template <int DYN, int INTEG>
 cudaError_t launch_append_t(const DevParams& P, cudaStream_t s) {
-    int blocks = (P.R + 127) / 128;
-    if (blocks > 4096) blocks = 4096;
-    k_append<DYN, INTEG><<<blocks, 128, 0, s>>>(P);
+    k_append<DYN, INTEG><<<persistent_blocks((P.R + 127) / 128, 4), 128, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 }  // namespace
-
-#define KPX_DISPATCH(FN, P, ...)                                                         \
-    switch ((P).dyn * 2 + (P).integ) {                                                  \
-        case KPX_DI6 * 2 + KPX_EULER: return FN<KPX_DI6, KPX_EULER>(P, __VA_ARGS__);         \
-        case KPX_DI6 * 2 + KPX_RK4: return FN<KPX_DI6, KPX_RK4>(P, __VA_ARGS__);             \
-        case KPX_DUBINS6 * 2 + KPX_EULER: return FN<KPX_DUBINS6, KPX_EULER>(P, __VA_ARGS__); \
-        case KPX_DUBINS6 * 2 + KPX_RK4: return FN<KPX_DUBINS6, KPX_RK4>(P, __VA_ARGS__);     \
-        case KPX_QUAD12 * 2 + KPX_EULER: return FN<KPX_QUAD12, KPX_EULER>(P, __VA_ARGS__);   \
-        case KPX_QUAD12 * 2 + KPX_RK4: return FN<KPX_QUAD12, KPX_RK4>(P, __VA_ARGS__);       \
-        default: return cudaErrorInvalidValue;                                          \
-    }
 
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s) {
     int64_t work = P.R > P.mask_words ? P.R : P.mask_words;
@@ -640,10 +767,18 @@ cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s) {
+    if (P.n_obs == 0) return cudaSuccess;
+    k_box_cells<<<(P.n_obs + 127) / 128, 128, 0, s>>>(P);
+    const int cell_blocks = persistent_blocks((P.n_cells + 7) / 8, 8);
+    k_grid_cells<false><<<cell_blocks, 256, 0, s>>>(P);
+    k_grid_scan<<<1, 1024, 0, s>>>(P);
+    k_grid_cells<true><<<cell_blocks, 256, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_begin(const DevParams& P, cudaStream_t s) {
-    int blocks = (P.R + 255) / 256;
-    if (blocks > 1024) blocks = 1024;
-    k_begin<<<blocks, 256, 0, s>>>(P);
+    k_begin<<<persistent_blocks((P.R + 255) / 256, 2), 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -652,19 +787,19 @@ cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, c
 }
 
 cudaError_t launch_mark(const DevParams& P, cudaStream_t s) {
-    k_mark<<<(P.R + 255) / 256, 256, 0, s>>>(P);
+    k_mark<<<persistent_blocks((P.R + 255) / 256, 4), 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const DevParams& P, cudaStream_t s) {
-    k_scan<<<P.n_win_tiles, WIN_THREADS, 0, s>>>(P);
+    k_scan<<<persistent_blocks(P.n_win_tiles, 2), WIN_THREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 
 cudaError_t launch_append(const DevParams& P, cudaStream_t s) { KPX_DISPATCH(launch_append_t, P, s); }
 
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
-    k_prune<<<P.n_prune_tiles, PRUNE_THREADS, 0, s>>>(P);
+    k_prune<<<persistent_blocks(P.n_prune_tiles, 4), PRUNE_THREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 
@@ -676,6 +811,11 @@ cudaError_t launch_end(const DevParams& P, cudaStream_t s) {
 cudaError_t launch_path(const DevParams& P, cudaStream_t s) {
     k_path<<<1, 1, 0, s>>>(P);
     return cudaGetLastError();
+}
+
+void prepare_launches(const DevParams& P) {
+    (void)sm_count();
+    propagate_occupancy(P);
 }
 
 cudaError_t launch_gather(const DevParams& P, int32_t first_row, int32_t rows, cudaStream_t s) {

@@ -144,6 +144,10 @@ def step_phases(pl, prob, check_append=True):
     pl.debug_step("end")
     fin = pl.arrays()
     expect_va = np.nonzero(fin["set"] == A)[0].astype(np.int32)
+    # the memoised "dominated" bit equals key(i) != key(region(i)) on every node
+    dom_bit = (fin["set_raw"] & 8) != 0
+    dom_key = fin["key"] != fin["region_key"][fin["region"]]
+    assert np.array_equal(dom_bit, dom_key), "dominated bit out of step with the region keys"
     assert fin["n_nodes"] == n0 + kept
     assert np.array_equal(fin["VA"], expect_va), "next V_A differs from the ascending active ids"
     assert fin["iter"] == it + 1
