@@ -71,6 +71,8 @@ std::string check_config(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t
         if (ax.state_dim < 0 || ax.state_dim >= n) return "region axis state_dim out of range";
         if (ax.bins < 1 || ax.bins > (1 << 20)) return "region axis bins out of range";
         if (!finite(ax.lo) || !finite(ax.hi) || !(ax.hi > ax.lo)) return "region axis needs finite lo < hi";
+        for (int b = 0; b < a; ++b)
+            if (cfg->axis[b].state_dim == ax.state_dim) return "a state component may appear in one region axis only";
         R *= ax.bins;
         if (R > (1 << 28)) return "too many regions (> 2^28)";
     }
@@ -403,6 +405,7 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
     }
     int64_t R = 1;
     for (int a = 0; a < cfg->n_axes; ++a) R *= cfg->axis[a].bins;
+    fill_region_by_component(P);
     P.N = cfg->tree_cap;
     P.R = (int32_t)R;
     P.lambda_fixed = cfg->samples_per_node;
@@ -781,6 +784,7 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
         P.ax_scale[a] = (float)ax.bins / width;
         R *= ax.bins;
     }
+    fill_region_by_component(P);
     P.N = cfg->tree_cap;
     P.R = (int32_t)R;
     P.lambda_fixed = cfg->samples_per_node;

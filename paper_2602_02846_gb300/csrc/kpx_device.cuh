@@ -150,23 +150,30 @@ __device__ __forceinline__ void step(const DevParams& P, float (&x)[Dims<DYN>::n
 #pragma unroll
         for (int i = 0; i < n; ++i) x[i] = fmaf(h, k1[i], x[i]);
     } else {
+        // one accumulator: acc = k1 + 2 k2 + 2 k3 + k4, stages evaluated into k
         const float hh = 0.5f * h;
         const float h6 = h * (1.0f / 6.0f);
-        float xt[n], k2[n], k3[n], k4[n];
-#pragma unroll
-        for (int i = 0; i < n; ++i) xt[i] = fmaf(hh, k1[i], x[i]);
-        deriv<DYN>(P, xt, u, k2);
-#pragma unroll
-        for (int i = 0; i < n; ++i) xt[i] = fmaf(hh, k2[i], x[i]);
-        deriv<DYN>(P, xt, u, k3);
-#pragma unroll
-        for (int i = 0; i < n; ++i) xt[i] = fmaf(h, k3[i], x[i]);
-        deriv<DYN>(P, xt, u, k4);
+        float xt[n], acc[n];
 #pragma unroll
         for (int i = 0; i < n; ++i) {
-            const float s = fmaf(2.0f, k2[i] + k3[i], k1[i] + k4[i]);
-            x[i] = fmaf(h6, s, x[i]);
+            acc[i] = k1[i];
+            xt[i] = fmaf(hh, k1[i], x[i]);
         }
+        deriv<DYN>(P, xt, u, k1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            acc[i] = fmaf(2.0f, k1[i], acc[i]);
+            xt[i] = fmaf(hh, k1[i], x[i]);
+        }
+        deriv<DYN>(P, xt, u, k1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            acc[i] = fmaf(2.0f, k1[i], acc[i]);
+            xt[i] = fmaf(h, k1[i], x[i]);
+        }
+        deriv<DYN>(P, xt, u, k1);
+#pragma unroll
+        for (int i = 0; i < n; ++i) x[i] = fmaf(h6, acc[i] + k1[i], x[i]);
     }
 }
 
@@ -281,41 +288,6 @@ struct Stepper<KPX_DUBINS6, KPX_RK4> {
     }
 };
 
-// PropagateODE over K steps.  CHECK = true tests every step's state (the
-// propagate kernel); CHECK = false reproduces the same arithmetic without
-// the checks (the append kernel re-materialises winners that passed them).
-template <int DYN, int INTEG, bool CHECK, bool OBST>
-__device__ __forceinline__ bool rollout(const DevParams& P, float (&x)[Dims<DYN>::n], const float (&u)[Dims<DYN>::m],
-                                        int K, float& path_len, uint32_t& steps, uint32_t& tests) {
-    Stepper<DYN, INTEG> st;
-    st.init(P, x, u);
-    float len = 0.0f;
-    const bool want_len = P.cost_kind == KPX_COST_PATH_LENGTH;
-    for (int k = 0; k < K; ++k) {
-        const float p0 = x[0], p1 = x[1], p2 = x[2];
-        st.advance(P, x, u);
-        ++steps;
-        if (want_len) {
-            const float dx = x[0] - p0, dy = x[1] - p1, dz = x[2] - p2;
-            len = len + sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
-        }
-        if constexpr (CHECK) {
-            if (!bounds_ok(P, x)) {
-                path_len = len;
-                return false;
-            }
-            if constexpr (OBST) {
-                if (hits_obstacle(P, x[0], x[1], x[2], tests)) {
-                    path_len = len;
-                    return false;
-                }
-            }
-        }
-    }
-    path_len = len;
-    return true;
-}
-
 // Obstacle pass alone over a re-integrated segment (used after an early cost
 // check; same integration arithmetic as rollout()).
 template <int DYN, int INTEG>
@@ -343,21 +315,19 @@ __device__ __forceinline__ int region_of(const DevParams& P, const float (&x)[N]
     constexpr float TWO_PI_F = 6.28318530717958647692f;
     int id = 0;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-        if (a < P.n_axes) {
-            float xv = x[0];
-#pragma unroll
-            for (int d = 1; d < N; ++d)
-                if (P.ax_dim[a] == d) xv = x[d];
-            if (P.ax_wrap[a]) {
+    for (int d = 0; d < N; ++d) {  // components in a fixed order: no indexed access to x
+        const int bins = P.rg_bins[d];
+        if (bins > 0) {
+            float xv = x[d];
+            if (P.rg_wrap[d]) {
                 const float t = __fdiv_rn(__fadd_rn(xv, PI_F), TWO_PI_F);
                 xv = __fsub_rn(xv, __fmul_rn(TWO_PI_F, floorf(t)));
             }
-            const float t = __fmul_rn(__fsub_rn(xv, P.ax_lo[a]), P.ax_scale[a]);
+            const float t = __fmul_rn(__fsub_rn(xv, P.rg_lo[d]), P.rg_scale[d]);
             int c = (int)floorf(t);
             c = c < 0 ? 0 : c;
-            c = c > P.ax_bins[a] - 1 ? P.ax_bins[a] - 1 : c;
-            id = id * P.ax_bins[a] + c;
+            c = c > bins - 1 ? bins - 1 : c;
+            id += c * P.rg_stride[d];
         }
     }
     return id;
@@ -394,5 +364,51 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t* p, uint64_t v) {
 __device__ __forceinline__ void set_status(kpx_device_header* h, int code) {
     atomicCAS(&h->status, (int)KPX_OK, code);
 }
+
+// One rollout held by one lane: started from a slot, advanced one
+// integration step at a time.  The propagate kernel interleaves many of
+// these per warp (a lane takes a new slot as soon as its rollout ends); the
+// append kernel replays a winner through the same advance(), which makes the
+// re-materialised end state and cost bit-identical.
+template <int DYN, int INTEG>
+struct LaneRollout {
+    static constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
+    float x[n], u[m];
+    Stepper<DYN, INTEG> st;
+    float len, cost0;
+    int K, k, node;
+
+    __device__ __forceinline__ void start(const DevParams& P, const int32_t* __restrict__ va, int lam, uint32_t iter,
+                                          int64_t slot) {
+        const int j = (int)(slot / lam);
+        const int s = (int)(slot - (int64_t)j * lam);
+        node = va[j];
+#pragma unroll
+        for (int d = 0; d < n; ++d) x[d] = P.x[(int64_t)d * P.N + node];
+        cost0 = key_cost(P.key[node]);
+        sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
+        st.init(P, x, u);
+        len = 0.0f;
+        k = 0;
+    }
+
+    // One step; returns whether the new point is valid (bounds, and the
+    // obstacles when OBST).
+    template <bool OBST>
+    __device__ __forceinline__ bool advance(const DevParams& P, uint32_t& tests) {
+        const float p0 = x[0], p1 = x[1], p2 = x[2];
+        st.advance(P, x, u);
+        ++k;
+        if (P.cost_kind == KPX_COST_PATH_LENGTH) {
+            const float dx = x[0] - p0, dy = x[1] - p1, dz = x[2] - p2;
+            len = len + sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+        }
+        if (!bounds_ok(P, x)) return false;
+        if (OBST && hits_obstacle(P, x[0], x[1], x[2], tests)) return false;
+        return true;
+    }
+
+    __device__ __forceinline__ float cost(const DevParams& P) const { return cost0 + edge_cost<m>(P, K, len, u); }
+};
 
 }  // namespace kpx

@@ -54,6 +54,10 @@ struct DevParams {
     int32_t n_axes;
     int32_t ax_dim[8], ax_bins[8], ax_wrap[8];
     float ax_lo[8], ax_scale[8];
+    // the same grid indexed by state component (0 bins: not a region axis);
+    // id = sum over axes of cell * stride, stride = product of later axes' bins
+    int32_t rg_bins[16], rg_wrap[16], rg_stride[16];
+    float rg_lo[16], rg_scale[16];
     float start[16];
     // planner
     int32_t N, R, lambda_fixed, i_max;
@@ -120,6 +124,27 @@ struct Layout {
     int32_t n_win_tiles, n_prune_tiles;
     int32_t traj_rows;
 };
+
+// fills the per-component region fields from the per-axis ones
+inline void fill_region_by_component(DevParams& P) {
+    for (int d = 0; d < 16; ++d) {
+        P.rg_bins[d] = 0;
+        P.rg_wrap[d] = 0;
+        P.rg_stride[d] = 0;
+        P.rg_lo[d] = 0.0f;
+        P.rg_scale[d] = 0.0f;
+    }
+    int stride = 1;
+    for (int a = P.n_axes - 1; a >= 0; --a) {
+        const int d = P.ax_dim[a];
+        P.rg_bins[d] = P.ax_bins[a];
+        P.rg_wrap[d] = P.ax_wrap[a];
+        P.rg_lo[d] = P.ax_lo[a];
+        P.rg_scale[d] = P.ax_scale[a];
+        P.rg_stride[d] = stride;
+        stride *= P.ax_bins[a];
+    }
+}
 
 // launchers (kpx_kernels.cu); each returns the launch status
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s);

@@ -265,12 +265,24 @@ __global__ void k_begin(DevParams P) {
 }
 
 // ---------------------------------------------------------------------------
-// propagate (Alg. 2).  Warps take 32 consecutive slots at a time from an
-// atomic ticket (dynamic balance of variable-length rollouts).  Slot =
-// rank j of the parent in V_A times lambda plus sample s.
+// propagate (Alg. 2).  Slot = rank j of the parent in V_A times lambda plus
+// sample s; one lane per slot.  A warp's first chunk of 32 slots is fixed
+// (warp-major across blocks, no atomic); later chunks come from a ticket, so
+// warps that drew short rollouts take more work.
 // ---------------------------------------------------------------------------
+// resident blocks per SM requested from the register allocator: the 12D
+// quadcopter's RK4 would otherwise need ~100 registers (two blocks per SM)
+#ifndef KPX_QUAD_MIN_BLOCKS
+#define KPX_QUAD_MIN_BLOCKS 3
+#endif
+template <int DYN>
+struct PropOccupancy {
+    static constexpr int blocks = DYN == KPX_QUAD12 ? KPX_QUAD_MIN_BLOCKS : 4;
+};
+
 template <int DYN, int INTEG>
-__global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_debug_records rec, int rec_on) {
+__global__ void __launch_bounds__(PROP_THREADS, PropOccupancy<DYN>::blocks)
+    k_propagate(DevParams P, kpx_debug_records rec, int rec_on) {
     constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
     kpx_device_header* H = P.hdr;
     if (!H->active) return;
@@ -281,80 +293,67 @@ __global__ void __launch_bounds__(PROP_THREADS) k_propagate(DevParams P, kpx_deb
     const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) && !rec_on;
     const int lane = threadIdx.x & 31;
     const uint32_t cand_base = (uint32_t)P.N;
-    uint32_t steps = 0, tests = 0;
-    // warp w first takes chunk w (no atomic); later chunks come from the
-    // ticket, offset by the number of warps in the grid
     const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    // warp-major: consecutive chunks land on different blocks (SMs)
     int64_t chunk = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    uint32_t steps = 0, tests = 0, n_valid = 0;
     for (;;) {
         const int64_t base = chunk * 32;
         if (base >= n_slots) break;
         const int64_t slot = base + lane;
-        bool valid = false;
         if (slot < n_slots) {
-            const int j = (int)(slot / lam);
-            const int s = (int)(slot - (int64_t)j * lam);
-            const int node = va[j];
-            float x[n], u[m];
-#pragma unroll
-            for (int d = 0; d < n; ++d) x[d] = P.x[(int64_t)d * P.N + node];
-            const float cost0 = key_cost(P.key[node]);
-            int K;
-            sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
-            float len;
+            LaneRollout<DYN, INTEG> R;
+            R.start(P, va, lam, iter, slot);
+            bool ok = true;
+            while (ok && R.k < R.K) {
+                ++steps;
+                ok = early ? R.template advance<false>(P, tests) : R.template advance<true>(P, tests);
+            }
             int r = -1;
             uint64_t key = KEY_INF;
-            if (early) {
-                float x0[n];
-#pragma unroll
-                for (int d = 0; d < n; ++d) x0[d] = x[d];
-                bool ok = rollout<DYN, INTEG, true, false>(P, x, u, K, len, steps, tests);
-                if (ok) {
-                    const float c = cost0 + edge_cost<m>(P, K, len, u);
-                    r = region_of<n>(P, x);
-                    key = pack_key(c, cand_base + (uint32_t)slot);
+            if (ok) {
+                r = region_of<n>(P, R.x);
+                key = pack_key(R.cost(P), cand_base + (uint32_t)slot);
+                if (early) {
+                    // collision-after-cost: only a possible winner is checked against obstacles
                     ok = key < __ldcg(&P.region_key[r]);
-                    if (ok) ok = obstacle_pass<DYN, INTEG>(P, x0, u, K, steps, tests);
+                    if (ok) {
+                        float x0[n];
+#pragma unroll
+                        for (int d = 0; d < n; ++d) x0[d] = P.x[(int64_t)d * P.N + R.node];
+                        ok = obstacle_pass<DYN, INTEG>(P, x0, R.u, R.K, steps, tests);
+                    }
                 }
-                valid = ok;
-            } else {
-                valid = rollout<DYN, INTEG, true, true>(P, x, u, K, len, steps, tests);
-                if (valid) {
-                    const float c = cost0 + edge_cost<m>(P, K, len, u);
-                    r = region_of<n>(P, x);
-                    key = pack_key(c, cand_base + (uint32_t)slot);
-                }
+                if (ok && key < __ldcg(&P.region_key[r]))
+                    atomicMin((unsigned long long*)&P.region_key[r], (unsigned long long)key);
             }
-            if (valid && key < __ldcg(&P.region_key[r]))
-                atomicMin((unsigned long long*)&P.region_key[r], (unsigned long long)key);
+            n_valid += ok ? 1u : 0u;
             if (rec_on && slot < rec.capacity) {
-                rec.valid[slot] = valid ? 1 : 0;
-                rec.region[slot] = valid ? r : -1;
-                rec.key[slot] = valid ? key : KEY_INF;
-                rec.K[slot] = K;
+                rec.valid[slot] = ok ? 1 : 0;
+                rec.region[slot] = ok ? r : -1;
+                rec.key[slot] = ok ? key : KEY_INF;
+                rec.K[slot] = R.K;
 #pragma unroll
-                for (int d = 0; d < n; ++d) rec.x[(int64_t)d * rec.capacity + slot] = x[d];
+                for (int d = 0; d < n; ++d) rec.x[(int64_t)d * rec.capacity + slot] = R.x[d];
 #pragma unroll
-                for (int d = 0; d < m; ++d) rec.u[(int64_t)d * rec.capacity + slot] = u[d];
+                for (int d = 0; d < m; ++d) rec.u[(int64_t)d * rec.capacity + slot] = R.u[d];
             }
         }
-        const uint32_t vb = __ballot_sync(FULL, valid);
-        if (lane == 0 && vb) atomicAdd((unsigned long long*)&H->last_valid, (unsigned long long)__popc(vb));
         unsigned long long t = 0ull;
         if (lane == 0) t = atomicAdd((unsigned long long*)&H->prop_ticket, 1ull);
         chunk = n_warps + (int64_t)__shfl_sync(FULL, t, 0);
     }
-    // work counters (one atomic per warp per launch)
-    unsigned long long st = steps, te = tests;
+    // work counters (one atomic each per warp)
+    unsigned long long st = steps, te = tests, nv = n_valid;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         st += __shfl_down_sync(FULL, st, o);
         te += __shfl_down_sync(FULL, te, o);
+        nv += __shfl_down_sync(FULL, nv, o);
     }
     if (lane == 0 && st) {
         atomicAdd((unsigned long long*)&H->total_steps, st);
         atomicAdd((unsigned long long*)&H->total_box_tests, te);
+        if (nv) atomicAdd((unsigned long long*)&H->last_valid, nv);
     }
 }
 
@@ -455,19 +454,15 @@ __global__ void __launch_bounds__(128) k_append(DevParams P) {
     const int32_t* va = va_current(P, H);
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x) {
         const int slot = P.win_slot[w];
-        const int j = slot / lam;
-        const int s = slot - j * lam;
-        const int node = va[j];
-        float x[n], u[m];
-#pragma unroll
-        for (int d = 0; d < n; ++d) x[d] = P.x[(int64_t)d * P.N + node];
-        const float cost0 = key_cost(P.key[node]);
-        int K;
-        sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
-        float len;
-        uint32_t st_unused = 0, te_unused = 0;
-        rollout<DYN, INTEG, false, false>(P, x, u, K, len, st_unused, te_unused);
-        const float c = cost0 + edge_cost<m>(P, K, len, u);
+        LaneRollout<DYN, INTEG> Rw;
+        Rw.start(P, va, lam, iter, (int64_t)slot);
+        uint32_t te_unused = 0;
+        for (int k = 0; k < Rw.K; ++k) Rw.template advance<false>(P, te_unused);
+        const float c = Rw.cost(P);
+        const int node = Rw.node;
+        float (&x)[n] = Rw.x;
+        float (&u)[m] = Rw.u;
+        const int K = Rw.K;
         const int r = region_of<n>(P, x);
         const uint64_t cand_key = pack_key(c, (uint32_t)P.N + (uint32_t)slot);
         if (P.region_key[r] != cand_key) {
