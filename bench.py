@@ -79,6 +79,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--ttfs-seeds", type=int, default=8, help="problems (scene seeds) for time-to-first-solution")
     return ap.parse_args(argv)
 
 
@@ -313,6 +314,31 @@ def run_kpx(args):
     else:
         pl.close()
 
+    # time to first solution over independent problems (scene seeds), and the
+    # best cost after the iterations that fit in 100 ms at the measured rate
+    ttfs = None
+    if args.ttfs_seeds > 0:
+        t_iter_ms = ms / args.steps / max(1, iters_done)
+        n100 = max(1, int(100.0 / t_iter_ms))
+        times, costs100, solved = [], [], 0
+        for k in range(args.ttfs_seeds):
+            pk = kpx.Planner(spec["make"](args.seed + 1000 * (rank + 1) + k), device=dev, stream=stream)
+            s_k = pk.iterate(iters, stats=True)
+            if s_k["first_solution_iter"] >= 0:
+                solved += 1
+                times.append(s_k["first_solution_ns"] / 1e6)
+            pk.reset()
+            s100 = pk.iterate(n100, stats=True)
+            if not math.isinf(s100["best_cost"]):
+                costs100.append(float(s100["best_cost"]))
+            pk.close()
+        ttfs = {"problems": args.ttfs_seeds, "solved": solved, "iterations": iters,
+                "p50_ms": float(np.percentile(times, 50)) if times else None,
+                "p99_ms": float(np.percentile(times, 99)) if times else None,
+                "cost_at_100ms_median": float(np.median(costs100)) if costs100 else None,
+                "cost_at_100ms_iterations": n100,
+                "note": "device clock from the first iteration to the iteration that appended the first goal node"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = oracle_sample(prob, iters, args.cpu_seconds)
@@ -341,6 +367,7 @@ def run_kpx(args):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,
+            "ttfs": ttfs,
             "gpu_launches": launches_per_step * args.steps,
         }
         print(json.dumps(line))
