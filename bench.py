@@ -52,6 +52,12 @@ UNIT = "valid expansions/s"
 OPS_PER_STEP = {scenes.DI6: 22.0, scenes.DUBINS6: 96.0, scenes.QUAD12: 270.0}
 OPS_PER_BOX_TEST = 6.0
 SM_COUNT_FALLBACK = 152
+# DRAM bytes (read + write) of one propagate launch from the ncu captures in
+# profiles/ (the kernel build named there); None for a workload not captured.
+PROPAGATE_DRAM_BYTES = {
+    "dubins6_forest300": 34816,      # profiles/k_propagate_dubins6_forest300.md
+    "quad12_building1000": 423424,   # profiles/k_propagate_quad12_building1000.md (a 95k-slot launch)
+}
 FP32_LANES_PER_SM = 128
 
 WORKLOADS = {
@@ -359,7 +365,10 @@ def run_kpx(args):
                        "tree_nodes": int(st["n_nodes"]), "solution_cost": (None if math.isinf(st["best_cost"])
                                                                           else float(st["best_cost"]))},
             "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0, "traffic": None,
+                         "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0,
+                         "traffic": PROPAGATE_DRAM_BYTES.get(args.workload),
+                         "traffic_note": "DRAM bytes per propagate launch (ncu capture, profiles/); the kernel "
+                                         "is ALU/latency-bound and its working set stays in L2",
                          "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
                                        % (sms, FP32_LANES_PER_SM, peak_mhz),
                          "launch_ms": prop_launch_ms,
