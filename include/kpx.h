@@ -207,6 +207,44 @@ const char* kpx_status_str(kpx_status s);
  * p == NULL the message of the last failing kpx_create in this thread. */
 const char* kpx_last_error(const kpx_planner* p);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems iterated together.  Every phase of an
+ * iteration is one launch over the whole batch (propagate and append once
+ * per dynamics class present), so launch overhead does not grow with the
+ * number of problems.  Problems may differ in dynamics, obstacles, grid,
+ * capacity and lambda; each keeps its own tree, counters and Philox stream,
+ * and its result is the one it would get planned alone with kpx_create.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    const kpx_dynamics* dyn;
+    const kpx_workspace* ws;
+    const kpx_obstacles* obs;
+    const float* start;
+    const kpx_goal* goal;
+    const kpx_cost* cost;
+    const kpx_config* cfg;
+} kpx_problem;
+
+typedef struct kpx_batch kpx_batch;
+
+/* Device bytes for the batch (0 if count is out of [1, 65535] or a problem is invalid). */
+size_t kpx_batch_workspace_size(int32_t count, const kpx_problem* problems);
+/* Validates and initialises every problem (as kpx_create does) inside one
+ * caller-owned workspace (256-byte aligned, >= kpx_batch_workspace_size bytes).
+ * Errors as kpx_create, with the failing problem's index in
+ * kpx_batch_last_error(NULL). */
+kpx_status kpx_batch_create(int32_t count, const kpx_problem* problems, void* device_workspace, size_t workspace_bytes,
+                            void* cuda_stream, kpx_batch** out);
+/* n_iters iterations of every problem (asynchronous; CUDA graphs after the first). */
+kpx_status kpx_batch_iterate(kpx_batch* b, int32_t n_iters);
+/* Borrowed handle of problem `index` (caller's order) for kpx_iterate(.., 0, &stats),
+ * kpx_best_trajectory, kpx_get_layout, kpx_snapshot; owned by the batch (do not destroy). */
+kpx_status kpx_batch_member(kpx_batch* b, int32_t index, kpx_planner** out);
+/* Every problem back to its create state (asynchronous). */
+kpx_status kpx_batch_reset(kpx_batch* b);
+kpx_status kpx_batch_destroy(kpx_batch* b);
+const char* kpx_batch_last_error(const kpx_batch* b);
+
 /* One complete planning run that allocates nothing (the paper has no
  * counterpart: this is a deployment convenience of this library).
  *

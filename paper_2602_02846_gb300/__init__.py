@@ -33,7 +33,8 @@ KEY_INF = 0xFFFFFFFFFFFFFFFF
 
 EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_trajectory", "kpx_reset",
             "kpx_destroy", "kpx_status_str", "kpx_last_error", "kpx_get_layout", "kpx_debug_step",
-            "kpx_snapshot", "kpx_restore", "kpx_plan_static")
+            "kpx_snapshot", "kpx_restore", "kpx_plan_static", "kpx_batch_workspace_size", "kpx_batch_create",
+            "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error")
 
 
 class kpx_dynamics(C.Structure):
@@ -106,6 +107,12 @@ class kpx_layout(C.Structure):
                 ("mask_words", C.c_int64), ("workspace_bytes", C.c_size_t)]
 
 
+class kpx_problem(C.Structure):
+    _fields_ = [("dyn", C.POINTER(kpx_dynamics)), ("ws", C.POINTER(kpx_workspace)),
+                ("obs", C.POINTER(kpx_obstacles)), ("start", C.POINTER(C.c_float)), ("goal", C.POINTER(kpx_goal)),
+                ("cost", C.POINTER(kpx_cost)), ("cfg", C.POINTER(kpx_config))]
+
+
 class kpx_debug_records(C.Structure):
     _fields_ = [("valid", C.c_void_p), ("region", C.c_void_p), ("key", C.c_void_p), ("K", C.c_void_p),
                 ("x", C.c_void_p), ("u", C.c_void_p), ("capacity", C.c_int64)]
@@ -159,6 +166,20 @@ def load(path: Optional[str] = None):
                                       C.POINTER(C.c_float), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                       C.POINTER(C.c_float)]
         L.kpx_plan_static.restype = C.c_int
+        L.kpx_batch_workspace_size.argtypes = [C.c_int32, C.POINTER(kpx_problem)]
+        L.kpx_batch_workspace_size.restype = C.c_size_t
+        L.kpx_batch_create.argtypes = [C.c_int32, C.POINTER(kpx_problem), vp, C.c_size_t, vp, C.POINTER(vp)]
+        L.kpx_batch_create.restype = C.c_int
+        L.kpx_batch_iterate.argtypes = [vp, C.c_int32]
+        L.kpx_batch_iterate.restype = C.c_int
+        L.kpx_batch_member.argtypes = [vp, C.c_int32, C.POINTER(vp)]
+        L.kpx_batch_member.restype = C.c_int
+        L.kpx_batch_reset.argtypes = [vp]
+        L.kpx_batch_reset.restype = C.c_int
+        L.kpx_batch_destroy.argtypes = [vp]
+        L.kpx_batch_destroy.restype = C.c_int
+        L.kpx_batch_last_error.argtypes = [vp]
+        L.kpx_batch_last_error.restype = C.c_char_p
         _lib = L
         return L
 
@@ -300,6 +321,9 @@ class Planner:
         self._check(load().kpx_reset(self.h))
 
     def close(self):
+        if getattr(self, "_borrowed", False):
+            self.h = None
+            return
         if getattr(self, "h", None):
             load().kpx_destroy(self.h)
             self.h = None
@@ -388,6 +412,82 @@ class Planner:
         import torch
         lay = self.layout()
         return self._view(lay.win_slot, 4 * lay.R, torch.int32)[:count].cpu().numpy()
+
+
+class BatchPlanner:
+    """Many independent problems iterated together (kpx_batch_*): every phase
+    is one launch for the whole batch.  ``member(i)`` gives a Planner view of
+    problem i (statistics, trajectory, arrays) owned by the batch."""
+
+    def __init__(self, problems, device=None, stream=None, flags: int = 0):
+        import torch
+        L = load()
+        self.problems = list(problems)
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._structs = [problem_structs(p, flags) for p in self.problems]
+        arr = (kpx_problem * len(self.problems))()
+        for i, (d, w, o, g, c, cfg, obs, start) in enumerate(self._structs):
+            arr[i].dyn, arr[i].ws, arr[i].obs = C.pointer(d), C.pointer(w), C.pointer(o)
+            arr[i].start = start.ctypes.data_as(C.POINTER(C.c_float))
+            arr[i].goal, arr[i].cost, arr[i].cfg = C.pointer(g), C.pointer(c), C.pointer(cfg)
+        self._arr = arr
+        size = int(L.kpx_batch_workspace_size(len(self.problems), arr))
+        if size == 0:
+            raise KpxError(KPX_E_INVALID, "batch rejected by kpx_batch_workspace_size")
+        self.workspace = torch.empty(size + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._off = (-base) % 256
+        self.ws_ptr = base + self._off
+        h = C.c_void_p()
+        st = L.kpx_batch_create(len(self.problems), arr, C.c_void_p(self.ws_ptr), C.c_size_t(size),
+                                C.c_void_p(self.stream.cuda_stream), C.byref(h))
+        if st != KPX_OK:
+            raise KpxError(st, L.kpx_batch_last_error(None).decode())
+        self.h = h
+        self._members = {}
+
+    def iterate(self, n_iters: int = 1):
+        st = load().kpx_batch_iterate(self.h, int(n_iters))
+        if st != KPX_OK:
+            raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
+
+    def reset(self):
+        st = load().kpx_batch_reset(self.h)
+        if st != KPX_OK:
+            raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
+
+    def member(self, i: int) -> "Planner":
+        if i in self._members:
+            return self._members[i]
+        L = load()
+        mh = C.c_void_p()
+        if L.kpx_batch_member(self.h, int(i), C.byref(mh)) != KPX_OK:
+            raise KpxError(KPX_E_INVALID, "no member %d" % i)
+        view = Planner.__new__(Planner)
+        view.prob = self.problems[i]
+        view.device, view.stream = self.device, self.stream
+        view.workspace = self.workspace
+        view.h = mh
+        view._borrowed = True
+        view.n, view.m = self.problems[i].n, self.problems[i].m
+        lay = view.layout()
+        view.ws_ptr = int(lay.header)
+        view._off = view.ws_ptr - self.workspace.data_ptr()
+        view.ws_bytes = int(lay.workspace_bytes)
+        self._members[i] = view
+        return view
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().kpx_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def kpx_plan_static(prob, n_iters: int, stream=None, capacity: int = 4096, flags: int = 0):

@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -25,6 +26,22 @@ struct kpx_planner {
     std::string err;
     // iterations captured as CUDA graphs (built on first use; launched on `stream`)
     int graph_state = 0;  // 0 not tried, 1 ready, -1 unavailable (plain launches)
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph_one = nullptr;
+    cudaGraphExec_t graph_many = nullptr;
+};
+
+// Many problems iterated together (one launch per phase for all of them).
+struct kpx_batch {
+    int B = 0;
+    std::vector<kpx_planner*> members;   // ordered by dynamics class
+    std::vector<int> member_of_index;    // caller's index -> position in members
+    int n_classes = 0;
+    int cls_kind[6] = {}, cls_lo[6] = {}, cls_hi[6] = {};
+    kpx::BatchParams BP{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    int graph_state = 0;  // 0 not tried, 1 ready, -1 plain launches
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph_one = nullptr;
     cudaGraphExec_t graph_many = nullptr;
@@ -299,25 +316,15 @@ kpx_status run_phase(kpx_planner* p, int phase, const kpx_debug_records* rec) {
     return KPX_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-size_t kpx_workspace_size(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obstacles) {
-    if (!check_config(dyn, cfg, n_obstacles).empty()) return 0;
-    return make_layout(dyn, cfg, n_obstacles).total;
-}
-
-kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
-                      const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
-                      void* device_workspace, size_t workspace_bytes, void* cuda_stream, kpx_planner** out) {
-    g_create_error.clear();
+// Validates one problem and lays it out in `device_workspace` (no device
+// work): fills p->P, p->L, p->ws.  On failure returns the status and a message.
+kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                        const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                        void* device_workspace, size_t workspace_bytes, kpx_planner* p, std::string& err) {
     auto reject = [&](kpx_status st, const std::string& msg) {
-        g_create_error = msg;
+        err = msg;
         return st;
     };
-    if (!out) return reject(KPX_E_INVALID, "out is null");
-    *out = nullptr;
     if (!ws || !obs || !start || !goal || !cost) return reject(KPX_E_INVALID, "null argument");
     const int32_t n_obs = obs->count;
     std::string msg = check_config(dyn, cfg, n_obs);
@@ -349,11 +356,7 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
     if (workspace_bytes < L.total) return reject(KPX_E_NOMEM, "device workspace smaller than kpx_workspace_size()");
     if ((uint64_t)cfg->tree_cap + (uint64_t)L.slot_cap >= 0xFFFFFFFFull)
         return reject(KPX_E_INVALID, "tree_cap + candidate slots must stay below 2^32");
-
-    kpx_planner* p = new (std::nothrow) kpx_planner();
-    if (!p) return reject(KPX_E_NOMEM, "host allocation failed");
     p->L = L;
-    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     p->ws = reinterpret_cast<char*>(device_workspace);
     p->ws_bytes = workspace_bytes;
     DevParams& P = p->P;
@@ -394,6 +397,7 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
         }
     }
     P.n_axes = cfg->n_axes;
+    int64_t R = 1;
     for (int a = 0; a < cfg->n_axes; ++a) {
         const kpx_region_axis& ax = cfg->axis[a];
         P.ax_dim[a] = ax.state_dim;
@@ -402,9 +406,8 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
         P.ax_lo[a] = ax.lo;
         const float width = ax.hi - ax.lo;
         P.ax_scale[a] = (float)ax.bins / width;
+        R *= ax.bins;
     }
-    int64_t R = 1;
-    for (int a = 0; a < cfg->n_axes; ++a) R *= cfg->axis[a].bins;
     fill_region_by_component(P);
     P.N = cfg->tree_cap;
     P.R = (int32_t)R;
@@ -421,12 +424,15 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
     P.n_prune_tiles = L.n_prune_tiles;
     bind_pointers(p);
     choose_grid(P, obs->aabb, n_obs);
+    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) return reject(KPX_E_INVALID, "start state is not in X_valid");
+    return KPX_OK;
+}
 
-    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) {
-        delete p;
-        return reject(KPX_E_INVALID, "start state is not in X_valid");
-    }
-    std::vector<float4> ob((size_t)2 * (n_obs > 0 ? n_obs : 1));
+// Copies the obstacles (staged in `ob`, which must outlive the copy) and
+// enqueues the initialisation and the obstacle grid build.
+cudaError_t upload_and_init(kpx_planner* p, const kpx_obstacles* obs, std::vector<float4>& ob) {
+    const int n_obs = obs->count;
+    ob.assign((size_t)2 * (n_obs > 0 ? n_obs : 1), make_float4(0.0f, 0.0f, 0.0f, 0.0f));
     for (int b = 0; b < n_obs; ++b) {
         const float* o = obs->aabb + 6 * b;
         ob[2 * b] = make_float4(o[0], o[1], o[2], 0.0f);
@@ -434,9 +440,67 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
     }
     cudaError_t e = cudaSuccess;
     if (n_obs > 0)
-        e = cudaMemcpyAsync(P.obs, ob.data(), (size_t)2 * n_obs * sizeof(float4), cudaMemcpyHostToDevice, p->stream);
-    if (e == cudaSuccess) e = launch_init(P, true, p->stream);
-    if (e == cudaSuccess) e = launch_grid_build(P, p->stream);
+        e = cudaMemcpyAsync(p->P.obs, ob.data(), (size_t)2 * n_obs * sizeof(float4), cudaMemcpyHostToDevice,
+                            p->stream);
+    if (e == cudaSuccess) e = launch_init(p->P, true, p->stream);
+    if (e == cudaSuccess) e = launch_grid_build(p->P, p->stream);
+    return e;
+}
+
+size_t batch_header_bytes(int B) {
+    size_t off = align_up(sizeof(BatchHeader), 256);
+    off += align_up((size_t)B * sizeof(DevParams), 256);
+    off += 4 * align_up((size_t)(B + 1) * sizeof(int64_t), 256);
+    return off;
+}
+
+cudaError_t capture_batch(kpx_batch* b, int count, cudaGraphExec_t* exec) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return e;
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < count && le == cudaSuccess; ++i)
+        le = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->capture_stream);
+    e = cudaStreamEndCapture(b->capture_stream, &g);
+    if (le != cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t kpx_workspace_size(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obstacles) {
+    if (!check_config(dyn, cfg, n_obstacles).empty()) return 0;
+    return make_layout(dyn, cfg, n_obstacles).total;
+}
+
+kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                      const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                      void* device_workspace, size_t workspace_bytes, void* cuda_stream, kpx_planner** out) {
+    g_create_error.clear();
+    if (!out) {
+        g_create_error = "out is null";
+        return KPX_E_INVALID;
+    }
+    *out = nullptr;
+    kpx_planner* p = new (std::nothrow) kpx_planner();
+    if (!p) {
+        g_create_error = "host allocation failed";
+        return KPX_E_NOMEM;
+    }
+    p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    std::string msg;
+    kpx_status st = setup_member(dyn, ws, obs, start, goal, cost, cfg, device_workspace, workspace_bytes, p, msg);
+    if (st != KPX_OK) {
+        g_create_error = msg;
+        delete p;
+        return st;
+    }
+    std::vector<float4> ob;
+    cudaError_t e = upload_and_init(p, obs, ob);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // the host copy buffer is local
     if (e != cudaSuccess) {
         g_create_error = std::string("kpx_create: ") + cudaGetErrorString(e);
@@ -624,6 +688,184 @@ kpx_status kpx_snapshot(kpx_planner* p, void* dst) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     return e == cudaSuccess ? KPX_OK : cuda_fail(p, e, "snapshot");
 }
+
+size_t kpx_batch_workspace_size(int32_t count, const kpx_problem* problems) {
+    if (count < 1 || count > 65535 || !problems) return 0;
+    size_t total = batch_header_bytes(count);
+    for (int i = 0; i < count; ++i) {
+        const kpx_problem& q = problems[i];
+        if (!q.obs || !check_config(q.dyn, q.cfg, q.obs->count).empty()) return 0;
+        total += align_up(make_layout(q.dyn, q.cfg, q.obs->count).total, 256);
+    }
+    return total;
+}
+
+kpx_status kpx_batch_create(int32_t count, const kpx_problem* problems, void* device_workspace, size_t workspace_bytes,
+                            void* cuda_stream, kpx_batch** out) {
+    g_create_error.clear();
+    if (!out || !problems || count < 1 || count > 65535) {
+        g_create_error = "need 1 <= count <= 65535 problems and an output handle";
+        return KPX_E_INVALID;
+    }
+    *out = nullptr;
+    if (!device_workspace || reinterpret_cast<uintptr_t>(device_workspace) % 256 != 0) {
+        g_create_error = "device workspace must be non-null and 256-byte aligned";
+        return KPX_E_INVALID;
+    }
+    const size_t need = kpx_batch_workspace_size(count, problems);
+    if (need == 0) {
+        g_create_error = "a problem of the batch has an invalid configuration";
+        return KPX_E_INVALID;
+    }
+    if (workspace_bytes < need) {
+        g_create_error = "device workspace smaller than kpx_batch_workspace_size()";
+        return KPX_E_NOMEM;
+    }
+    kpx_batch* b = new (std::nothrow) kpx_batch();
+    if (!b) {
+        g_create_error = "host allocation failed";
+        return KPX_E_NOMEM;
+    }
+    b->B = count;
+    b->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    // order problems by dynamics class (stable), one propagate/append launch per class
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    auto kind_of = [&](int i) { return problems[i].dyn->kind * 2 + problems[i].dyn->integ; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return kind_of(a) < kind_of(c); });
+    b->member_of_index.assign(count, 0);
+    char* base = reinterpret_cast<char*>(device_workspace);
+    size_t off = batch_header_bytes(count);
+    std::vector<std::vector<float4>> staging(count);
+    std::vector<DevParams> host_ps(count);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+        const int i = order[k];
+        const kpx_problem& q = problems[i];
+        kpx_planner* p = new (std::nothrow) kpx_planner();
+        if (!p) {
+            g_create_error = "host allocation failed";
+            kpx_batch_destroy(b);
+            return KPX_E_NOMEM;
+        }
+        p->stream = b->stream;
+        b->members.push_back(p);
+        b->member_of_index[i] = k;
+        const size_t bytes = align_up(make_layout(q.dyn, q.cfg, q.obs->count).total, 256);
+        std::string msg;
+        kpx_status st = setup_member(q.dyn, q.ws, q.obs, q.start, q.goal, q.cost, q.cfg, base + off, bytes, p, msg);
+        if (st != KPX_OK) {
+            g_create_error = "problem " + std::to_string(i) + ": " + msg;
+            kpx_batch_destroy(b);
+            return st;
+        }
+        off += bytes;
+        host_ps[k] = p->P;
+        e = upload_and_init(p, q.obs, staging[k]);
+        const int kind = kind_of(i);
+        if (b->n_classes == 0 || b->cls_kind[b->n_classes - 1] != kind) {
+            b->cls_kind[b->n_classes] = kind;
+            b->cls_lo[b->n_classes] = k;
+            ++b->n_classes;
+        }
+        b->cls_hi[b->n_classes - 1] = k + 1;
+    }
+    BatchParams& BP = b->BP;
+    size_t h = 0;
+    BP.B = count;
+    BP.bh = reinterpret_cast<BatchHeader*>(base + h);
+    h += align_up(sizeof(BatchHeader), 256);
+    BP.Ps = reinterpret_cast<const DevParams*>(base + h);
+    h += align_up((size_t)count * sizeof(DevParams), 256);
+    int64_t* pre[4];
+    for (int t = 0; t < 4; ++t) {
+        pre[t] = reinterpret_cast<int64_t*>(base + h);
+        h += align_up((size_t)(count + 1) * sizeof(int64_t), 256);
+    }
+    BP.chunk_prefix = pre[0];
+    BP.scan_prefix = pre[1];
+    BP.win_prefix = pre[2];
+    BP.prune_prefix = pre[3];
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<DevParams*>(BP.Ps), host_ps.data(), (size_t)count * sizeof(DevParams),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(BP.bh, 0, sizeof(BatchHeader), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // staging buffers are local
+    if (e != cudaSuccess) {
+        g_create_error = std::string("kpx_batch_create: ") + cudaGetErrorString(e);
+        kpx_batch_destroy(b);
+        return KPX_E_CUDA;
+    }
+    *out = b;
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_iterate(kpx_batch* b, int32_t n_iters) {
+    if (!b) return KPX_E_INVALID;
+    if (n_iters < 0) {
+        b->err = "n_iters must be >= 0";
+        return KPX_E_INVALID;
+    }
+    int32_t it = 0;
+    cudaError_t e = cudaSuccess;
+    if (b->graph_state == 0 && n_iters > 0) {
+        // the first iteration runs plainly (it also computes the launch shapes),
+        // then the iteration is captured once as a graph
+        e = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->stream);
+        ++it;
+        b->graph_state = -1;
+        if (e == cudaSuccess && cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) == cudaSuccess) {
+            if (capture_batch(b, 1, &b->graph_one) == cudaSuccess &&
+                capture_batch(b, kGraphIterations, &b->graph_many) == cudaSuccess)
+                b->graph_state = 1;
+            else
+                cudaGetLastError();
+        }
+    }
+    if (b->graph_state == 1) {
+        for (; e == cudaSuccess && it + kGraphIterations <= n_iters; it += kGraphIterations)
+            e = cudaGraphLaunch(b->graph_many, b->stream);
+        for (; e == cudaSuccess && it < n_iters; ++it) e = cudaGraphLaunch(b->graph_one, b->stream);
+    }
+    for (; e == cudaSuccess && it < n_iters; ++it)
+        e = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->stream);
+    if (e != cudaSuccess) {
+        b->err = std::string("batch iteration: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_member(kpx_batch* b, int32_t index, kpx_planner** out) {
+    if (!b || !out || index < 0 || index >= b->B) return KPX_E_INVALID;
+    *out = b->members[b->member_of_index[index]];
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_reset(kpx_batch* b) {
+    if (!b) return KPX_E_INVALID;
+    for (kpx_planner* p : b->members) {
+        cudaError_t e = launch_init(p->P, false, b->stream);
+        if (e != cudaSuccess) {
+            b->err = std::string("batch reset: ") + cudaGetErrorString(e);
+            return KPX_E_CUDA;
+        }
+    }
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_destroy(kpx_batch* b) {
+    if (!b) return KPX_OK;
+    cudaError_t e = b->stream ? cudaStreamSynchronize(b->stream) : cudaSuccess;
+    for (kpx_planner* p : b->members) kpx_destroy(p);
+    if (b->graph_one) cudaGraphExecDestroy(b->graph_one);
+    if (b->graph_many) cudaGraphExecDestroy(b->graph_many);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    delete b;
+    return e == cudaSuccess ? KPX_OK : KPX_E_CUDA;
+}
+
+const char* kpx_batch_last_error(const kpx_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
 
 kpx_status kpx_restore(kpx_planner* p, const void* src) {
     if (!p || !src) return KPX_E_INVALID;

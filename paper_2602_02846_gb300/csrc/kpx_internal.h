@@ -146,6 +146,27 @@ inline void fill_region_by_component(DevParams& P) {
     }
 }
 
+// Many problems in one launch per phase (kpx_batch.cu).
+struct BatchHeader {
+    unsigned long long prop_ticket[6];  // per dynamics class
+    uint32_t scan_ticket, prune_ticket;
+};
+
+struct BatchParams {
+    int32_t B;       // problems, ordered by class
+    int32_t lo, hi;  // class range for the per-class launches
+    int32_t cls;     // class index (its ticket)
+    const DevParams* Ps;     // [B] device copy of every problem's parameters
+    BatchHeader* bh;
+    int64_t* chunk_prefix;   // [B+1] propagate chunks (32 slots) before problem p
+    int64_t* scan_prefix;    // [B+1] winner-scan tiles before p
+    int64_t* win_prefix;     // [B+1] winners before p
+    int64_t* prune_prefix;   // [B+1] prune tiles before p
+};
+
+cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const int* cls_kind, const int* cls_lo,
+                                   const int* cls_hi, cudaStream_t s);
+
 // launchers (kpx_kernels.cu); each returns the launch status
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s);
 cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s);

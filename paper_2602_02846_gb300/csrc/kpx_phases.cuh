@@ -1,0 +1,453 @@
+// kpx_phases.cuh -- one unit of work of each phase of a Kino-PAX+ iteration,
+// shared by the single-problem kernels (kpx_kernels.cu) and the batched
+// kernels (kpx_batch.cu).  A unit is a 32-slot chunk (propagate), a region
+// (mark), a tile of the winner bitmask (scan), a winner (append) or a tile of
+// node ids (prune); the kernels only decide which units a block or warp takes.
+#pragma once
+
+#include "kpx_device.cuh"
+
+namespace kpx {
+
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+constexpr uint32_t LOOKBACK_POLL_LIMIT = 1u << 20;
+
+// ---------------------------------------------------------------------------
+// Block-wide exclusive scan of one value per thread.
+// ---------------------------------------------------------------------------
+template <int THREADS>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < NW ? s_warp[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NW) s_warp[lane] = w;
+    }
+    __syncthreads();
+    const uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
+    total = s_warp[NW - 1];
+    __syncthreads();
+    return excl;
+}
+
+// Single-pass chained scan across tiles ("decoupled look-back"): each tile
+// publishes its aggregate, then walks back over predecessors until it meets
+// an inclusive prefix.  Tile ids come from an atomic ticket, so every
+// predecessor of a waiting tile is already running.  Status word:
+// epoch (30 bits) << 34 | flag (1 aggregate, 2 prefix) << 32 | value.
+// The wait is bounded: after LOOKBACK_POLL_LIMIT polls the kernel records
+// KPX_E_TIMEOUT and continues with the partial prefix.
+__device__ __forceinline__ uint32_t lookback(uint64_t* tiles, uint32_t tile, uint32_t agg, uint32_t epoch,
+                                             kpx_device_header* H) {
+    const uint64_t E = (uint64_t)(epoch & 0x3FFFFFFFu);
+    if (tile == 0) {
+        st_relaxed_u64(&tiles[0], (E << 34) | (2ull << 32) | agg);
+        return 0u;
+    }
+    st_relaxed_u64(&tiles[tile], (E << 34) | (1ull << 32) | agg);
+    uint32_t excl = 0u;
+    int t = (int)tile - 1;
+    uint32_t polls = 0;
+    while (t >= 0) {
+        const uint64_t w = ld_relaxed_u64(&tiles[t]);
+        const uint32_t flag = (uint32_t)(w >> 32) & 3u;
+        if ((w >> 34) == E && flag != 0u) {
+            excl += (uint32_t)w;
+            if (flag == 2u) break;
+            --t;
+        } else {
+            if (++polls > LOOKBACK_POLL_LIMIT) {
+                set_status(H, KPX_E_TIMEOUT);
+                H->err_info[0] = 0x10000u | tile;
+                break;
+            }
+            __nanosleep(32);
+        }
+    }
+    st_relaxed_u64(&tiles[tile], (E << 34) | (2ull << 32) | (excl + agg));
+    return excl;
+}
+
+__device__ __forceinline__ const int32_t* va_current(const DevParams& P, const kpx_device_header* H) {
+    return H->va_sel ? P.va1 : P.va0;
+}
+
+// ---------------------------------------------------------------------------
+// begin: branching factor (fixed, or floor(t_e/|V_A|)), slot count, tickets.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int begin_lambda(const DevParams& P, int count_A) {
+    return P.lambda_fixed > 0 ? P.lambda_fixed : (count_A > 0 ? max(1, P.N / count_A) : 0);
+}
+
+// one thread per problem
+__device__ __forceinline__ void begin_counters(const DevParams& P) {
+    kpx_device_header* H = P.hdr;
+    const bool active = H->status == KPX_OK;
+    const int lam = begin_lambda(P, H->count_A);
+    H->active = active ? 1 : 0;
+    H->lambda = lam;
+    H->n_slots = active ? (int64_t)H->count_A * lam : 0;
+    H->prop_ticket = 0ull;
+    H->win_ticket = 0u;
+    H->prune_ticket = 0u;
+    H->n_win = 0;
+    H->n_kept = 0;
+    H->count_A_next = 0;
+    H->last_valid = 0ull;
+    H->n_active = H->n_inactive = H->n_terminal = 0;
+    if (active) {
+        H->epoch = (H->epoch + 1) & 0x3FFFFFFF;
+        if (H->epoch == 0) H->epoch = 1;
+        if (H->t_start_ns == 0ull) H->t_start_ns = globaltimer_ns();
+    }
+}
+
+// The capacity rule can only trigger when the largest possible number of
+// winners (one per region, at most one per slot) overflows the tree.
+// Computed from counters that begin_counters does not write.
+__device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P) {
+    const kpx_device_header* H = P.hdr;
+    if (H->status != KPX_OK) return false;
+    const int64_t n_slots = (int64_t)H->count_A * begin_lambda(P, H->count_A);
+    const int64_t max_new = n_slots < P.R ? n_slots : P.R;
+    return (int64_t)H->n_nodes + max_new > P.N;
+}
+
+// ---------------------------------------------------------------------------
+// propagate (Alg. 2): 32 consecutive slots, one per lane.  Slot = rank j of
+// the parent in V_A times lambda plus sample s.
+// ---------------------------------------------------------------------------
+template <int DYN, int INTEG>
+__device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_slots, int lam, uint32_t iter,
+                                                const int32_t* va, bool early, int64_t chunk,
+                                                const kpx_debug_records& rec, int rec_on, uint32_t& steps,
+                                                uint32_t& tests, uint32_t& n_valid) {
+    constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
+    const int64_t slot = chunk * 32 + (threadIdx.x & 31);
+    if (slot >= n_slots) return;
+    LaneRollout<DYN, INTEG> R;
+    R.start(P, va, lam, iter, slot);
+    bool ok = true;
+    while (ok && R.k < R.K) {
+        ++steps;
+        ok = early ? R.template advance<false>(P, tests) : R.template advance<true>(P, tests);
+    }
+    int r = -1;
+    uint64_t key = KEY_INF;
+    if (ok) {
+        r = region_of<n>(P, R.x);
+        key = pack_key(R.cost(P), (uint32_t)P.N + (uint32_t)slot);
+        if (early) {
+            // collision-after-cost: only a possible winner is checked against obstacles
+            ok = key < __ldcg(&P.region_key[r]);
+            if (ok) {
+                float x0[n];
+#pragma unroll
+                for (int d = 0; d < n; ++d) x0[d] = P.x[(int64_t)d * P.N + R.node];
+                ok = obstacle_pass<DYN, INTEG>(P, x0, R.u, R.K, steps, tests);
+            }
+        }
+        if (ok && key < __ldcg(&P.region_key[r]))
+            atomicMin((unsigned long long*)&P.region_key[r], (unsigned long long)key);
+    }
+    n_valid += ok ? 1u : 0u;
+    if (rec_on && slot < rec.capacity) {
+        rec.valid[slot] = ok ? 1 : 0;
+        rec.region[slot] = ok ? r : -1;
+        rec.key[slot] = ok ? key : KEY_INF;
+        rec.K[slot] = R.K;
+#pragma unroll
+        for (int d = 0; d < n; ++d) rec.x[(int64_t)d * rec.capacity + slot] = R.x[d];
+#pragma unroll
+        for (int d = 0; d < m; ++d) rec.u[(int64_t)d * rec.capacity + slot] = R.u[d];
+    }
+}
+
+// warp-wide: add the lane counters to the problem's header (one atomic each)
+__device__ __forceinline__ void flush_propagate_counters(kpx_device_header* H, uint32_t& steps, uint32_t& tests,
+                                                         uint32_t& n_valid) {
+    unsigned long long st = steps, te = tests, nv = n_valid;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        st += __shfl_down_sync(FULL, st, o);
+        te += __shfl_down_sync(FULL, te, o);
+        nv += __shfl_down_sync(FULL, nv, o);
+    }
+    if ((threadIdx.x & 31) == 0 && st) {
+        atomicAdd((unsigned long long*)&H->total_steps, st);
+        atomicAdd((unsigned long long*)&H->total_box_tests, te);
+        if (nv) atomicAdd((unsigned long long*)&H->last_valid, nv);
+    }
+    steps = tests = n_valid = 0;
+}
+
+// ---------------------------------------------------------------------------
+// mark: a region whose key carries a candidate id (>= N) names the slot of
+// the winner of that region (the V_U filter: "cost(x) = cost(R_i)").
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void mark_region(const DevParams& P, int r) {
+    const uint64_t k = P.region_key[r];
+    if (k == KEY_INF) return;
+    const uint32_t id = (uint32_t)k;
+    if (id < (uint32_t)P.N) return;
+    const uint32_t slot = id - (uint32_t)P.N;
+    if ((int64_t)slot >= P.slot_cap) {  // a stale candidate id: cannot happen in a consistent state
+        set_status(P.hdr, KPX_E_INTERNAL);
+        return;
+    }
+    atomicOr(&P.win_mask[slot >> 5], 1u << (slot & 31));
+}
+
+// ---------------------------------------------------------------------------
+// scan (block-wide): one tile of the winner bitmask; ranks in ascending slot
+// order -> win_slot[rank]; clears the words.  The problem's last tile writes
+// its winner count.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void scan_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int64_t n_tiles,
+                                          int64_t live_words, uint32_t* s_warp, uint32_t& s_prefix) {
+    const int64_t w0 = (int64_t)tile * WIN_TILE_WORDS + (int64_t)threadIdx.x * WIN_WORDS_PER_THREAD;
+    uint32_t w[WIN_WORDS_PER_THREAD];
+    uint32_t cnt = 0;
+#pragma unroll
+    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
+        w[i] = (w0 + i < live_words) ? P.win_mask[w0 + i] : 0u;
+        cnt += __popc(w[i]);
+    }
+    uint32_t agg;
+    const uint32_t excl = block_exclusive_scan<WIN_THREADS>(cnt, agg, s_warp);
+    if (threadIdx.x == 0) {
+        s_prefix = lookback(P.win_tiles, tile, agg, (uint32_t)H->epoch, H);
+        if ((int64_t)tile == n_tiles - 1) H->n_win = (int32_t)(s_prefix + agg);
+    }
+    __syncthreads();
+    uint32_t rank = s_prefix + excl;
+#pragma unroll
+    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
+        uint32_t word = w[i];
+        while (word) {
+            const int b = __ffs(word) - 1;
+            word &= word - 1;
+            if (rank < (uint32_t)P.R)
+                P.win_slot[rank] = (int32_t)((w0 + i) * 32 + b);
+            else
+                set_status(H, KPX_E_INTERNAL);
+            ++rank;
+        }
+        if (w[i]) P.win_mask[w0 + i] = 0u;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// append (UpdateTree, Alg. 4) of winner w: its rollout is re-materialised
+// from (seed, iteration, node, sample) with the propagate arithmetic, written
+// to T at n_old + w, and its region key rewritten with the new id; the
+// previous owner of the region becomes dominated.  Winners beyond the
+// capacity restore their region from the snapshot.  Goal nodes lower the
+// solution key.
+// ---------------------------------------------------------------------------
+template <int DYN, int INTEG>
+__device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_header* H, int w, int kept, int n_old,
+                                              int lam, uint32_t iter, const int32_t* va) {
+    constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
+    const int slot = P.win_slot[w];
+    LaneRollout<DYN, INTEG> Rw;
+    Rw.start(P, va, lam, iter, (int64_t)slot);
+    uint32_t te_unused = 0;
+    for (int k = 0; k < Rw.K; ++k) Rw.template advance<false>(P, te_unused);
+    const float c = Rw.cost(P);
+    const int r = region_of<n>(P, Rw.x);
+    const uint64_t cand_key = pack_key(c, (uint32_t)P.N + (uint32_t)slot);
+    if (P.region_key[r] != cand_key) {
+        set_status(H, KPX_E_INTERNAL);
+        H->err_info[1] = (uint32_t)slot;
+        return;
+    }
+    if (w < kept) {
+        const int id = n_old + w;
+#pragma unroll
+        for (int d = 0; d < n; ++d) P.x[(int64_t)d * P.N + id] = Rw.x[d];
+#pragma unroll
+        for (int d = 0; d < m; ++d) P.u[(int64_t)d * P.N + id] = Rw.u[d];
+        P.K[id] = (uint16_t)Rw.K;
+        P.parent[id] = Rw.node;
+        const uint64_t k = pack_key(c, (uint32_t)id);
+        P.key[id] = k;
+        P.region[id] = r;
+        P.set[id] = SET_A;
+        P.icount[id] = 0;
+        P.region_key[r] = k;
+        // the previous owner of r loses its region (one winner per region,
+        // so this thread is the only writer of that node's set byte)
+        const int old = P.region_owner[r];
+        if (old >= 0) P.set[old] = (uint8_t)(P.set[old] | SET_DOM);
+        P.region_owner[r] = id;
+        if (in_goal(P, Rw.x[0], Rw.x[1], Rw.x[2])) atomicMin((unsigned long long*)&H->goal_key, (unsigned long long)k);
+    } else {
+        P.region_key[r] = P.region_snap[r];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// prune (block-wide): PruneNodes (Alg. 3) over the tile's nodes below n_old,
+// literal rule order, then the tile's part of the compaction of V_A (Alg. 5)
+// over [0, total): nodes appended this iteration are active by Alg. 4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
+                                           int n_old, int total, int32_t* s_parent, uint8_t* s_set, uint32_t* s_warp,
+                                           uint32_t& s_prefix, int& cA, int& cI, int& cT) {
+    const int i_max = P.i_max;
+    const int tile0 = (int)tile * PRUNE_TILE;
+    // the tile's parent ids and set bytes: ancestor walks that stay inside
+    // the tile read shared memory (parents precede children)
+    for (int k = threadIdx.x; k < PRUNE_TILE; k += PRUNE_THREADS) {
+        const int i = tile0 + k;
+        s_parent[k] = i < n_old ? P.parent[i] : -1;
+        s_set[k] = i < n_old ? P.set[i] : 0;
+    }
+    __syncthreads();
+    const int base = tile0 + threadIdx.x * PRUNE_PER_THREAD;
+    uint32_t amask = 0;
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+        const int i = base + q;
+        if (i >= total) break;
+        if (i >= n_old) {  // appended this iteration: in V_A
+            amask |= 1u << q;
+            ++cA;
+            continue;
+        }
+        const uint8_t sb = P.set[i];
+        const int st = sb & SET_MASK;
+        if (st == SET_T) {  // V_T is permanent
+            ++cT;
+            continue;
+        }
+        // key(i) >= key(region(i)) always, with equality only for the region's
+        // owner: "best" is "not dominated"
+        const bool dominated = (sb & SET_DOM) != 0;
+        const bool best = !dominated;
+        int ic = P.icount[i];
+        const int ic0 = ic;
+        int nst = st;
+        bool anc = (sb & SET_ANC) != 0;
+        bool done = false;
+        if (best && st == SET_I) {  // rule 1: region best while inactive
+            ++ic;
+            if (ic > i_max) {
+                nst = SET_A;
+                done = true;
+            }
+        }
+        if (!done && ic > i_max && best) done = true;  // rule 2
+        if (!done && dominated) {                       // rule 3: dominated
+            nst = SET_T;
+            done = true;
+        }
+        if (!done) {  // rule 4: any strict ancestor dominated
+            if (!anc) {
+                int p = s_parent[i - tile0];
+                while (p >= tile0) {  // inside the tile: shared memory (a stale set byte
+                    // only lacks a monotone flag, which the walk re-derives)
+                    const uint8_t sp = s_set[p - tile0];
+                    if (sp & (SET_DOM | SET_ANC)) {
+                        anc = true;
+                        break;
+                    }
+                    p = s_parent[p - tile0];
+                }
+                for (; !anc && p >= 0; p = P.parent[p]) {
+                    const uint8_t sp = *(volatile const uint8_t*)&P.set[p];
+                    if (sp & (SET_DOM | SET_ANC)) anc = true;
+                }
+            }
+            if (anc) nst = SET_I;
+        }
+        const uint8_t nb = (uint8_t)(nst | (anc ? SET_ANC : 0) | (sb & SET_DOM));
+        if (nb != sb) P.set[i] = nb;
+        if (ic != ic0) P.icount[i] = (uint8_t)ic;
+        if (nst == SET_A) {
+            amask |= 1u << q;
+            ++cA;
+        } else if (nst == SET_I) {
+            ++cI;
+        } else {
+            ++cT;
+        }
+    }
+    uint32_t agg;
+    const uint32_t excl = block_exclusive_scan<PRUNE_THREADS>((uint32_t)__popc(amask), agg, s_warp);
+    if (threadIdx.x == 0) {
+        s_prefix = lookback(P.prune_tiles, tile, agg, (uint32_t)H->epoch, H);
+        if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
+    }
+    __syncthreads();
+    int32_t* va_next = H->va_sel ? P.va0 : P.va1;
+    uint32_t pos = s_prefix + excl;
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+        if (amask & (1u << q)) {
+            // at most one active node per region, so pos < min(N, R) = va_cap
+            if (pos < (uint32_t)P.va_cap)
+                va_next[pos] = base + q;
+            else
+                set_status(H, KPX_E_INTERNAL);
+            ++pos;
+        }
+    }
+    __syncthreads();
+}
+
+// warp-wide: add the set sizes to the problem's header
+__device__ __forceinline__ void flush_prune_counters(kpx_device_header* H, int& cA, int& cI, int& cT) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        cA += __shfl_down_sync(FULL, cA, o);
+        cI += __shfl_down_sync(FULL, cI, o);
+        cT += __shfl_down_sync(FULL, cT, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (cA) atomicAdd(&H->n_active, cA);
+        if (cI) atomicAdd(&H->n_inactive, cI);
+        if (cT) atomicAdd(&H->n_terminal, cT);
+    }
+    cA = cI = cT = 0;
+}
+
+// ---------------------------------------------------------------------------
+// end (one thread per problem): commit the counters of the iteration.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void end_counters(const DevParams& P) {
+    kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    H->n_nodes += H->n_kept;
+    H->count_A = H->count_A_next;
+    H->va_sel ^= 1;
+    H->last_candidates = (uint64_t)H->n_slots;
+    H->last_winners = (uint64_t)H->n_kept;
+    H->total_candidates += (uint64_t)H->n_slots;
+    H->total_valid += H->last_valid;
+    H->total_winners += (uint64_t)H->n_kept;
+    const uint64_t now = globaltimer_ns();
+    if (H->goal_key != KEY_INF && H->first_solution_iter < 0) {
+        H->first_solution_iter = H->iter;
+        H->t_first_solution_ns = now;
+    }
+    H->iter += 1;
+    H->t_last_ns = now;
+}
+
+}  // namespace kpx
