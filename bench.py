@@ -70,6 +70,11 @@ WORKLOADS = {
                                 desc="12D quadcopter, 1,000-box building, RK4 h=0.005, 16^3x4^3 regions, "
                                      "cap 2^22, lambda 128"),
 }
+BATCH_WORKLOADS = {
+    "mixed_batch512": dict(count=512, desc="512 independent problems (DI / Dubins / quadcopter in turn), 10-1,000 "
+                                           "boxes, tree caps 2^14-2^20, each family's grid and lambda, one "
+                                           "launch per phase for all problems"),
+}
 DEFAULT_WORKLOAD = "dubins6_forest300"
 
 
@@ -79,7 +84,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("kpx", "reference"), default="kpx")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--iters", type=int, default=0, help="planner iterations per step (0 = the config's)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
@@ -383,10 +388,154 @@ def run_kpx(args):
     return 0
 
 
+def run_batch(args):
+    """Batched planning: one step = kpx_batch_reset + kpx_batch_iterate(I) over
+    all problems; compared with the plain planner run problem by problem."""
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2602_02846_gb300 as kpx
+    kpx.load()
+    spec = BATCH_WORKLOADS[args.workload]
+    iters = args.iters or 100
+    probs = scenes.mixed_batch(spec["count"], seed=args.seed + 1000 * rank, iterations=iters)
+    stream = torch.cuda.Stream(dev)
+    with torch.cuda.stream(stream):
+        batch = kpx.BatchPlanner(probs, device=dev, stream=stream)
+    B = len(probs)
+
+    def totals():
+        v = steps = tests = 0
+        ops = 0.0
+        for i, pr in enumerate(probs):
+            st = batch.member(i).iterate(0, stats=True)
+            v += int(st["total_valid"])
+            ops += OPS_PER_STEP[pr.dyn] * int(st["total_steps"]) + OPS_PER_BOX_TEST * int(st["total_box_tests"])
+        return v, ops
+
+    batch.reset()
+    batch.iterate(iters)
+    valid_per_step, ops_per_step = totals()
+    for _ in range(max(0, args.warmup - 1)):
+        batch.reset()
+        batch.iterate(iters)
+    stream.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        batch.reset()
+        batch.iterate(iters)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    assert totals()[0] == valid_per_step, "steps are not identical"
+    # time to first solution of every problem in the last step (device clock
+    # from the batch's first iteration)
+    first = []
+    for i in range(B):
+        st = batch.member(i).iterate(0, stats=True)
+        if st["first_solution_iter"] >= 0:
+            first.append(st["first_solution_ns"] / 1e6)
+    ms_max = allreduce(ms, "max", dev)
+    valid_all = allreduce(valid_per_step * args.steps, "sum", dev)
+    value = valid_all / (ms_max / 1e3)
+    # the plain planner, problem by problem, on the same problems (same results)
+    plain_ms = None
+    if not args.no_e2e:
+        singles = [kpx.Planner(pr, device=dev, stream=stream) for pr in probs]
+        for pl in singles:
+            pl.reset()
+            pl.iterate(iters)
+        stream.synchronize()
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for pl in singles:
+            pl.reset()
+            pl.iterate(iters)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        plain_ms = a.elapsed_time(b)
+        for pl in singles:
+            pl.close()
+        del singles
+    # end to end: create from host arrays, iterate, every best trajectory to host
+    e2e = None
+    if not args.no_e2e:
+        ws = batch.workspace
+        batch.close()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                b2 = kpx.BatchPlanner(probs, device=dev, stream=stream)
+            b2.iterate(iters)
+            d2h = 0
+            for i in range(B):
+                tr = b2.member(i).best_trajectory()
+                d2h += ctypes.sizeof(kpx.kpx_device_header)
+                if tr is not None:
+                    d2h += (len(tr["steps"]) + 1) * (probs[i].n + probs[i].m + 1) * 4
+            b2.close()
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        h2d = sum(int(np.asarray(pr.obstacles).shape[0]) * 32 for pr in probs)
+        e2e = {"value": valid_all / allreduce(wall, "max", dev), "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    else:
+        batch.close()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
+    peak = sms * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+    achieved = ops_per_step / (ms / args.steps / 1e3) / 1e12
+    if rank == 0:
+        kinds = {}
+        for pr in probs:
+            kinds[pr.name] = kinds.get(pr.name, 0) + 1
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": spec["desc"], "problems": B, "families": kinds,
+                       "iterations_per_step": iters, "seed": args.seed, "l2": "flushed between steps (256 MB write)",
+                       "valid_per_step": valid_per_step},
+            "plain_sequential": None if plain_ms is None else {
+                "value": valid_per_step / (plain_ms / 1e3), "ms_per_step": plain_ms,
+                "note": "the same problems planned one after another with kpx_create/kpx_iterate (identical "
+                        "results, so equal solution cost)"},
+            "batch_speedup_vs_plain": None if plain_ms is None else plain_ms / (ms / args.steps),
+            "roofline": {"bound": "alu", "kernel": "k_b_propagate (whole iteration time: a lower bound)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None},
+            "ttfs": {"problems": B, "solved": len(first),
+                     "p50_ms": float(np.percentile(first, 50)) if first else None,
+                     "p99_ms": float(np.percentile(first, 99)) if first else None,
+                     "note": "device clock from the batch's first iteration"},
+            "cpu_baseline": None, "e2e": e2e, "clocks": clk,
+            # per step: one reset kernel per problem, then per iteration begin, snapshot, mark, scan,
+            # prefix, prune, end and one propagate + one append per dynamics class
+            "gpu_launches": args.steps * (B + iters * (7 + 2 * len({(pr.dyn, pr.integ) for pr in probs}))),
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in BATCH_WORKLOADS:
+        return run_batch(args)
     return run_kpx(args)
 
 

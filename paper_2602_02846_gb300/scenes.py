@@ -274,6 +274,13 @@ def _seg_box_dist(box, a, b, samples=9):
     return min(_box_point_dist(box, a + (b - a) * t) for t in np.linspace(0.0, 1.0, samples))
 
 
+def _near_any_segment(box, seg_points, limit):
+    """True if any sample point of the opening axes lies within ``limit`` of
+    the box (same test as _seg_box_dist over every segment, vectorised)."""
+    d = np.maximum(np.maximum(box[:3] - seg_points, seg_points - box[3:]), 0.0)
+    return bool((np.sqrt((d * d).sum(axis=1)) <= limit).any())
+
+
 def voxel_connected(obstacles: np.ndarray, start, goal, ws_lo=(0, 0, 0), ws_hi=(1, 1, 1),
                     res: float = 0.005) -> bool:
     """Certify point-robot connectivity from start to goal on a voxel grid.
@@ -311,6 +318,8 @@ def quad_obstacles(seed: int, clutter: int = 964, edge=(0.01, 0.03), certify: bo
             axes.append((np.array([x - 0.05, cy, cz]), np.array([x + 0.05, cy, cz])))
         s = np.asarray(start, dtype=np.float64)
         g = np.asarray(goal, dtype=np.float64)
+        ts = np.linspace(0.0, 1.0, 9)[:, None]
+        seg_points = np.concatenate([a + (b - a) * ts for a, b in axes])
         n_clutter = 0
         while n_clutter < clutter:
             c = rng.uniform(0.0, 1.0, 3)
@@ -319,7 +328,7 @@ def quad_obstacles(seed: int, clutter: int = 964, edge=(0.01, 0.03), certify: bo
             box = box.astype(np.float32).astype(np.float64)
             if _box_point_dist(box, s) <= 0.08 or _box_point_dist(box, g) <= 0.08:
                 continue
-            if any(_seg_box_dist(box, a, b) <= 0.04 for a, b in axes):
+            if _near_any_segment(box, seg_points, 0.04):
                 continue
             boxes.append(list(box))
             n_clutter += 1
@@ -375,3 +384,27 @@ def obstacle_volume_fraction(obstacles: np.ndarray, res: float = 0.005) -> float
         i1 = [min(n, int(round(b[3 + a] / res))) for a in range(3)]
         occ[i0[0]:i1[0], i0[1]:i1[1], i0[2]:i1[2]] = True
     return float(occ.mean())
+
+
+def mixed_batch(count: int = 512, seed: int = 0, iterations: int = 100) -> List[Problem]:
+    """Independent problems of uneven size for batched planning: the three
+    families in turn, 10-1,000 seeded boxes each (walls plus clutter for the
+    quadcopter), tree capacities 2^14..2^20 (log-uniform), each family's
+    region grid and lambda (the double integrator on the 16^3 x 2^3 grid of
+    the paper's large-delta setting).  Quadcopter buildings are not
+    voxel-certified here (generation time)."""
+    rng = np.random.default_rng([0x5CE7E, 9, seed])
+    out = []
+    for k in range(count):
+        n_obs = int(rng.integers(10, 1001))
+        cap = 1 << int(rng.integers(14, 21))
+        s = int(rng.integers(1 << 30))
+        kind = k % 3
+        if kind == 0:
+            out.append(di_scene(s, n_obstacles=n_obs, tree_cap=cap, grid_pos=16, iterations=iterations))
+        elif kind == 1:
+            out.append(dubins_scene(s, n_obstacles=n_obs, tree_cap=cap, iterations=iterations))
+        else:
+            out.append(quad_scene(s, clutter=max(0, n_obs - 36), tree_cap=cap, certify=False,
+                                  iterations=iterations))
+    return out
