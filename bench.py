@@ -75,6 +75,11 @@ BATCH_WORKLOADS = {
                                            "boxes, tree caps 2^14-2^20, each family's grid and lambda, one "
                                            "launch per phase for all problems"),
 }
+SERVE_WORKLOADS = {
+    "serve_poisson200": dict(rate=200.0, desc="request loop: Poisson arrivals at 200 queries/s drawn from the "
+                                              "mixed-batch problem mix, admitted by device memory into per-class "
+                                              "slots, iterations of all resident queries batched"),
+}
 DEFAULT_WORKLOAD = "dubins6_forest300"
 
 
@@ -84,13 +89,18 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("kpx", "reference"), default="kpx")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS),
+                    default=DEFAULT_WORKLOAD)
     ap.add_argument("--iters", type=int, default=0, help="planner iterations per step (0 = the config's)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--ttfs-seeds", type=int, default=8, help="problems (scene seeds) for time-to-first-solution")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the served request stream")
+    ap.add_argument("--serve-memory-gb", type=float, default=32.0, help="device arena of the request loop")
+    ap.add_argument("--serve-slots", type=int, default=64, help="request-loop slots per dynamics class")
+    ap.add_argument("--serve-round", type=int, default=4, help="iterations per request-loop round")
     return ap.parse_args(argv)
 
 
@@ -530,12 +540,95 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """The request loop (continuous batching) on one stream of Poisson
+    arrivals; a step serves the whole stream in real time.  Beside it, the
+    same stream through the plain planner one query at a time."""
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2602_02846_gb300 as kpx
+    from paper_2602_02846_gb300 import serve
+    kpx.load()
+    spec = SERVE_WORKLOADS[args.workload]
+    budget = args.iters or 64
+    stream_reqs = scenes.poisson_requests(spec["rate"], args.serve_seconds, seed=args.seed + 1000 * rank)
+    sizes = [kpx.kpx_workspace_size(p) for _, p in stream_reqs]
+
+    def requests():
+        return [serve.Request(i, p, t, budget, nbytes=n) for i, ((t, p), n) in enumerate(zip(stream_reqs, sizes))]
+
+    stream = torch.cuda.Stream(dev)
+    srv = serve.Server.create(int(args.serve_memory_gb * (1 << 30)), slots_per_class=args.serve_slots, device=dev,
+                              stream=stream, iters_per_round=args.serve_round)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    warm = requests()[:min(len(stream_reqs), 48)]
+    for _ in range(args.warmup):
+        srv.serve(warm, realtime=False)
+    clocks = ClockSampler(local)
+    walls, results = [], None
+    srv.rounds = srv.resident_sum = srv.admits = srv.trajectories = 0
+    barrier()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        results = srv.serve(requests(), realtime=True)
+        torch.cuda.synchronize(dev)
+        walls.append(time.perf_counter() - t0)
+    barrier()
+    clk = clocks.stop()
+    wall = sum(walls)
+    summ = serve.summarize(results, srv.offset, walls[-1])
+    valid_step = sum(o.total_valid for o in results)
+    value = allreduce(valid_step * args.steps, "sum", dev) / allreduce(wall, "max", dev)
+    rounds, resident = srv.rounds, srv.resident_sum
+    launches = (rounds * (args.serve_round * (7 + 2 * 3) + 1) + srv.admits * 5 + srv.trajectories * 2)
+    srv.batch.close()
+    plain = None
+    if not args.no_e2e:
+        t0 = time.perf_counter()
+        pouts = serve.serve_plain(requests(), device=dev, stream=stream, iters_per_round=args.serve_round)
+        pwall = time.perf_counter() - t0
+        plain = serve.summarize(pouts, 0.0, pwall)
+        plain["wall_s"] = pwall
+        same = sum(1 for a, b in zip(results, pouts) if a.cost == b.cost and a.iterations == b.iterations)
+        plain["identical_costs"] = same
+    if rank == 0:
+        h2d = sum(int(np.asarray(p.obstacles).size) * 4 + int(np.asarray(p.start).size) * 4 for _, p in stream_reqs)
+        d2h = sum(0 if o.trajectory is None else
+                  (len(o.trajectory["steps"]) + 1) * (o.trajectory["states"].shape[1] + 1) * 4 for o in results)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": spec["desc"], "rate_qps": spec["rate"],
+                       "stream_seconds": args.serve_seconds, "requests": len(stream_reqs),
+                       "iterations_per_request": budget, "iterations_per_round": args.serve_round,
+                       "slots_per_class": args.serve_slots, "arena_gb": args.serve_memory_gb, "seed": args.seed,
+                       "l2": "flushed before each served stream (256 MB write)",
+                       "timing": "host wall clock of serve() over the whole stream (arrivals in real time)"},
+            "serving": summ,
+            "mean_resident": resident / rounds if rounds else None,
+            "plain_one_at_a_time": plain,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "note": "the request loop is end to end: problems from host arrays, trajectories to host"},
+            "cpu_baseline": None, "clocks": clk, "gpu_launches": launches,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload in BATCH_WORKLOADS:
         return run_batch(args)
+    if args.workload in SERVE_WORKLOADS:
+        return run_serve(args)
     return run_kpx(args)
 
 

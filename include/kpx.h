@@ -242,6 +242,40 @@ kpx_status kpx_batch_iterate(kpx_batch* b, int32_t n_iters);
 kpx_status kpx_batch_member(kpx_batch* b, int32_t index, kpx_planner** out);
 /* Every problem back to its create state (asynchronous). */
 kpx_status kpx_batch_reset(kpx_batch* b);
+
+/* Continuous batching: a request loop admits problems into slots as they
+ * free up, each in device memory sized for it.
+ *
+ * kpx_batch_assign re-initialises slot `index` with a new problem of the
+ * slot's dynamics class (else KPX_E_INVALID), asynchronously on the batch's
+ * stream.  device_workspace (256-byte aligned, >= kpx_workspace_size() of the
+ * problem, else KPX_E_NOMEM; caller-owned, kept alive until the slot is
+ * released or reassigned) holds the slot's tree; NULL keeps the slot's
+ * current workspace (the one from kpx_batch_create or the last assign) and
+ * workspace_bytes is ignored.  The slot then iterates with the batch while
+ * its iteration count is below iter_limit (0: no limit; < 0 KPX_E_INVALID)
+ * and idles after; its result equals that of the problem planned alone with
+ * kpx_create for the same number of iterations.
+ *
+ * kpx_batch_release marks slot `index` vacant.  Work enqueued on the batch's
+ * stream after it never touches the slot's workspace, so the caller may
+ * reuse that memory in stream order (its arrays stay readable until then).
+ * kpx_batch_reset skips vacant slots.
+ *
+ * kpx_batch_poll waits for the batch's stream and fills out[count] with every
+ * slot's state (status -1 for a vacant slot).  KPX_E_CUDA on a CUDA error. */
+typedef struct {
+    int32_t status, iter, n_nodes, first_solution_iter;
+    uint64_t goal_key;            /* (FP32 cost bits << 32) | node id; all ones: no solution */
+    /* device clock (%globaltimer, ns): the slot's first iteration, its first
+     * solution (0: none), the end of its last iteration, and the poll itself
+     * (t_poll_ns maps device times onto a host clock read right after). */
+    uint64_t t_start_ns, t_first_solution_ns, t_last_ns, t_poll_ns;
+} kpx_slot_state;
+kpx_status kpx_batch_assign(kpx_batch* b, int32_t index, const kpx_problem* problem, int32_t iter_limit,
+                            void* device_workspace, size_t workspace_bytes);
+kpx_status kpx_batch_release(kpx_batch* b, int32_t index);
+kpx_status kpx_batch_poll(kpx_batch* b, kpx_slot_state* out);
 kpx_status kpx_batch_destroy(kpx_batch* b);
 const char* kpx_batch_last_error(const kpx_batch* b);
 

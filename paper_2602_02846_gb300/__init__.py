@@ -34,7 +34,8 @@ KEY_INF = 0xFFFFFFFFFFFFFFFF
 EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_trajectory", "kpx_reset",
             "kpx_destroy", "kpx_status_str", "kpx_last_error", "kpx_get_layout", "kpx_debug_step",
             "kpx_snapshot", "kpx_restore", "kpx_plan_static", "kpx_batch_workspace_size", "kpx_batch_create",
-            "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error")
+            "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error",
+            "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll")
 
 
 class kpx_dynamics(C.Structure):
@@ -113,6 +114,12 @@ class kpx_problem(C.Structure):
                 ("cost", C.POINTER(kpx_cost)), ("cfg", C.POINTER(kpx_config))]
 
 
+class kpx_slot_state(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iter", C.c_int32), ("n_nodes", C.c_int32),
+                ("first_solution_iter", C.c_int32), ("goal_key", C.c_uint64), ("t_start_ns", C.c_uint64),
+                ("t_first_solution_ns", C.c_uint64), ("t_last_ns", C.c_uint64), ("t_poll_ns", C.c_uint64)]
+
+
 class kpx_debug_records(C.Structure):
     _fields_ = [("valid", C.c_void_p), ("region", C.c_void_p), ("key", C.c_void_p), ("K", C.c_void_p),
                 ("x", C.c_void_p), ("u", C.c_void_p), ("capacity", C.c_int64)]
@@ -180,6 +187,12 @@ def load(path: Optional[str] = None):
         L.kpx_batch_destroy.restype = C.c_int
         L.kpx_batch_last_error.argtypes = [vp]
         L.kpx_batch_last_error.restype = C.c_char_p
+        L.kpx_batch_assign.argtypes = [vp, C.c_int32, C.POINTER(kpx_problem), C.c_int32, vp, C.c_size_t]
+        L.kpx_batch_assign.restype = C.c_int
+        L.kpx_batch_release.argtypes = [vp, C.c_int32]
+        L.kpx_batch_release.restype = C.c_int
+        L.kpx_batch_poll.argtypes = [vp, C.POINTER(kpx_slot_state)]
+        L.kpx_batch_poll.restype = C.c_int
         _lib = L
         return L
 
@@ -414,6 +427,13 @@ class Planner:
         return self._view(lay.win_slot, 4 * lay.R, torch.int32)[:count].cpu().numpy()
 
 
+def _fill_problem(dst, structs):
+    d, w, o, g, c, cfg, obs, start = structs
+    dst.dyn, dst.ws, dst.obs = C.pointer(d), C.pointer(w), C.pointer(o)
+    dst.start = start.ctypes.data_as(C.POINTER(C.c_float))
+    dst.goal, dst.cost, dst.cfg = C.pointer(g), C.pointer(c), C.pointer(cfg)
+
+
 class BatchPlanner:
     """Many independent problems iterated together (kpx_batch_*): every phase
     is one launch for the whole batch.  ``member(i)`` gives a Planner view of
@@ -425,13 +445,13 @@ class BatchPlanner:
         self.problems = list(problems)
         self.device = torch.device(device if device is not None else "cuda")
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.flags = flags
         self._structs = [problem_structs(p, flags) for p in self.problems]
         arr = (kpx_problem * len(self.problems))()
-        for i, (d, w, o, g, c, cfg, obs, start) in enumerate(self._structs):
-            arr[i].dyn, arr[i].ws, arr[i].obs = C.pointer(d), C.pointer(w), C.pointer(o)
-            arr[i].start = start.ctypes.data_as(C.POINTER(C.c_float))
-            arr[i].goal, arr[i].cost, arr[i].cfg = C.pointer(g), C.pointer(c), C.pointer(cfg)
+        for i, st in enumerate(self._structs):
+            _fill_problem(arr[i], st)
         self._arr = arr
+        self._poll = (kpx_slot_state * len(self.problems))()
         size = int(L.kpx_batch_workspace_size(len(self.problems), arr))
         if size == 0:
             raise KpxError(KPX_E_INVALID, "batch rejected by kpx_batch_workspace_size")
@@ -446,6 +466,7 @@ class BatchPlanner:
             raise KpxError(st, L.kpx_batch_last_error(None).decode())
         self.h = h
         self._members = {}
+        self._slot_ws = {}  # slot -> tensor holding its workspace when not the batch's own
 
     def iterate(self, n_iters: int = 1):
         st = load().kpx_batch_iterate(self.h, int(n_iters))
@@ -457,6 +478,57 @@ class BatchPlanner:
         if st != KPX_OK:
             raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
 
+    def assign(self, i: int, prob, iter_limit: int = 0, workspace=None, offset: int = 0,
+               nbytes: Optional[int] = None):
+        """Re-initialise slot i with ``prob`` (same dynamics class); it
+        iterates with the batch until it has done ``iter_limit`` iterations
+        (0: no limit).  ``workspace``: a uint8 device tensor holding the
+        slot's tree from byte ``offset`` (256-byte aligned address, ``nbytes``
+        bytes, default the rest of the tensor), kept alive by the caller until
+        the slot is released; None keeps the slot's current workspace.
+        Asynchronous."""
+        structs = problem_structs(prob, self.flags)
+        one = kpx_problem()
+        _fill_problem(one, structs)
+        ptr, size = None, 0
+        if workspace is not None:
+            ptr = workspace.data_ptr() + int(offset)
+            size = int(nbytes) if nbytes is not None else workspace.numel() - int(offset)
+        st = load().kpx_batch_assign(self.h, int(i), C.byref(one), int(iter_limit), C.c_void_p(ptr),
+                                     C.c_size_t(size))
+        if st != KPX_OK:
+            raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
+        self.problems[i] = prob
+        self._structs[i] = structs
+        if workspace is not None:
+            self._slot_ws[i] = workspace
+        self._members.pop(i, None)  # the slot's layout follows the new problem
+
+    def release(self, i: int):
+        """Mark slot i vacant: work enqueued after this never touches the
+        slot's workspace (its arrays stay readable until that memory is
+        reused)."""
+        st = load().kpx_batch_release(self.h, int(i))
+        if st != KPX_OK:
+            raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
+
+    def poll(self):
+        """Waits for the batch's stream; returns one dict per slot (status -1:
+        vacant; goal_cost None: no solution yet)."""
+        st = load().kpx_batch_poll(self.h, self._poll)
+        if st != KPX_OK:
+            raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
+        out = []
+        for s in self._poll:
+            key = int(s.goal_key)
+            cost = None if key == KEY_INF else \
+                float(np.frombuffer(np.uint32(key >> 32).tobytes(), np.float32)[0])
+            out.append({"status": int(s.status), "iter": int(s.iter), "n_nodes": int(s.n_nodes),
+                        "first_solution_iter": int(s.first_solution_iter), "goal_cost": cost,
+                        "t_start_ns": int(s.t_start_ns), "t_first_solution_ns": int(s.t_first_solution_ns),
+                        "t_last_ns": int(s.t_last_ns), "t_poll_ns": int(s.t_poll_ns)})
+        return out
+
     def member(self, i: int) -> "Planner":
         if i in self._members:
             return self._members[i]
@@ -467,13 +539,13 @@ class BatchPlanner:
         view = Planner.__new__(Planner)
         view.prob = self.problems[i]
         view.device, view.stream = self.device, self.stream
-        view.workspace = self.workspace
+        view.workspace = self._slot_ws.get(i, self.workspace)
         view.h = mh
         view._borrowed = True
         view.n, view.m = self.problems[i].n, self.problems[i].m
         lay = view.layout()
         view.ws_ptr = int(lay.header)
-        view._off = view.ws_ptr - self.workspace.data_ptr()
+        view._off = view.ws_ptr - view.workspace.data_ptr()
         view.ws_bytes = int(lay.workspace_bytes)
         self._members[i] = view
         return view

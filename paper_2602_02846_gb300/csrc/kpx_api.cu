@@ -45,6 +45,10 @@ struct kpx_batch {
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graph_one = nullptr;
     cudaGraphExec_t graph_many = nullptr;
+    std::vector<std::vector<float4>> staging;  // per member: obstacles of the last (re)assignment
+    std::vector<kpx::SlotState> poll_buf;
+    kpx_device_header* parking = nullptr;     // [B] headers that vacant slots point at
+    std::vector<DevParams> parked;             // host source of a vacant slot's device parameters
 };
 
 namespace {
@@ -451,7 +455,16 @@ size_t batch_header_bytes(int B) {
     size_t off = align_up(sizeof(BatchHeader), 256);
     off += align_up((size_t)B * sizeof(DevParams), 256);
     off += 4 * align_up((size_t)(B + 1) * sizeof(int64_t), 256);
+    off += align_up((size_t)B * sizeof(SlotState), 256);
+    off += align_up((size_t)B * sizeof(kpx_device_header), 256);
     return off;
+}
+
+void drop_member_graphs(kpx_planner* p) {
+    if (p->graph_one) cudaGraphExecDestroy(p->graph_one);
+    if (p->graph_many) cudaGraphExecDestroy(p->graph_many);
+    p->graph_one = p->graph_many = nullptr;
+    p->graph_state = 0;
 }
 
 cudaError_t capture_batch(kpx_batch* b, int count, cudaGraphExec_t* exec) {
@@ -736,7 +749,8 @@ kpx_status kpx_batch_create(int32_t count, const kpx_problem* problems, void* de
     b->member_of_index.assign(count, 0);
     char* base = reinterpret_cast<char*>(device_workspace);
     size_t off = batch_header_bytes(count);
-    std::vector<std::vector<float4>> staging(count);
+    b->staging.assign(count, std::vector<float4>());
+    std::vector<std::vector<float4>>& staging = b->staging;
     std::vector<DevParams> host_ps(count);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < count && e == cudaSuccess; ++k) {
@@ -786,10 +800,17 @@ kpx_status kpx_batch_create(int32_t count, const kpx_problem* problems, void* de
     BP.scan_prefix = pre[1];
     BP.win_prefix = pre[2];
     BP.prune_prefix = pre[3];
+    BP.slots = reinterpret_cast<SlotState*>(base + h);
+    h += align_up((size_t)count * sizeof(SlotState), 256);
+    b->poll_buf.assign(count, SlotState{});
+    b->parking = reinterpret_cast<kpx_device_header*>(base + h);
+    h += align_up((size_t)count * sizeof(kpx_device_header), 256);
+    b->parked.assign(count, DevParams{});
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(const_cast<DevParams*>(BP.Ps), host_ps.data(), (size_t)count * sizeof(DevParams),
                             cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(BP.bh, 0, sizeof(BatchHeader), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->parking, 0, (size_t)count * sizeof(kpx_device_header), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // staging buffers are local
     if (e != cudaSuccess) {
         g_create_error = std::string("kpx_batch_create: ") + cudaGetErrorString(e);
@@ -842,9 +863,81 @@ kpx_status kpx_batch_member(kpx_batch* b, int32_t index, kpx_planner** out) {
     return KPX_OK;
 }
 
+kpx_status kpx_batch_assign(kpx_batch* b, int32_t index, const kpx_problem* problem, int32_t iter_limit,
+                            void* device_workspace, size_t workspace_bytes) {
+    if (!b || !problem || index < 0 || index >= b->B || iter_limit < 0) return KPX_E_INVALID;
+    const int k = b->member_of_index[index];
+    kpx_planner* p = b->members[k];
+    if (!problem->dyn || problem->dyn->kind * 2 + problem->dyn->integ != p->P.dyn * 2 + p->P.integ) {
+        b->err = "the slot holds another dynamics class";
+        return KPX_E_INVALID;
+    }
+    kpx_planner tmp;
+    tmp.stream = b->stream;
+    std::string msg;
+    void* ws = device_workspace ? device_workspace : p->ws;
+    const size_t ws_bytes = device_workspace ? workspace_bytes : p->ws_bytes;
+    kpx_status st = setup_member(problem->dyn, problem->ws, problem->obs, problem->start, problem->goal,
+                                 problem->cost, problem->cfg, ws, ws_bytes, &tmp, msg);
+    if (st != KPX_OK) {
+        b->err = msg;
+        return st;
+    }
+    drop_member_graphs(p);
+    p->P = tmp.P;
+    p->L = tmp.L;
+    p->ws = tmp.ws;
+    p->ws_bytes = tmp.ws_bytes;
+    p->P.iter_limit = iter_limit;
+    cudaError_t e = upload_and_init(p, problem->obs, b->staging[k]);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<DevParams*>(b->BP.Ps) + k, &p->P, sizeof(DevParams), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e != cudaSuccess) {
+        b->err = std::string("batch assign: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_release(kpx_batch* b, int32_t index) {
+    if (!b || index < 0 || index >= b->B) return KPX_E_INVALID;
+    const int k = b->member_of_index[index];
+    kpx_planner* p = b->members[k];
+    p->P.iter_limit = -1;
+    // the device copy points at a parking header: from here on (in stream
+    // order) no batch kernel touches the slot's workspace
+    b->parked[k] = p->P;
+    b->parked[k].hdr = b->parking + k;
+    cudaError_t e = cudaMemcpyAsync(const_cast<DevParams*>(b->BP.Ps) + k, &b->parked[k], sizeof(DevParams),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e != cudaSuccess) {
+        b->err = std::string("batch release: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_poll(kpx_batch* b, kpx_slot_state* out) {
+    if (!b || !out) return KPX_E_INVALID;
+    cudaError_t e = launch_batch_poll(b->BP, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->poll_buf.data(), b->BP.slots, (size_t)b->B * sizeof(SlotState), cudaMemcpyDeviceToHost,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        b->err = std::string("batch poll: ") + cudaGetErrorString(e);
+        return KPX_E_CUDA;
+    }
+    static_assert(sizeof(SlotState) == sizeof(kpx_slot_state), "slot state layouts differ");
+    for (int i = 0; i < b->B; ++i) memcpy(&out[i], &b->poll_buf[b->member_of_index[i]], sizeof(kpx_slot_state));
+    return KPX_OK;
+}
+
 kpx_status kpx_batch_reset(kpx_batch* b) {
     if (!b) return KPX_E_INVALID;
     for (kpx_planner* p : b->members) {
+        if (p->P.iter_limit < 0) continue;  // vacant slot
         cudaError_t e = launch_init(p->P, false, b->stream);
         if (e != cudaSuccess) {
             b->err = std::string("batch reset: ") + cudaGetErrorString(e);

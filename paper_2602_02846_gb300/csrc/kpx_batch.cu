@@ -198,6 +198,23 @@ __global__ void k_b_end(BatchParams BP) {
     if (p < BP.B) end_counters(BP.Ps[p]);
 }
 
+__global__ void k_b_poll(BatchParams BP) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= BP.B) return;
+    const kpx_device_header* H = BP.Ps[p].hdr;
+    SlotState st;
+    st.status = BP.Ps[p].iter_limit < 0 ? -1 : H->status;
+    st.iter = H->iter;
+    st.n_nodes = H->n_nodes;
+    st.first_solution_iter = H->first_solution_iter;
+    st.goal_key = H->goal_key;
+    st.t_start_ns = H->t_start_ns;
+    st.t_first_solution_ns = H->first_solution_iter >= 0 ? H->t_first_solution_ns : 0ull;
+    st.t_last_ns = H->t_last_ns;
+    st.t_poll_ns = globaltimer_ns();
+    BP.slots[p] = st;
+}
+
 int b_sm_count() {
     static int cached[64] = {};
     int dev = 0;
@@ -241,6 +258,11 @@ cudaError_t launch_b_append_t(const BatchParams& BP, cudaStream_t s) {
     }
 
 }  // namespace
+
+cudaError_t launch_batch_poll(const BatchParams& base, cudaStream_t s) {
+    k_b_poll<<<(base.B + 255) / 256, 256, 0, s>>>(base);
+    return cudaGetLastError();
+}
 
 // One batched iteration: begin, snapshot, propagate per class, mark, scan,
 // prefix, append per class, prune, end.

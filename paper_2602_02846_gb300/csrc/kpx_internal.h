@@ -64,7 +64,7 @@ struct DevParams {
     uint32_t seed_lo, seed_hi;
     int32_t flags, n_obs;
     int32_t va_cap;
-    int32_t pad0;
+    int32_t iter_limit;   // batch slots: iterate while iter < iter_limit (0: no limit, -1: vacant)
     int64_t slot_cap, mask_words;
     int32_t n_win_tiles, n_prune_tiles;
     // obstacle grid: cell(c, axis a) = clamp(floor((c - ws_lo[a]) * grid_inv[a]), 0, grid_n[a] - 1)
@@ -152,6 +152,15 @@ struct BatchHeader {
     uint32_t scan_ticket, prune_ticket;
 };
 
+// Per-slot summary gathered by kpx_batch_poll (mirrors kpx_slot_state).
+struct SlotState {
+    int32_t status, iter, n_nodes, first_solution_iter;
+    uint64_t goal_key;
+    // device clock (ns): first active iteration, first solution (0: none),
+    // end of the last iteration, and the poll itself
+    uint64_t t_start_ns, t_first_solution_ns, t_last_ns, t_poll_ns;
+};
+
 struct BatchParams {
     int32_t B;       // problems, ordered by class
     int32_t lo, hi;  // class range for the per-class launches
@@ -162,7 +171,10 @@ struct BatchParams {
     int64_t* scan_prefix;    // [B+1] winner-scan tiles before p
     int64_t* win_prefix;     // [B+1] winners before p
     int64_t* prune_prefix;   // [B+1] prune tiles before p
+    SlotState* slots;        // [B] poll staging
 };
+
+cudaError_t launch_batch_poll(const BatchParams& base, cudaStream_t s);
 
 cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const int* cls_kind, const int* cls_lo,
                                    const int* cls_hi, cudaStream_t s);

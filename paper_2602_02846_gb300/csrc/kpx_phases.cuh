@@ -93,13 +93,23 @@ __device__ __forceinline__ int begin_lambda(const DevParams& P, int count_A) {
 }
 
 // one thread per problem
+__device__ __forceinline__ bool problem_runs(const DevParams& P, const kpx_device_header* H) {
+    return H->status == KPX_OK && P.iter_limit >= 0 && (P.iter_limit == 0 || H->iter < P.iter_limit);
+}
+
 __device__ __forceinline__ void begin_counters(const DevParams& P) {
     kpx_device_header* H = P.hdr;
-    const bool active = H->status == KPX_OK;
+    if (!problem_runs(P, H)) {
+        // a stopped (tree full) or idle planner is a no-op: its header stays
+        // as its last iteration left it
+        H->active = 0;
+        H->n_slots = 0;
+        return;
+    }
     const int lam = begin_lambda(P, H->count_A);
-    H->active = active ? 1 : 0;
+    H->active = 1;
     H->lambda = lam;
-    H->n_slots = active ? (int64_t)H->count_A * lam : 0;
+    H->n_slots = (int64_t)H->count_A * lam;
     H->prop_ticket = 0ull;
     H->win_ticket = 0u;
     H->prune_ticket = 0u;
@@ -108,11 +118,9 @@ __device__ __forceinline__ void begin_counters(const DevParams& P) {
     H->count_A_next = 0;
     H->last_valid = 0ull;
     H->n_active = H->n_inactive = H->n_terminal = 0;
-    if (active) {
-        H->epoch = (H->epoch + 1) & 0x3FFFFFFF;
-        if (H->epoch == 0) H->epoch = 1;
-        if (H->t_start_ns == 0ull) H->t_start_ns = globaltimer_ns();
-    }
+    H->epoch = (H->epoch + 1) & 0x3FFFFFFF;
+    if (H->epoch == 0) H->epoch = 1;
+    if (H->t_start_ns == 0ull) H->t_start_ns = globaltimer_ns();
 }
 
 // The capacity rule can only trigger when the largest possible number of
@@ -120,7 +128,7 @@ __device__ __forceinline__ void begin_counters(const DevParams& P) {
 // Computed from counters that begin_counters does not write.
 __device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P) {
     const kpx_device_header* H = P.hdr;
-    if (H->status != KPX_OK) return false;
+    if (!problem_runs(P, H)) return false;
     const int64_t n_slots = (int64_t)H->count_A * begin_lambda(P, H->count_A);
     const int64_t max_new = n_slots < P.R ? n_slots : P.R;
     return (int64_t)H->n_nodes + max_new > P.N;

@@ -386,25 +386,37 @@ def obstacle_volume_fraction(obstacles: np.ndarray, res: float = 0.005) -> float
     return float(occ.mean())
 
 
+def mixed_problem(rng: np.random.Generator, kind: int, iterations: int = 100) -> Problem:
+    """One problem of the batched / served mix: family ``kind`` (0 double
+    integrator on the 16^3 x 2^3 grid, 1 Dubins airplane, 2 quadcopter),
+    10-1,000 seeded boxes (walls plus clutter for the quadcopter), tree
+    capacity 2^14..2^20 (log-uniform), the family's region grid and lambda.
+    Quadcopter buildings are not voxel-certified here (generation time)."""
+    n_obs = int(rng.integers(10, 1001))
+    cap = 1 << int(rng.integers(14, 21))
+    s = int(rng.integers(1 << 30))
+    if kind == 0:
+        return di_scene(s, n_obstacles=n_obs, tree_cap=cap, grid_pos=16, iterations=iterations)
+    if kind == 1:
+        return dubins_scene(s, n_obstacles=n_obs, tree_cap=cap, iterations=iterations)
+    return quad_scene(s, clutter=max(0, n_obs - 36), tree_cap=cap, certify=False, iterations=iterations)
+
+
 def mixed_batch(count: int = 512, seed: int = 0, iterations: int = 100) -> List[Problem]:
     """Independent problems of uneven size for batched planning: the three
-    families in turn, 10-1,000 seeded boxes each (walls plus clutter for the
-    quadcopter), tree capacities 2^14..2^20 (log-uniform), each family's
-    region grid and lambda (the double integrator on the 16^3 x 2^3 grid of
-    the paper's large-delta setting).  Quadcopter buildings are not
-    voxel-certified here (generation time)."""
+    families in turn, each drawn by mixed_problem."""
     rng = np.random.default_rng([0x5CE7E, 9, seed])
-    out = []
-    for k in range(count):
-        n_obs = int(rng.integers(10, 1001))
-        cap = 1 << int(rng.integers(14, 21))
-        s = int(rng.integers(1 << 30))
-        kind = k % 3
-        if kind == 0:
-            out.append(di_scene(s, n_obstacles=n_obs, tree_cap=cap, grid_pos=16, iterations=iterations))
-        elif kind == 1:
-            out.append(dubins_scene(s, n_obstacles=n_obs, tree_cap=cap, iterations=iterations))
-        else:
-            out.append(quad_scene(s, clutter=max(0, n_obs - 36), tree_cap=cap, certify=False,
-                                  iterations=iterations))
-    return out
+    return [mixed_problem(rng, k % 3, iterations) for k in range(count)]
+
+
+def poisson_requests(rate: float, duration: float, seed: int = 0, iterations: int = 100):
+    """A request stream for the serving loop: Poisson arrivals at ``rate``
+    per second over ``duration`` seconds, each a mixed_problem of a family
+    drawn uniformly.  Returns [(arrival_seconds, Problem)] in arrival order."""
+    rng = np.random.default_rng([0x5E27E, 11, seed])
+    out, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            return out
+        out.append((t, mixed_problem(rng, int(rng.integers(3)), iterations)))
