@@ -54,6 +54,7 @@ OPS_PER_BOX_TEST = 6.0
 SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
+FUSED_DRAM_BYTES = {}  # filled from the ncu captures of k_fused in profiles/
 PROPAGATE_DRAM_BYTES = {
     "dubins6_forest300": 34816,      # profiles/k_propagate_dubins6_forest300.md
     "quad12_building1000": 423424,   # profiles/k_propagate_quad12_building1000.md (a 95k-slot launch)
@@ -96,6 +97,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fused", action="store_true",
+                    help="run every iteration as the seven phase kernels (KPX_FLAG_NO_FUSED; same results)")
     ap.add_argument("--ttfs-seeds", type=int, default=8, help="problems (scene seeds) for time-to-first-solution")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the served request stream")
     ap.add_argument("--serve-memory-gb", type=float, default=32.0, help="device arena of the request loop")
@@ -248,8 +251,8 @@ def run_kpx(args):
     prob = spec["make"](args.seed + rank)
     iters = args.iters or prob.iterations
     stream = torch.cuda.current_stream(dev)
-    pl = kpx.Planner(prob, device=dev, stream=stream)
-    launches_per_step = 1 + 7 * iters
+    flags = kpx.KPX_FLAG_NO_FUSED if args.no_fused else 0
+    pl = kpx.Planner(prob, device=dev, stream=stream, flags=flags)
 
     # one step to learn the (deterministic) work of a step
     pl.reset()
@@ -286,6 +289,23 @@ def run_kpx(args):
     valid_all = allreduce(valid_per_step * args.steps, "sum", dev)
     value = valid_all / (ms_max / 1e3)
 
+    # launches of one step, counted graph by graph (kpx_graph_info): a graph
+    # of g iterations is 1 fused launch, plus 7 g phase launches when the
+    # fused kernel left iterations to them; 7 per iteration without graphs
+    max_g, fused = pl.graph_info()
+    plan = kpx.Planner.launch_plan(iters, max_g) if max_g else [1] * iters
+    pl.reset()
+    launches_per_step = 1  # k_init (reset)
+    graph_launches = 0
+    for g in plan:
+        pl.iterate(g)
+        if fused:
+            graph_launches += 1
+            launches_per_step += 1 + (7 * g if pl.header().graph_pending > 0 else 0)
+        else:
+            launches_per_step += 7 * g
+    fused_iters = int(pl.header().fused_iterations)
+
     # per-phase device time over one step (same launches, CUDA events on the planner's stream)
     phase_ms = [0.0] * 7
     pl.reset()
@@ -309,6 +329,14 @@ def run_kpx(args):
     peak_mhz = 2070.0
     peak = sms * FP32_LANES_PER_SM * 2 * peak_mhz * 1e6 / 1e12  # TFLOP/s
     achieved = (ops_step / max(1, iters_done)) / (prop_launch_ms / 1e3) / 1e12 if prop_ms > 0 else 0.0
+    kernel, launch_ms = "k_propagate", prop_launch_ms
+    traffic = PROPAGATE_DRAM_BYTES.get(args.workload)
+    if fused and fused_iters == iters_done and graph_launches:
+        # every iteration ran in the fused kernel: it is the step (the reset
+        # kernel aside), so its time per launch comes from the timed region
+        kernel, launch_ms = "k_fused (whole iterations, one cluster)", ms / args.steps / graph_launches
+        achieved = ops_step / (ms / args.steps / 1e3) / 1e12
+        traffic = FUSED_DRAM_BYTES.get(args.workload)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -379,15 +407,22 @@ def run_kpx(args):
                        "integration_steps_per_step": steps_per_step, "box_tests_per_step": tests_per_step,
                        "tree_nodes": int(st["n_nodes"]), "solution_cost": (None if math.isinf(st["best_cost"])
                                                                           else float(st["best_cost"]))},
-            "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0,
-                         "traffic": PROPAGATE_DRAM_BYTES.get(args.workload),
-                         "traffic_note": "DRAM bytes per propagate launch (ncu capture, profiles/); the kernel "
-                                         "is ALU/latency-bound and its working set stays in L2",
+                         "traffic": traffic,
+                         "traffic_note": "DRAM bytes per launch of this kernel (ncu capture, profiles/); the "
+                                         "kernel is ALU/latency-bound and its working set stays in L2",
                          "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
                                        % (sms, FP32_LANES_PER_SM, peak_mhz),
-                         "launch_ms": prop_launch_ms,
-                         "phase_share": {n: round(t / sum(phase_ms), 4) for n, t in zip(kpx.PHASES, phase_ms)}},
+                         "launch_ms": launch_ms,
+                         "phase_kernels": {"propagate_launch_ms": prop_launch_ms,
+                                           "propagate_achieved_tflops": (ops_step / max(1, iters_done))
+                                           / (prop_launch_ms / 1e3) / 1e12 if prop_ms > 0 else 0.0,
+                                           "phase_share": {n: round(t / sum(phase_ms), 4)
+                                                           for n, t in zip(kpx.PHASES, phase_ms)},
+                                           "note": "phase-by-phase pass over one step (kpx_debug_step)"}},
+            "launch_path": {"fused": bool(fused), "fused_iterations": fused_iters, "graph_launches": graph_launches,
+                            "max_iterations_per_graph": max_g},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

@@ -121,7 +121,11 @@ enum {
     /* Reject a candidate whose key cannot win its region before checking
      * obstacles (the collision-after-cost remark of the appendix).  Results
      * are identical; only the "valid" statistic then counts fewer rollouts. */
-    KPX_FLAG_EARLY_REJECT = 1
+    KPX_FLAG_EARLY_REJECT = 1,
+    /* Never run whole iterations in the single-launch cluster kernel (used
+     * while an iteration has at most a few thousand slots); every iteration
+     * then launches the seven phase kernels.  Results are identical. */
+    KPX_FLAG_NO_FUSED = 2
 };
 
 /* Planner hyperparameters (appendix "Hyperparameters"): tree capacity t_e,
@@ -197,6 +201,18 @@ kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, 
 /* Re-initialises the planner to its kpx_create state on the device (same
  * problem, same workspace), without host copies.  Asynchronous. */
 kpx_status kpx_reset(kpx_planner* p);
+
+/* How kpx_iterate launches (the graphs are built on first use): n
+ * iterations go out as CUDA graphs of 16, 8, 4, 2 and 1 iterations, largest
+ * first (*max_iterations_per_launch = 16; 0 when graphs are unavailable and
+ * every iteration is seven plain launches).  *fused = 1 when each graph
+ * starts with the fused single-launch kernel, which runs its iterations in
+ * one thread-block cluster while an iteration has at most one 32-slot chunk
+ * per warp of the cluster and the tree at most 32,768 nodes; the remaining
+ * iterations of that graph then run as the phase kernels.  A graph of g
+ * iterations launches 1 kernel if the header's graph_pending is 0 after it,
+ * else 1 + 7 g. */
+kpx_status kpx_graph_info(kpx_planner* p, int32_t* max_iterations_per_launch, int32_t* fused);
 
 /* Waits for the planner's stream and releases the host handle; the device
  * workspace is the caller's to free afterwards. */
@@ -326,14 +342,17 @@ typedef struct {
     int32_t n_win, n_kept, count_A_next, epoch;
     uint64_t prop_ticket;
     uint32_t win_ticket, prune_ticket;
-    int32_t n_active, n_inactive, n_terminal, pad0;
+    int32_t n_active, n_inactive, n_terminal;
+    int32_t graph_pending;     /* iterations of the current graph launch left to the phase kernels */
     uint64_t last_candidates, last_valid, last_winners;
     uint64_t total_candidates, total_valid, total_winners;
     uint64_t t_start_ns, t_first_solution_ns, t_last_ns;
-    int32_t traj_len, pad1;
+    int32_t traj_len;
+    int32_t graph_ctl;         /* internal: the fused iteration's control word */
     uint64_t total_steps;      /* integration steps executed by Propagate since create/reset */
     uint64_t total_box_tests;  /* point-in-box tests executed by Propagate since create/reset */
     uint32_t err_info[4];
+    uint64_t fused_iterations; /* iterations run by the fused single-launch kernel since create/reset */
 } kpx_device_header;
 
 /* Device addresses of the planner's arrays inside the workspace (SoA):

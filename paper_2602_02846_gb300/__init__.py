@@ -28,6 +28,7 @@ _lib = None
 KPX_OK, KPX_E_INVALID, KPX_E_NOMEM, KPX_E_CUDA = 0, 1, 2, 3
 KPX_TREE_FULL, KPX_NO_SOLUTION, KPX_E_TIMEOUT, KPX_E_INTERNAL = 4, 5, 6, 7
 KPX_FLAG_EARLY_REJECT = 1
+KPX_FLAG_NO_FUSED = 2
 PHASES = ("begin", "propagate", "mark", "scan", "append", "prune", "end")
 KEY_INF = 0xFFFFFFFFFFFFFFFF
 
@@ -35,7 +36,7 @@ EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_traject
             "kpx_destroy", "kpx_status_str", "kpx_last_error", "kpx_get_layout", "kpx_debug_step",
             "kpx_snapshot", "kpx_restore", "kpx_plan_static", "kpx_batch_workspace_size", "kpx_batch_create",
             "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error",
-            "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll")
+            "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info")
 
 
 class kpx_dynamics(C.Structure):
@@ -90,12 +91,12 @@ class kpx_device_header(C.Structure):
                 ("first_solution_iter", C.c_int32), ("n_slots", C.c_int64), ("goal_key", C.c_uint64),
                 ("n_win", C.c_int32), ("n_kept", C.c_int32), ("count_A_next", C.c_int32), ("epoch", C.c_int32),
                 ("prop_ticket", C.c_uint64), ("win_ticket", C.c_uint32), ("prune_ticket", C.c_uint32),
-                ("n_active", C.c_int32), ("n_inactive", C.c_int32), ("n_terminal", C.c_int32), ("pad0", C.c_int32),
+                ("n_active", C.c_int32), ("n_inactive", C.c_int32), ("n_terminal", C.c_int32), ("graph_pending", C.c_int32),
                 ("last_candidates", C.c_uint64), ("last_valid", C.c_uint64), ("last_winners", C.c_uint64),
                 ("total_candidates", C.c_uint64), ("total_valid", C.c_uint64), ("total_winners", C.c_uint64),
                 ("t_start_ns", C.c_uint64), ("t_first_solution_ns", C.c_uint64), ("t_last_ns", C.c_uint64),
-                ("traj_len", C.c_int32), ("pad1", C.c_int32), ("total_steps", C.c_uint64),
-                ("total_box_tests", C.c_uint64), ("err_info", C.c_uint32 * 4)]
+                ("traj_len", C.c_int32), ("graph_ctl", C.c_int32), ("total_steps", C.c_uint64),
+                ("total_box_tests", C.c_uint64), ("err_info", C.c_uint32 * 4), ("fused_iterations", C.c_uint64)]
 
 
 class kpx_layout(C.Structure):
@@ -193,6 +194,8 @@ def load(path: Optional[str] = None):
         L.kpx_batch_release.restype = C.c_int
         L.kpx_batch_poll.argtypes = [vp, C.POINTER(kpx_slot_state)]
         L.kpx_batch_poll.restype = C.c_int
+        L.kpx_graph_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+        L.kpx_graph_info.restype = C.c_int
         _lib = L
         return L
 
@@ -332,6 +335,25 @@ class Planner:
 
     def reset(self):
         self._check(load().kpx_reset(self.h))
+
+    def graph_info(self):
+        """kpx_graph_info: (max iterations per graph launch, fused)."""
+        mx, fu = C.c_int32(), C.c_int32()
+        self._check(load().kpx_graph_info(self.h, C.byref(mx), C.byref(fu)))
+        return int(mx.value), bool(fu.value)
+
+    @staticmethod
+    def launch_plan(n_iters: int, max_per_launch: int = 16):
+        """Iterations per graph launch of kpx_iterate(n_iters): largest power
+        of two first (kpx_graph_info)."""
+        out, left = [], int(n_iters)
+        while left > 0 and max_per_launch > 0:
+            g = max_per_launch
+            while g > left:
+                g //= 2
+            out.append(g)
+            left -= g
+        return out
 
     def close(self):
         if getattr(self, "_borrowed", False):

@@ -17,6 +17,10 @@
 
 using namespace kpx;
 
+// kpx_iterate launches iterations as CUDA graphs of 2^k iterations,
+// k < kGraphLevels, largest first (each graph built on first use).
+constexpr int kGraphLevels = 5;
+
 struct kpx_planner {
     DevParams P;
     Layout L;
@@ -25,10 +29,10 @@ struct kpx_planner {
     size_t ws_bytes;
     std::string err;
     // iterations captured as CUDA graphs (built on first use; launched on `stream`)
-    int graph_state = 0;  // 0 not tried, 1 ready, -1 unavailable (plain launches)
+    int graph_state = 0;  // 0 not decided, 1 graphs, -1 unavailable (plain launches)
+    bool graph_fused = false;  // graphs start with the fused kernel
     cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph_one = nullptr;
-    cudaGraphExec_t graph_many = nullptr;
+    cudaGraphExec_t graphs[kGraphLevels] = {};  // graphs[k]: 2^k iterations
 };
 
 // Many problems iterated together (one launch per phase for all of them).
@@ -261,8 +265,10 @@ kpx_status read_header(kpx_planner* p, kpx_device_header* h) {
 
 constexpr int kGraphIterations = 8;
 
-cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s) {
-    cudaError_t e = launch_begin(P, s);
+// One iteration of the phase kernels.  j, n_iter: iteration j of a graph
+// launch of n_iter iterations that starts with the fused kernel (0, 0: none).
+cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s, int j = 0, int n_iter = 0) {
+    cudaError_t e = launch_begin(P, s, j, n_iter);
     if (e == cudaSuccess) e = launch_propagate(P, nullptr, s);
     if (e == cudaSuccess) e = launch_mark(P, s);
     if (e == cudaSuccess) e = launch_scan(P, s);
@@ -285,23 +291,96 @@ cudaError_t capture_iterations(kpx_planner* p, int count, cudaGraphExec_t* exec)
     return e;
 }
 
-// Builds the two iteration graphs once; on any failure the planner keeps
-// using plain launches (same kernels, same order).
+// A graph launch of `count` iterations that starts with the fused kernel
+// (kpx_fused.cu): it runs iterations while the problem is small and leaves
+// the rest (header graph_pending) to the phase kernels, captured into the
+// body of a conditional node that runs only when the fused kernel sets its
+// handle.  Iteration j of the body runs only if j >= count - graph_pending.
+cudaError_t capture_fused_iterations(kpx_planner* p, int count, cudaGraphExec_t* exec) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h = 0;
+    cudaGraphNode_t fused_node = nullptr, cond_node = nullptr;
+    cudaError_t le = cudaSuccess;
+    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(p->capture_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        le = launch_fused(p->P, count, h, 1, p->capture_stream);
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(p->capture_stream, &out);
+        if (le != cudaSuccess) e = le;
+    }
+    size_t n_nodes = 1;
+    if (e == cudaSuccess) e = cudaGraphGetNodes(g, &fused_node, &n_nodes);  // the fused kernel: the only node
+    if (e == cudaSuccess && n_nodes != 1) e = cudaErrorUnknown;
+    cudaGraphNodeParams cp = {};
+    if (e == cudaSuccess) {
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = h;
+        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.size = 1;
+        e = cudaGraphAddNode(&cond_node, g, &fused_node, nullptr, 1, &cp);
+    }
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(p->capture_stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            for (int j = 0; j < count && le == cudaSuccess; ++j)
+                le = enqueue_iteration(p->P, p->capture_stream, j, count);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(p->capture_stream, &out);
+            if (le != cudaSuccess) e = le;
+        }
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+void drop_graphs(kpx_planner* p) {
+    for (int k = 0; k < kGraphLevels; ++k) {
+        if (p->graphs[k]) cudaGraphExecDestroy(p->graphs[k]);
+        p->graphs[k] = nullptr;
+    }
+}
+
+// Decides once how kpx_iterate launches: graphs that start with the fused
+// kernel when the device can run its cluster (and KPX_FLAG_NO_FUSED is
+// clear), else graphs of the phase kernels alone; plain launches (same
+// kernels, same order) when no graph can be made.
 void ensure_graphs(kpx_planner* p) {
     if (p->graph_state != 0) return;
     p->graph_state = -1;
     prepare_launches(p->P);
-    if (cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    p->graph_fused = !(p->P.flags & KPX_FLAG_NO_FUSED) && fused_cluster_size(p->P) > 0;
+    cudaGetLastError();
+    if (!p->capture_stream && cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         p->capture_stream = nullptr;
         return;
     }
-    if (capture_iterations(p, 1, &p->graph_one) == cudaSuccess &&
-        capture_iterations(p, kGraphIterations, &p->graph_many) == cudaSuccess) {
-        p->graph_state = 1;
-        return;
+    p->graph_state = 1;
+}
+
+// The graph of 2^k iterations, built on first use (nullptr: none can be
+// made; the planner falls back to plain launches).
+cudaGraphExec_t get_graph(kpx_planner* p, int k) {
+    if (p->graphs[k]) return p->graphs[k];
+    if (p->graph_fused) {
+        if (capture_fused_iterations(p, 1 << k, &p->graphs[k]) == cudaSuccess) return p->graphs[k];
+        cudaGetLastError();
+        p->graphs[k] = nullptr;
+        drop_graphs(p);  // the fused form is unavailable: every graph uses the phase kernels
+        p->graph_fused = false;
     }
+    if (capture_iterations(p, 1 << k, &p->graphs[k]) == cudaSuccess) return p->graphs[k];
     cudaGetLastError();
+    p->graphs[k] = nullptr;
+    p->graph_state = -1;
+    return nullptr;
 }
 
 kpx_status run_phase(kpx_planner* p, int phase, const kpx_debug_records* rec) {
@@ -461,9 +540,7 @@ size_t batch_header_bytes(int B) {
 }
 
 void drop_member_graphs(kpx_planner* p) {
-    if (p->graph_one) cudaGraphExecDestroy(p->graph_one);
-    if (p->graph_many) cudaGraphExecDestroy(p->graph_many);
-    p->graph_one = p->graph_many = nullptr;
+    drop_graphs(p);
     p->graph_state = 0;
 }
 
@@ -529,12 +606,14 @@ kpx_status kpx_iterate(kpx_planner* p, int32_t n_iters, kpx_iter_stats* out_last
     if (n_iters < 0) return fail(p, KPX_E_INVALID, "n_iters must be >= 0");
     if (n_iters > 0) ensure_graphs(p);
     int32_t it = 0;
-    if (p->graph_state == 1) {
-        cudaError_t e = cudaSuccess;
-        for (; e == cudaSuccess && it + kGraphIterations <= n_iters; it += kGraphIterations)
-            e = cudaGraphLaunch(p->graph_many, p->stream);
-        for (; e == cudaSuccess && it < n_iters; ++it) e = cudaGraphLaunch(p->graph_one, p->stream);
+    while (p->graph_state == 1 && it < n_iters) {
+        int k = kGraphLevels - 1;
+        while ((1 << k) > n_iters - it) --k;
+        cudaGraphExec_t g = get_graph(p, k);
+        if (!g) break;  // plain launches for the rest
+        cudaError_t e = cudaGraphLaunch(g, p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+        it += 1 << k;
     }
     for (; it < n_iters; ++it) {
         cudaError_t e = enqueue_iteration(p->P, p->stream);
@@ -623,6 +702,14 @@ kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, 
     return KPX_OK;
 }
 
+kpx_status kpx_graph_info(kpx_planner* p, int32_t* max_iterations_per_launch, int32_t* fused) {
+    if (!p || !max_iterations_per_launch || !fused) return KPX_E_INVALID;
+    ensure_graphs(p);
+    *max_iterations_per_launch = p->graph_state == 1 ? (1 << (kGraphLevels - 1)) : 0;
+    *fused = p->graph_state == 1 && p->graph_fused ? 1 : 0;
+    return KPX_OK;
+}
+
 kpx_status kpx_reset(kpx_planner* p) {
     if (!p) return KPX_E_INVALID;
     cudaError_t e = launch_init(p->P, false, p->stream);
@@ -633,8 +720,7 @@ kpx_status kpx_reset(kpx_planner* p) {
 kpx_status kpx_destroy(kpx_planner* p) {
     if (!p) return KPX_OK;
     cudaError_t e = cudaStreamSynchronize(p->stream);
-    if (p->graph_one) cudaGraphExecDestroy(p->graph_one);
-    if (p->graph_many) cudaGraphExecDestroy(p->graph_many);
+    drop_graphs(p);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     delete p;
     return e == cudaSuccess ? KPX_OK : KPX_E_CUDA;

@@ -378,7 +378,7 @@ struct LaneRollout {
     float len, cost0;
     int K, k, node;
 
-    __device__ __forceinline__ void start(const DevParams& P, const int32_t* __restrict__ va, int lam, uint32_t iter,
+    __device__ __forceinline__ void start(const DevParams& P, const int32_t* va, int lam, uint32_t iter,
                                           int64_t slot) {
         const int j = (int)(slot / lam);
         const int s = (int)(slot - (int64_t)j * lam);

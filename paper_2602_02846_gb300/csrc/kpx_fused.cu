@@ -1,0 +1,214 @@
+// kpx_fused.cu -- whole Kino-PAX+ iterations in one launch while the problem
+// is small.
+//
+// With a few thousand slots per iteration, the seven phase kernels are
+// bound by launch and dependency latency rather than by work: every kernel
+// boundary costs a few microseconds, while the iteration's rollouts need a
+// few in total.  This kernel runs whole iterations inside one thread-block
+// cluster (up to 16 CTAs on 16 SMs).  A hardware cluster barrier
+// (barrier.cluster, release/acquire) stands where the phase kernels have a
+// kernel boundary, and the kernel loops over the iterations of one graph
+// launch on the device.  Every unit of work is the function the phase kernels
+// call (kpx_phases.cuh), so the results are bit-identical to theirs.
+//
+// Before each iteration the leader thread checks that the iteration fits: at
+// most one 32-slot chunk per warp, and a tree of at most FUSED_MAX_NODES
+// nodes.  When it does not fit, the kernel stops and leaves the number of
+// iterations still owed to this graph launch in the header (graph_pending).
+// It then sets the graph's conditional handle, so that the phase kernels run
+// them (see capture_fused_iterations in kpx_api.cu).
+#include <cuda_runtime.h>
+
+#include "kpx_phases.cuh"
+
+namespace kpx {
+
+namespace {
+
+constexpr int FUSED_THREADS = 256;  // = WIN_THREADS = PRUNE_THREADS (block-wide units)
+constexpr int FUSED_MAX_CLUSTER = 16;
+constexpr int FUSED_MAX_NODES = 32768;
+static_assert(FUSED_THREADS == WIN_THREADS && FUSED_THREADS == PRUNE_THREADS, "block-wide units");
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(volatile const int32_t*)p; }
+
+// Leader only: decide whether the next iteration runs here; if so, begin it.
+// remaining: iterations this graph launch still owes (including this one).
+__device__ __forceinline__ void fused_begin(const DevParams& P, kpx_device_header* H, int remaining,
+                                            int64_t max_slots) {
+    int ctl = 0;
+    if (remaining <= 0 || !problem_runs(P, H)) {
+        H->graph_pending = 0;  // done, or every further iteration is a no-op
+    } else {
+        const int64_t n_slots = (int64_t)H->count_A * begin_lambda(P, H->count_A);
+        if (n_slots > max_slots || H->n_nodes > FUSED_MAX_NODES) {
+            H->graph_pending = remaining;  // too large: the phase kernels take over
+        } else {
+            ctl = 1 | (begin_needs_snapshot(P) ? 2 : 0);
+            begin_counters(P);
+        }
+    }
+    H->graph_ctl = ctl;
+}
+
+template <int DYN, int INTEG>
+__global__ void __launch_bounds__(FUSED_THREADS, 1)
+    k_fused(DevParams P, int n_iter, cudaGraphConditionalHandle handle, int use_handle) {
+    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_warp[FUSED_THREADS / 32];
+    __shared__ int32_t s_parent[PRUNE_TILE];
+    __shared__ uint8_t s_set[PRUNE_TILE];
+    (void)s_tile;
+    kpx_device_header* H = P.hdr;
+    const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
+    const int n_cta = (int)gridDim.x;  // the grid is one cluster
+    const int64_t gtid = (int64_t)blockIdx.x * FUSED_THREADS + threadIdx.x;
+    const int64_t gthreads = (int64_t)n_cta * FUSED_THREADS;
+    const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) != 0;
+    const kpx_debug_records no_rec{};
+    if (leader) fused_begin(P, H, n_iter, gthreads);
+    int done = 0;
+    for (;;) {
+        cluster_barrier();
+        const int ctl = ld_volatile_i32(&H->graph_ctl);
+        if (!(ctl & 1)) break;
+        // this iteration's parameters, written by the leader before the barrier
+        const int64_t n_slots = H->n_slots;
+        const int lam = H->lambda;
+        const uint32_t iter = (uint32_t)H->iter;
+        const int32_t* va = va_current(P, H);
+        if (ctl & 2) {  // region snapshot for the capacity rule
+            for (int64_t r = gtid; r < P.R; r += gthreads) P.region_snap[r] = P.region_key[r];
+            cluster_barrier();
+        }
+        // propagate (Alg. 2): one chunk per warp, warp-major across the CTAs
+        {
+            uint32_t steps = 0, tests = 0, n_valid = 0;
+            const int64_t chunk = (int64_t)(threadIdx.x >> 5) * n_cta + blockIdx.x;
+            if (chunk * 32 < n_slots)
+                propagate_chunk<DYN, INTEG>(P, n_slots, lam, iter, va, early, chunk, no_rec, 0, steps, tests,
+                                            n_valid);
+            flush_propagate_counters(H, steps, tests, n_valid);
+        }
+        cluster_barrier();
+        // mark
+        for (int64_t r = gtid; r < P.R; r += gthreads) mark_region(P, (int)r);
+        cluster_barrier();
+        // scan: tiles in CTA order (every CTA of the cluster is resident, so
+        // each look-back wait ends)
+        {
+            const int64_t live_words = (n_slots + 31) / 32;
+            const int64_t n_tiles = (live_words + WIN_TILE_WORDS - 1) / WIN_TILE_WORDS;
+            for (int64_t t = blockIdx.x; t < n_tiles; t += n_cta)
+                scan_tile(P, H, (uint32_t)t, n_tiles, live_words, s_warp, s_prefix);
+        }
+        cluster_barrier();
+        // append (UpdateTree) with the capacity rule
+        {
+            const int W = H->n_win;
+            const int n_old = H->n_nodes;
+            const int room = P.N - n_old;
+            const int kept = W < room ? W : room;
+            if (leader) {
+                H->n_kept = kept;
+                if (W > kept) set_status(H, KPX_TREE_FULL);
+            }
+            for (int64_t w = gtid; w < W; w += gthreads)
+                append_winner<DYN, INTEG>(P, H, (int)w, kept, n_old, lam, iter, va);
+        }
+        cluster_barrier();
+        // prune (Alg. 3) + compaction of the next V_A
+        {
+            const int n_old = H->n_nodes;
+            const int total = n_old + H->n_kept;
+            const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
+            int cA = 0, cI = 0, cT = 0;
+            for (int t = blockIdx.x; t < n_tiles; t += n_cta)
+                prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, s_parent, s_set, s_warp, s_prefix, cA, cI, cT);
+            flush_prune_counters(H, cA, cI, cT);
+        }
+        cluster_barrier();
+        ++done;
+        if (leader) {
+            end_counters(P);
+            H->fused_iterations += 1;
+            fused_begin(P, H, n_iter - done, gthreads);
+        }
+    }
+    if (leader && use_handle) cudaGraphSetConditional(handle, H->graph_pending > 0 ? 1u : 0u);
+}
+
+template <int DYN, int INTEG>
+int fused_cluster_size_t(const DevParams&, int) {
+    static int size = -1;
+    if (size < 0) {
+        size = 0;
+        if (cudaFuncSetAttribute(k_fused<DYN, INTEG>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+            cudaGetLastError();
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(FUSED_MAX_CLUSTER);
+        cfg.blockDim = dim3(FUSED_THREADS);
+        int cl = 0;
+        if (cudaOccupancyMaxPotentialClusterSize(&cl, (const void*)k_fused<DYN, INTEG>, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            cl = 0;
+        }
+        // a power of two up to 16 (the grid is one cluster)
+        int c = 1;
+        while (c * 2 <= cl && c * 2 <= FUSED_MAX_CLUSTER) c *= 2;
+        size = c >= 4 ? c : 0;
+    }
+    return size;
+}
+
+template <int DYN, int INTEG>
+cudaError_t launch_fused_t(const DevParams& P, int n_iter, cudaGraphConditionalHandle handle, int use_handle,
+                           cudaStream_t s) {
+    const int cl = fused_cluster_size_t<DYN, INTEG>(P, 0);
+    if (cl == 0) return cudaErrorNotSupported;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cl);
+    cfg.blockDim = dim3(FUSED_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_fused<DYN, INTEG>, P, n_iter, handle, use_handle);
+}
+
+#define KPX_FUSED_DISPATCH(FN, P, ...)                                                   \
+    switch ((P).dyn * 2 + (P).integ) {                                                  \
+        case KPX_DI6 * 2 + KPX_EULER: return FN<KPX_DI6, KPX_EULER>(P, __VA_ARGS__);         \
+        case KPX_DI6 * 2 + KPX_RK4: return FN<KPX_DI6, KPX_RK4>(P, __VA_ARGS__);             \
+        case KPX_DUBINS6 * 2 + KPX_EULER: return FN<KPX_DUBINS6, KPX_EULER>(P, __VA_ARGS__); \
+        case KPX_DUBINS6 * 2 + KPX_RK4: return FN<KPX_DUBINS6, KPX_RK4>(P, __VA_ARGS__);     \
+        case KPX_QUAD12 * 2 + KPX_EULER: return FN<KPX_QUAD12, KPX_EULER>(P, __VA_ARGS__);   \
+        case KPX_QUAD12 * 2 + KPX_RK4: return FN<KPX_QUAD12, KPX_RK4>(P, __VA_ARGS__);       \
+        default: break;                                                                 \
+    }
+
+}  // namespace
+
+int fused_cluster_size(const DevParams& P) {
+    KPX_FUSED_DISPATCH(fused_cluster_size_t, P, 0);
+    return 0;
+}
+
+cudaError_t launch_fused(const DevParams& P, int n_iter, cudaGraphConditionalHandle handle, int use_handle,
+                         cudaStream_t s) {
+    KPX_FUSED_DISPATCH(launch_fused_t, P, n_iter, handle, use_handle, s);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace kpx

@@ -157,9 +157,13 @@ __global__ void __launch_bounds__(1024) k_grid_scan(DevParams P) {
 // begin: branching factor, slot count, tickets; region snapshot for the
 // capacity rule (only when an overflow is possible this iteration).
 // ---------------------------------------------------------------------------
-__global__ void k_begin(DevParams P) {
-    const bool snap = begin_needs_snapshot(P);  // reads counters begin_counters leaves alone
-    if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P);
+// In a graph launch whose first iterations ran in the fused kernel
+// (n_iter > 0), iteration j of the graph runs here only if the fused kernel
+// left it: j >= n_iter - graph_pending.
+__global__ void k_begin(DevParams P, int j, int n_iter) {
+    const bool allowed = n_iter == 0 || j >= n_iter - P.hdr->graph_pending;
+    const bool snap = begin_needs_snapshot(P, allowed);  // reads counters begin_counters leaves alone
+    if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P, allowed);
     if (!snap) return;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -384,8 +388,8 @@ cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_begin(const DevParams& P, cudaStream_t s) {
-    k_begin<<<persistent_blocks((P.R + 255) / 256, 2), 256, 0, s>>>(P);
+cudaError_t launch_begin(const DevParams& P, cudaStream_t s, int j, int n_iter) {
+    k_begin<<<persistent_blocks((P.R + 255) / 256, 2), 256, 0, s>>>(P, j, n_iter);
     return cudaGetLastError();
 }
 

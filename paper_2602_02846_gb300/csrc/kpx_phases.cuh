@@ -97,9 +97,9 @@ __device__ __forceinline__ bool problem_runs(const DevParams& P, const kpx_devic
     return H->status == KPX_OK && P.iter_limit >= 0 && (P.iter_limit == 0 || H->iter < P.iter_limit);
 }
 
-__device__ __forceinline__ void begin_counters(const DevParams& P) {
+__device__ __forceinline__ void begin_counters(const DevParams& P, bool allowed = true) {
     kpx_device_header* H = P.hdr;
-    if (!problem_runs(P, H)) {
+    if (!allowed || !problem_runs(P, H)) {
         // a stopped (tree full) or idle planner is a no-op: its header stays
         // as its last iteration left it
         H->active = 0;
@@ -126,9 +126,9 @@ __device__ __forceinline__ void begin_counters(const DevParams& P) {
 // The capacity rule can only trigger when the largest possible number of
 // winners (one per region, at most one per slot) overflows the tree.
 // Computed from counters that begin_counters does not write.
-__device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P) {
+__device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P, bool allowed = true) {
     const kpx_device_header* H = P.hdr;
-    if (!problem_runs(P, H)) return false;
+    if (!allowed || !problem_runs(P, H)) return false;
     const int64_t n_slots = (int64_t)H->count_A * begin_lambda(P, H->count_A);
     const int64_t max_new = n_slots < P.R ? n_slots : P.R;
     return (int64_t)H->n_nodes + max_new > P.N;

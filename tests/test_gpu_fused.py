@@ -1,0 +1,100 @@
+"""The fused iteration (whole iterations in one cluster launch while the
+problem is small) against the phase kernels: kpx_iterate with and without
+KPX_FLAG_NO_FUSED ends bit-identical.  The cases cover problems that stay
+small, problems that outgrow the fused kernel in the middle of a graph launch
+(the phase kernels take over the remaining iterations through the
+conditional node), the capacity rule inside the fused kernel, the early cost
+rejection, and iteration counts that mix the 16-iteration and 1-iteration
+graphs."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_2602_02846_gb300 import scenes  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def kpx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2602_02846_gb300 as k
+    k.load()
+    return k
+
+
+def _state(pl):
+    a = pl.arrays()
+    h = a.pop("header")
+    a["counters"] = np.array([h.status, h.iter, h.n_nodes, h.count_A, h.first_solution_iter, h.n_active,
+                              h.n_inactive, h.n_terminal, h.lam], np.int64)
+    a["totals"] = np.array([h.total_candidates, h.total_valid, h.total_winners, h.total_steps,
+                            h.total_box_tests, h.goal_key], np.uint64)
+    a.pop("region_snap")  # scratch of the capacity rule: unwritten until a snapshot is due
+    return a
+
+
+def _same(a, b, label):
+    for k in a:
+        if isinstance(a[k], np.ndarray):
+            assert np.array_equal(np.ascontiguousarray(a[k]).view(np.uint8),
+                                  np.ascontiguousarray(b[k]).view(np.uint8)), "%s: %s differs" % (label, k)
+        else:
+            assert a[k] == b[k], "%s: %s differs" % (label, k)
+
+
+CASES = {
+    # stays small for the whole run (the confined forest airplane)
+    "dubins_forest": (lambda: scenes.dubins_scene(0), 37, 0),
+    # the literal double-integrator configuration (stalls at a few dozen nodes)
+    "di_literal": (lambda: scenes.di_scene(0), 40, 0),
+    # grows past one chunk per warp within a few iterations: the switch to
+    # the phase kernels happens inside a graph launch
+    "dubins_open_growing": (lambda: scenes.dubins_scene(3, n_obstacles=0, tree_cap=1 << 16, lam=16), 29, 0),
+    "di16_growing": (lambda: scenes.di_scene(1, grid_pos=16, tree_cap=32768), 35, 0),
+    # the tree fills inside the fused kernel: capacity rule + snapshot
+    "di_capacity": (lambda: scenes.di_scene(4, grid_pos=16, tree_cap=700), 33, 0),
+    "quad_small": (lambda: scenes.quad_scene(1, clutter=100, certify=False, tree_cap=1 << 15, lam=4), 21, 0),
+    "dubins_early_reject": (lambda: scenes.dubins_scene(2, n_obstacles=120, tree_cap=1 << 16, lam=32), 19, 1),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fused_equals_phase_kernels(kpx, case):
+    make, iters, early = CASES[case]
+    prob = make()
+    flags = kpx.KPX_FLAG_EARLY_REJECT if early else 0
+    fused = kpx.Planner(prob, flags=flags)
+    plain = kpx.Planner(prob, flags=flags | kpx.KPX_FLAG_NO_FUSED)
+    # uneven call sizes: 16-iteration graphs, 1-iteration graphs, and calls
+    # that start in the middle of the problem's growth
+    done = 0
+    for n in (3, 16, iters - 19):
+        fused.iterate(n)
+        plain.iterate(n)
+        done += n
+        _same(_state(plain), _state(fused), "%s after %d iterations" % (case, done))
+    if case == "di_capacity":
+        assert fused.header().status == kpx.KPX_TREE_FULL
+    tf, tp = fused.best_trajectory(), plain.best_trajectory()
+    assert (tf is None) == (tp is None)
+    if tf is not None:
+        assert np.array_equal(tf["states"], tp["states"]) and tf["cost"] == tp["cost"]
+    fused.close()
+    plain.close()
+
+
+def test_fused_reset_and_restore(kpx):
+    prob = scenes.di_scene(1, grid_pos=16, tree_cap=32768)
+    pl = kpx.Planner(prob)
+    pl.iterate(20)
+    ref = _state(pl)
+    snap = pl.snapshot()
+    pl.iterate(7)
+    pl.restore(snap)
+    _same(ref, _state(pl), "restore")
+    pl.reset()
+    pl.iterate(20)
+    _same(ref, _state(pl), "reset")
+    pl.close()
