@@ -54,10 +54,12 @@ OPS_PER_BOX_TEST = 6.0
 SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
-FUSED_DRAM_BYTES = {}  # filled from the ncu captures of k_fused in profiles/
+FUSED_DRAM_BYTES = {
+    "dubins6_forest300": 220160,     # profiles/k_fused_dubins6_forest300.md (one 16-iteration launch)
+}
 PROPAGATE_DRAM_BYTES = {
-    "dubins6_forest300": 34816,      # profiles/k_propagate_dubins6_forest300.md
-    "quad12_building1000": 423424,   # profiles/k_propagate_quad12_building1000.md (a 95k-slot launch)
+    "dubins6_forest300": 34816,      # profiles/k_propagate_dubins6_forest300.md (phase-kernel path)
+    "quad12_building1000": 928768,   # profiles/k_propagate_quad12_building1000.md (iteration 20)
 }
 FP32_LANES_PER_SM = 128
 
