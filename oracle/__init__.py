@@ -140,6 +140,20 @@ def _declare(L):
     L.kpo_destroy.argtypes = [vp]
     L.kpo_revalidate.argtypes = [C.POINTER(Problem), C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.kpo_revalidate.restype = C.c_int32
+    L.kpo_box_distance.argtypes = [vp, vp, vp]
+    L.kpo_box_distance.restype = C.c_double
+    L.kpo_refine_cost.argtypes = [C.POINTER(Problem), C.POINTER(Refine), vp, C.c_int32, vp, vp, vp, C.c_int32]
+    L.kpo_refine_cost.restype = C.c_double
+    L.kpo_refine_grad.argtypes = [C.POINTER(Problem), C.POINTER(Refine), vp, C.c_int32, vp, vp, vp, C.c_int32, vp]
+    L.kpo_refine_grad.restype = C.c_double
+    L.kpo_validate_controls.argtypes = [C.POINTER(Problem), vp, vp, vp, C.c_int32, vp, vp, vp, vp]
+    L.kpo_validate_controls.restype = C.c_int32
+
+
+class Refine(C.Structure):
+    """Weights of the refinement objective (kpx_oracle.h)."""
+    _fields_ = [("w_obs", C.c_double), ("beta", C.c_double), ("margin", C.c_double), ("w_goal", C.c_double),
+                ("goal", C.c_double * 3), ("w_effort", C.c_double)]
 
 
 class OracleProblem:
@@ -428,3 +442,66 @@ class Planner:
             return None
         L = int(ln[0])
         return dict(states=st[:L + 1].copy(), controls=ct[:L].copy(), steps=sp[:L].copy(), cost=float(cost[0]))
+
+
+# ---------------------------------------------------------------------------
+# refinement objective (adjoint post-pass reference)
+# ---------------------------------------------------------------------------
+def _refine_struct(spec) -> Refine:
+    r = Refine()
+    r.w_obs, r.beta, r.margin, r.w_goal = (float(spec["w_obs"]), float(spec["beta"]), float(spec["margin"]),
+                                           float(spec["w_goal"]))
+    for a in range(3):
+        r.goal[a] = float(spec["goal"][a])
+    r.w_effort = float(spec["w_effort"])
+    return r
+
+
+def box_distance(box, p):
+    """Signed distance from p to a closed box (negative inside) and its gradient."""
+    b = np.ascontiguousarray(box, dtype=np.float64)
+    q = np.ascontiguousarray(p, dtype=np.float64)
+    g = np.zeros(3)
+    d = lib().kpo_box_distance(b.ctypes.data, q.ctypes.data, g.ctypes.data)
+    return float(d), g
+
+
+def _refine_args(prob, x0, u, K, obstacles):
+    P = as_oracle(prob)
+    obs = P.obs if obstacles is None else np.ascontiguousarray(np.asarray(obstacles, np.float64).reshape(-1, 6))
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    u = np.ascontiguousarray(np.asarray(u, dtype=np.float64).reshape(-1, 4))
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    return P, obs, x0, u, K
+
+
+def refine_cost(prob, spec, x0, u, K, obstacles=None) -> float:
+    """The refinement objective J of a control sequence u[S][4] held K[s] steps."""
+    P, obs, x0, u, K = _refine_args(prob, x0, u, K, obstacles)
+    r = _refine_struct(spec)
+    return float(lib().kpo_refine_cost(P.ref, C.byref(r), obs.ctypes.data, obs.shape[0], x0.ctypes.data,
+                                       u.ctypes.data, K.ctypes.data, K.shape[0]))
+
+
+def refine_grad(prob, spec, x0, u, K, obstacles=None):
+    """(J, dJ/du[S][4]) by plain reverse mode in FP64."""
+    P, obs, x0, u, K = _refine_args(prob, x0, u, K, obstacles)
+    r = _refine_struct(spec)
+    g = np.zeros_like(u)
+    J = lib().kpo_refine_grad(P.ref, C.byref(r), obs.ctypes.data, obs.shape[0], x0.ctypes.data, u.ctypes.data,
+                              K.ctypes.data, K.shape[0], g.ctypes.data)
+    return float(J), g
+
+
+def validate_controls(prob, x0, u, K):
+    """Open-loop FP64 re-validation of FP32 controls u[S][m] from x0."""
+    P = as_oracle(prob)
+    x0 = np.ascontiguousarray(x0, dtype=np.float64)
+    uf = np.ascontiguousarray(np.asarray(u, dtype=np.float32).reshape(-1))
+    K = np.ascontiguousarray(K, dtype=np.int32)
+    mc, gd, c = np.zeros(1), np.zeros(1), np.zeros(1)
+    xe = np.zeros(P.n)
+    ok = lib().kpo_validate_controls(P.ref, x0.ctypes.data, uf.ctypes.data, K.ctypes.data, K.shape[0],
+                                     mc.ctypes.data, gd.ctypes.data, c.ctypes.data, xe.ctypes.data)
+    return dict(valid=bool(ok), min_clearance=float(mc[0]), goal_dist=float(gd[0]), cost=float(c[0]), x_end=xe)
+

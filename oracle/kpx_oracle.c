@@ -762,3 +762,255 @@ int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, 
     *openloop_err = olerr;
     return (clear >= -1e-4 && *goal_slack >= -1e-4) ? 1 : 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Refinement objective and its gradient (TEST INFRASTRUCTURE: the reference
+ * for the adjoint kernel).  The objective is defined in kpx_oracle.h.  The
+ * gradient is plain reverse mode: the forward pass keeps every state, the
+ * reverse pass walks the steps backwards through the RK4 stages with the
+ * hand-derived vector-Jacobian product of the quadcopter dynamics below.
+ * ---------------------------------------------------------------------- */
+
+/* signed distance from p to the closed box (lo, hi); grad (may be NULL)
+ * receives its gradient: (p - q)/|p - q| outside (q = nearest box point),
+ * the outward normal of the nearest face inside. */
+double kpo_box_distance(const double* box, const double* p, double* grad) {
+    double q[3], o2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        q[a] = p[a] < box[a] ? box[a] : (p[a] > box[3 + a] ? box[3 + a] : p[a]);
+        o2 += (p[a] - q[a]) * (p[a] - q[a]);
+    }
+    if (o2 > 0.0) {
+        double d = sqrt(o2);
+        if (grad)
+            for (int a = 0; a < 3; ++a) grad[a] = (p[a] - q[a]) / d;
+        return d;
+    }
+    /* inside: depth to the nearest face */
+    double best = INFINITY;
+    int axis = 0, side = 0;
+    for (int a = 0; a < 3; ++a) {
+        double dl = p[a] - box[a], dh = box[3 + a] - p[a];
+        if (dl < best) { best = dl; axis = a; side = -1; }
+        if (dh < best) { best = dh; axis = a; side = 1; }
+    }
+    if (grad) {
+        for (int a = 0; a < 3; ++a) grad[a] = 0.0;
+        grad[axis] = (double)side;
+    }
+    return -best;
+}
+
+static double softplus_b(double z, double beta) {
+    double t = beta * z;
+    return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t))) / beta;
+}
+
+static double sigmoid_b(double z, double beta) {
+    double t = beta * z;
+    if (t >= 0.0) return 1.0 / (1.0 + exp(-t));
+    double e = exp(t);
+    return e / (1.0 + e);
+}
+
+/* obstacle penalty at position p, and its gradient (added into g3) */
+static double obstacle_penalty(const kpo_refine* R, const double* obs, int32_t n_obs, const double* p, double* g3) {
+    double sum = 0.0;
+    for (int32_t b = 0; b < n_obs; ++b) {
+        double gd[3];
+        double d = kpo_box_distance(obs + 6 * b, p, g3 ? gd : NULL);
+        double z = R->margin - d;
+        sum += softplus_b(z, R->beta);
+        if (g3) {
+            double s = sigmoid_b(z, R->beta) * R->w_obs;
+            for (int a = 0; a < 3; ++a) g3[a] -= s * gd[a];
+        }
+    }
+    return R->w_obs * sum;
+}
+
+/* a^T df/dx and a^T df/du of the quadcopter dynamics (kpo_deriv), by hand */
+static void quad_vjp(const kpo_problem* P, const double* x, const double* u, const double* a, double* gx,
+                     double* gu) {
+    double mass = P->param[0];
+    double Jx = P->param[2], Jy = P->param[3], Jz = P->param[4];
+    double phi = x[3], th = x[4], psi = x[5];
+    double p = x[9], q = x[10], r = x[11];
+    double cphi = cos(phi), sphi = sin(phi);
+    double cth = cos(th), sth = sin(th), tth = tan(th);
+    double cpsi = cos(psi), spsi = sin(psi);
+    double A = u[0] / mass;
+    double r13 = cpsi * sth * cphi + spsi * sphi;
+    double r23 = spsi * sth * cphi - cpsi * sphi;
+    double r33 = cth * cphi;
+    double w = sphi * q + cphi * r; /* appears in the theta derivatives */
+    for (int i = 0; i < 12; ++i) gx[i] = 0.0;
+    /* p' = v */
+    gx[6] += a[0];
+    gx[7] += a[1];
+    gx[8] += a[2];
+    /* phi' = p + sphi tth q + cphi tth r */
+    gx[3] += a[3] * (cphi * tth * q - sphi * tth * r);
+    gx[4] += a[3] * w / (cth * cth);
+    gx[9] += a[3];
+    gx[10] += a[3] * sphi * tth;
+    gx[11] += a[3] * cphi * tth;
+    /* theta' = cphi q - sphi r */
+    gx[3] += a[4] * (-sphi * q - cphi * r);
+    gx[10] += a[4] * cphi;
+    gx[11] += a[4] * (-sphi);
+    /* psi' = (sphi q + cphi r) / cth */
+    gx[3] += a[5] * (cphi * q - sphi * r) / cth;
+    gx[4] += a[5] * w * sth / (cth * cth);
+    gx[10] += a[5] * sphi / cth;
+    gx[11] += a[5] * cphi / cth;
+    /* v' = A (r13, r23, r33) - g e3 */
+    gx[3] += A * (a[6] * (-cpsi * sth * sphi + spsi * cphi) + a[7] * (-spsi * sth * sphi - cpsi * cphi) +
+                  a[8] * (-cth * sphi));
+    gx[4] += A * (a[6] * cpsi * cth * cphi + a[7] * spsi * cth * cphi + a[8] * (-sth * cphi));
+    gx[5] += A * (a[6] * (-spsi * sth * cphi + cpsi * sphi) + a[7] * (cpsi * sth * cphi + spsi * sphi));
+    gu[0] = (a[6] * r13 + a[7] * r23 + a[8] * r33) / mass;
+    /* omega' = J^-1 (tau - omega x J omega), J diagonal */
+    gx[10] += -a[9] * (Jz - Jy) * r / Jx;
+    gx[11] += -a[9] * (Jz - Jy) * q / Jx;
+    gx[11] += -a[10] * (Jx - Jz) * p / Jy;
+    gx[9] += -a[10] * (Jx - Jz) * r / Jy;
+    gx[9] += -a[11] * (Jy - Jx) * q / Jz;
+    gx[10] += -a[11] * (Jy - Jx) * p / Jz;
+    gu[1] = a[9] / Jx;
+    gu[2] = a[10] / Jy;
+    gu[3] = a[11] / Jz;
+}
+
+static double effort_cost(const kpo_problem* P, const kpo_refine* R, const double* u, int32_t K, double* g4) {
+    double mg = P->param[0] * P->param[1], tmax = P->param[5];
+    double dur = (double)K * P->h;
+    double e = ((u[0] - mg) / mg) * ((u[0] - mg) / mg);
+    for (int i = 1; i < 4; ++i) e += (u[i] / tmax) * (u[i] / tmax);
+    if (g4) {
+        g4[0] += dur * R->w_effort * 2.0 * (u[0] - mg) / (mg * mg);
+        for (int i = 1; i < 4; ++i) g4[i] += dur * R->w_effort * 2.0 * u[i] / (tmax * tmax);
+    }
+    return dur * (1.0 + R->w_effort * e);
+}
+
+static int32_t total_steps(const int32_t* K, int32_t S) {
+    int32_t n = 0;
+    for (int32_t s = 0; s < S; ++s) n += K[s];
+    return n;
+}
+
+double kpo_refine_cost(const kpo_problem* P, const kpo_refine* R, const double* obs, int32_t n_obs,
+                       const double* x0, const double* u, const int32_t* K, int32_t S) {
+    double x[16], xn[16], J = 0.0;
+    for (int d = 0; d < 12; ++d) x[d] = x0[d];
+    for (int32_t s = 0; s < S; ++s) {
+        J += effort_cost(P, R, u + 4 * s, K[s], NULL);
+        for (int32_t k = 0; k < K[s]; ++k) {
+            kpo_step(P, x, u + 4 * s, xn);
+            for (int d = 0; d < 12; ++d) x[d] = xn[d];
+            J += obstacle_penalty(R, obs, n_obs, x, NULL);
+        }
+    }
+    for (int a = 0; a < 3; ++a) J += R->w_goal * (x[a] - R->goal[a]) * (x[a] - R->goal[a]);
+    return J;
+}
+
+double kpo_refine_grad(const kpo_problem* P, const kpo_refine* R, const double* obs, int32_t n_obs,
+                       const double* x0, const double* u, const int32_t* K, int32_t S, double* grad_u) {
+    const int32_t N = total_steps(K, S);
+    const double h = P->h;
+    double* xs = (double*)malloc((size_t)(N + 1) * 12 * sizeof(double));
+    int32_t* seg = (int32_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
+    for (int d = 0; d < 12; ++d) xs[d] = x0[d];
+    double J = 0.0;
+    int32_t k = 0;
+    for (int32_t s = 0; s < S; ++s) {
+        for (int i = 0; i < 4; ++i) grad_u[4 * s + i] = 0.0;
+        J += effort_cost(P, R, u + 4 * s, K[s], grad_u + 4 * s);
+        for (int32_t j = 0; j < K[s]; ++j, ++k) {
+            kpo_step(P, xs + 12 * k, u + 4 * s, xs + 12 * (k + 1));
+            seg[k] = s;
+            J += obstacle_penalty(R, obs, n_obs, xs + 12 * (k + 1), NULL);
+        }
+    }
+    /* adjoint of the last state: goal pull + the penalty at p_N */
+    double lam[12] = {0.0};
+    for (int a = 0; a < 3; ++a) {
+        double e = xs[12 * N + a] - R->goal[a];
+        J += R->w_goal * e * e;
+        lam[a] = 2.0 * R->w_goal * e;
+    }
+    for (k = N - 1; k >= 0; --k) {
+        const double* xk = xs + 12 * k;
+        const double* uk = u + 4 * seg[k];
+        if (k + 1 <= N) obstacle_penalty(R, obs, n_obs, xs + 12 * (k + 1), lam); /* d/dp of the penalty at p_{k+1} */
+        /* RK4 stages of step k */
+        double k1[12], k2[12], k3[12], k4[12], x2[12], x3[12], x4[12];
+        kpo_deriv(P, xk, uk, k1);
+        for (int i = 0; i < 12; ++i) x2[i] = xk[i] + 0.5 * h * k1[i];
+        kpo_deriv(P, x2, uk, k2);
+        for (int i = 0; i < 12; ++i) x3[i] = xk[i] + 0.5 * h * k2[i];
+        kpo_deriv(P, x3, uk, k3);
+        for (int i = 0; i < 12; ++i) x4[i] = xk[i] + h * k3[i];
+        kpo_deriv(P, x4, uk, k4);
+        (void)k4;
+        /* x_{k+1} = x_k + h/6 (k1 + 2 k2 + 2 k3 + k4): adjoints of the stage derivatives */
+        double ak1[12], ak2[12], ak3[12], ak4[12], g[12], gu[4], ax[12];
+        for (int i = 0; i < 12; ++i) {
+            ak1[i] = h / 6.0 * lam[i];
+            ak2[i] = h / 3.0 * lam[i];
+            ak3[i] = h / 3.0 * lam[i];
+            ak4[i] = h / 6.0 * lam[i];
+            ax[i] = lam[i];
+        }
+        double* gus = grad_u + 4 * seg[k];
+        /* k4 = f(x4), x4 = x_k + h k3 */
+        quad_vjp(P, x4, uk, ak4, g, gu);
+        for (int i = 0; i < 12; ++i) { ak3[i] += h * g[i]; ax[i] += g[i]; }
+        for (int i = 0; i < 4; ++i) gus[i] += gu[i];
+        /* k3 = f(x3), x3 = x_k + h/2 k2 */
+        quad_vjp(P, x3, uk, ak3, g, gu);
+        for (int i = 0; i < 12; ++i) { ak2[i] += 0.5 * h * g[i]; ax[i] += g[i]; }
+        for (int i = 0; i < 4; ++i) gus[i] += gu[i];
+        /* k2 = f(x2), x2 = x_k + h/2 k1 */
+        quad_vjp(P, x2, uk, ak2, g, gu);
+        for (int i = 0; i < 12; ++i) { ak1[i] += 0.5 * h * g[i]; ax[i] += g[i]; }
+        for (int i = 0; i < 4; ++i) gus[i] += gu[i];
+        /* k1 = f(x_k) */
+        quad_vjp(P, xk, uk, ak1, g, gu);
+        for (int i = 0; i < 12; ++i) ax[i] += g[i];
+        for (int i = 0; i < 4; ++i) gus[i] += gu[i];
+        for (int i = 0; i < 12; ++i) lam[i] = ax[i];
+    }
+    free(xs);
+    free(seg);
+    return J;
+}
+
+int32_t kpo_validate_controls(const kpo_problem* P, const double* x0, const float* u, const int32_t* K,
+                              int32_t S, double* min_clearance, double* goal_dist, double* cost,
+                              double* x_end) {
+    const int n = P->n;
+    double x[16], xn[16], ud[8], clear = INFINITY, total = 0.0;
+    int32_t ok = 1;
+    for (int d = 0; d < n; ++d) x[d] = x0[d];
+    for (int32_t s = 0; s < S; ++s) {
+        for (int d = 0; d < P->m; ++d) ud[d] = u[(int64_t)s * P->m + d];
+        total += (double)K[s] * P->h * (1.0 + P->w_effort * effort(P, ud));
+        for (int32_t k = 0; k < K[s]; ++k) {
+            kpo_step(P, x, ud, xn);
+            for (int d = 0; d < n; ++d) x[d] = xn[d];
+            if (!kpo_point_valid(P, x)) ok = 0;
+            clear = fmin(clear, kpo_point_clearance(P, x));
+        }
+    }
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) d2 += (x[a] - P->goal_c[a]) * (x[a] - P->goal_c[a]);
+    *min_clearance = clear;
+    *goal_dist = sqrt(d2);
+    *cost = total;
+    for (int d = 0; d < n; ++d) x_end[d] = x[d];
+    return (ok && sqrt(d2) <= P->goal_r) ? 1 : 0;
+}
+

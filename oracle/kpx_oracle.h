@@ -151,6 +151,32 @@ int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, 
                        const int32_t* steps, double* max_seg_err, double* min_clearance,
                        double* goal_slack, double* cost, double* openloop_err);
 
+/* ------------------------------------------------------------------------
+ * Refinement objective of a control sequence (the adjoint post-pass; the
+ * paper has no refinement, so the objective is a reading):
+ *   J = sum_s K_s h (1 + w_effort e(u_s))                     effort + duration
+ *     + w_obs sum_{k=1..N} sum_b sp(margin - d_b(p_k))        obstacle penalty
+ *     + w_goal |p_N - goal|^2                                  goal pull
+ * sp(z) = log(1 + exp(beta z)) / beta; d_b = signed distance from the
+ * position p_k after RK4 step k to box b (negative inside); N = sum_s K_s.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double w_obs, beta, margin, w_goal;
+    double goal[3];
+    double w_effort;
+} kpo_refine;
+
+double kpo_box_distance(const double* box, const double* p, double* grad);
+double kpo_refine_cost(const kpo_problem* P, const kpo_refine* R, const double* obs, int32_t n_obs,
+                       const double* x0, const double* u, const int32_t* K, int32_t S);
+double kpo_refine_grad(const kpo_problem* P, const kpo_refine* R, const double* obs, int32_t n_obs,
+                       const double* x0, const double* u, const int32_t* K, int32_t S, double* grad_u);
+/* Open-loop FP64 re-validation of a control sequence from x0: 1 when every
+ * point after a step is valid and the last position lies in the goal ball. */
+int32_t kpo_validate_controls(const kpo_problem* P, const double* x0, const float* u, const int32_t* K,
+                              int32_t S, double* min_clearance, double* goal_dist, double* cost,
+                              double* x_end);
+
 #ifdef __cplusplus
 }
 #endif

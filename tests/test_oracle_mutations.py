@@ -14,6 +14,7 @@ import oracle
 
 from tests import test_oracle_dynamics as dyn
 from tests import test_oracle_geometry as geo
+from tests import test_oracle_refine as ref
 from tests import test_oracle_sampling as smp
 from tests import test_oracle_steps as stp
 
@@ -76,6 +77,29 @@ MUTATIONS = [
      "for (int32_t p = parent[i]; p >= 0; p = -1) {", [stp.test_prune_ancestor_chain_is_strict_and_reaches_root]),
     ("compact_off_by_one", "if (mask[i]) I[acc++] = i;", "if (mask[i] && i + 1 < n) I[acc++] = i;",
      [stp.test_compaction_paper_example]),
+    # refinement objective and its reverse-mode gradient
+    ("box_inside_sign", "return -best;", "return best;", [ref.test_box_distance_hand_values]),
+    ("box_outside_norm", "grad[a] = (p[a] - q[a]) / d;", "grad[a] = (p[a] - q[a]);",
+     [ref.test_box_distance_hand_values]),
+    ("vjp_phi_row1_sign", "gx[3] += a[3] * (cphi * tth * q - sphi * tth * r);",
+     "gx[3] += a[3] * (cphi * tth * q + sphi * tth * r);", [ref.test_gradient_matches_central_differences]),
+    ("vjp_thrust_column", "gu[0] = (a[6] * r13 + a[7] * r23 + a[8] * r33) / mass;",
+     "gu[0] = (a[6] * r13 + a[7] * r23 + a[8] * r13) / mass;", [ref.test_thrust_gradient_at_hover_closed_form]),
+    ("vjp_torque_index", "gu[3] = a[11] / Jz;", "gu[3] = a[10] / Jz;", [ref.test_gradient_matches_central_differences]),
+    ("vjp_gyro_drop", "gx[9] += -a[11] * (Jy - Jx) * q / Jz;", "(void)0;",
+     [ref.test_gradient_matches_central_differences]),
+    ("rk4_adjoint_weight", "ak2[i] = h / 3.0 * lam[i];", "ak2[i] = h / 6.0 * lam[i];",
+     [ref.test_gradient_matches_central_differences, ref.test_thrust_gradient_at_hover_closed_form]),
+    ("rk4_adjoint_stage", "ak3[i] += h * g[i];", "ak3[i] += 0.5 * h * g[i];",
+     [ref.test_gradient_matches_central_differences]),
+    ("penalty_grad_sign", "g3[a] -= s * gd[a];", "g3[a] += s * gd[a];", [ref.test_gradient_matches_central_differences]),
+    ("effort_grad_factor", "g4[0] += dur * R->w_effort * 2.0 * (u[0] - mg) / (mg * mg);",
+     "g4[0] += dur * R->w_effort * (u[0] - mg) / (mg * mg);", [ref.test_effort_cost_and_gradient_closed_form]),
+    ("goal_grad_factor", "lam[a] = 2.0 * R->w_goal * e;", "lam[a] = R->w_goal * e;",
+     [ref.test_thrust_gradient_at_hover_closed_form]),
+    ("softplus_scale", "return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t))) / beta;",
+     "return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t)));", [ref.test_penalty_value_by_hand]),
+    ("validate_no_check", "if (!kpo_point_valid(P, x)) ok = 0;", "(void)0;", [ref.test_validate_controls]),
 ]
 
 
