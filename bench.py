@@ -83,6 +83,18 @@ SERVE_WORKLOADS = {
                                               "mixed-batch problem mix, admitted by device memory into per-class "
                                               "slots, iterations of all resident queries batched"),
 }
+REFINE_WORKLOADS = {
+    "refine_quad4096": dict(count=4096, desc="adjoint refinement post-pass: 4,096 12D-quadcopter control sequences "
+                                             "of 64-512 segments (10-60 RK4 steps each) among the 1,000-box "
+                                             "building; one step = the objective and its gradient (forward with "
+                                             "checkpoints every 32 steps + adjoint) for every sequence"),
+}
+# algorithmic FP32 work of the refinement objective and gradient (an FMA
+# counts 2, a transcendental 1): per RK4 step and per box at each step
+REFINE_OPS_RK4_STEP = 328.0        # 4 derivative evaluations (6 sin/cos + ~40 flops) + stage updates
+REFINE_OPS_RK4_ADJOINT = 794.0     # 3 derivative + 4 vector-Jacobian evaluations + stage adjoints
+REFINE_OPS_BOX_PENALTY = 22.0      # signed distance + softplus
+REFINE_OPS_BOX_GRADIENT = 29.0     # signed distance + its gradient + sigmoid
 DEFAULT_WORKLOAD = "dubins6_forest300"
 
 
@@ -92,8 +104,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("kpx", "reference"), default="kpx")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS),
-                    default=DEFAULT_WORKLOAD)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(SERVE_WORKLOADS)
+                    + sorted(REFINE_WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--iters", type=int, default=0, help="planner iterations per step (0 = the config's)")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
@@ -208,9 +220,36 @@ def oracle_sample(prob, iters, budget_s):
     return dict(valid=int(st["total_valid"]), candidates=int(st["total_candidates"]), iters=done, seconds=dt)
 
 
+def refine_oracle_sample(batch, budget_s):
+    """The FP64 oracle's objective + gradient on whole trajectories of the
+    refinement batch, in order, until the budget is spent."""
+    import oracle
+    oracle.build()
+    from paper_2602_02846_gb300 import refine
+    prob = batch["problem"]
+    spec = refine.default_cost(prob)
+    t0 = time.perf_counter()
+    done = steps = 0
+    while done < batch["u"].shape[0]:
+        n = int(batch["n_seg"][done])
+        oracle.refine_grad(prob, spec, batch["x0"][done].astype(np.float64), batch["u"][done, :n].astype(np.float64),
+                           batch["steps"][done, :n], obstacles=batch["obstacles"].astype(np.float64))
+        steps += int(batch["steps"][done, :n].sum())
+        done += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return dict(trajectories=done, steps=steps, seconds=time.perf_counter() - t0)
+
+
 def run_reference(args):
     world, rank, local = dist_setup("gloo")
     if rank != 0:
+        return 0
+    if args.workload in REFINE_WORKLOADS:
+        return run_refine_reference(args)
+    if args.workload not in WORKLOADS:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm times the single-problem and "
+                          "refinement workloads; %s has no oracle leg" % args.workload}))
         return 0
     spec = WORKLOADS[args.workload]
     prob = spec["make"](args.seed)
@@ -658,6 +697,144 @@ def run_serve(args):
     return 0
 
 
+def run_refine_reference(args):
+    spec = REFINE_WORKLOADS[args.workload]
+    batch = scenes.refine_batch(spec["count"], seed=args.seed)
+    budget = max(1.0, args.cpu_seconds / max(1, args.steps))
+    refine_oracle_sample(batch, 0.1)
+    trajs = steps = 0
+    secs = 0.0
+    for _ in range(args.steps):
+        r = refine_oracle_sample(batch, budget)
+        trajs += r["trajectories"]
+        steps += r["steps"]
+        secs += r["seconds"]
+    value = trajs / secs if secs > 0 else 0.0
+    unit = "trajectory gradients/s"
+    line = {
+        "impl": "reference", "metric": "trajectory gradients/s", "value": value, "unit": unit, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": spec["desc"], "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": 1, "kind": "oracle",
+                         "sample": "%d whole trajectories (%d RK4 steps) of the batch, FP64 objective + reverse-mode "
+                                   "gradient, single-threaded C" % (trajs, steps)},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_refine(args):
+    """Objective + adjoint gradient of 4,096 control sequences per step."""
+    import torch
+    world, rank, local = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2602_02846_gb300 as kpx
+    from paper_2602_02846_gb300 import refine
+    kpx.load()
+    spec = REFINE_WORKLOADS[args.workload]
+    data = scenes.refine_batch(spec["count"], seed=args.seed + 1000 * rank)
+    prob = data["problem"]
+    batch = refine.Batch(prob, data["x0"], data["u"], data["steps"], data["n_seg"], obstacles=data["obstacles"],
+                         device=dev)
+    cost = refine.default_cost(prob)
+    stream = torch.cuda.current_stream(dev)
+    n_steps = int(data["steps"].sum())
+    M = int(data["obstacles"].shape[0])
+    for _ in range(args.warmup):
+        refine.evaluate(batch, cost, grad=True)
+    torch.cuda.synchronize(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize(dev)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        J, g = refine.evaluate(batch, cost, grad=True)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    clk = clocks.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev)
+    finite = bool(torch.isfinite(J).all().item() and torch.isfinite(g).all().item())
+    ms_max = allreduce(ms, "max", dev)
+    value = allreduce(spec["count"] * args.steps, "sum", dev) / (ms_max / 1e3)
+    # the forward and the backward kernels timed apart (same launches)
+    a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    flush.zero_()
+    a.record(stream)
+    refine.evaluate(batch, cost)
+    b.record(stream)
+    refine.evaluate(batch, cost, grad=True)
+    c.record(stream)
+    torch.cuda.synchronize(dev)
+    fwd_ms, both_ms = a.elapsed_time(b), b.elapsed_time(c)
+    ops = n_steps * (2 * REFINE_OPS_RK4_STEP + REFINE_OPS_RK4_ADJOINT
+                     + M * (REFINE_OPS_BOX_PENALTY + REFINE_OPS_BOX_GRADIENT))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
+    peak = sms * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
+    achieved = ops / (ms / args.steps / 1e3) / 1e12
+    # end to end: controls, start states and step counts from pinned host
+    # memory, objective and gradient back to the host
+    e2e = None
+    if not args.no_e2e:
+        hu = torch.from_numpy(data["u"]).pin_memory()
+        hx = torch.from_numpy(data["x0"]).pin_memory()
+        hs = torch.from_numpy(data["steps"]).pin_memory()
+        hJ = torch.empty(spec["count"], dtype=torch.float32).pin_memory()
+        hg = torch.empty_like(hu).pin_memory()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            batch.u.copy_(hu, non_blocking=True)
+            batch.x0.copy_(hx, non_blocking=True)
+            batch.steps.copy_(hs, non_blocking=True)
+            J, g = refine.evaluate(batch, cost, grad=True)
+            hJ.copy_(J, non_blocking=True)
+            hg.copy_(g, non_blocking=True)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        e2e = {"value": allreduce(spec["count"] * args.steps, "sum", dev) / allreduce(wall, "max", dev),
+               "unit": "trajectory gradients/s",
+               "h2d_bytes_per_step": int(hu.numel() * 4 + hx.numel() * 4 + hs.numel() * 4),
+               "d2h_bytes_per_step": int(hJ.numel() * 4 + hg.numel() * 4)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = refine_oracle_sample(data, args.cpu_seconds)
+        cpu = {"value": r["trajectories"] / r["seconds"], "unit": "trajectory gradients/s", "cores": 1,
+               "kind": "oracle", "sample": "the first %d trajectories (%d RK4 steps) of the batch, FP64 objective "
+                                           "+ reverse-mode gradient, single-threaded C (%.1f s)"
+                                           % (r["trajectories"], r["steps"], r["seconds"])}
+    if rank == 0:
+        line = {
+            "metric": "trajectory gradients/s", "value": value, "unit": "trajectory gradients/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": spec["desc"], "trajectories": spec["count"],
+                       "rk4_steps_per_step": n_steps, "boxes": M, "seed": args.seed,
+                       "l2": "flushed between steps (256 MB write)", "all_finite": finite},
+            "roofline": {"bound": "alu", "kernel": "k_refine_forward<true> + k_refine_backward (one step)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "ops_note": "per RK4 step: forward %.0f + recomputation %.0f + adjoint %.0f, plus %.0f per "
+                                     "box (penalty %.0f + gradient %.0f)"
+                                     % (REFINE_OPS_RK4_STEP, REFINE_OPS_RK4_STEP, REFINE_OPS_RK4_ADJOINT,
+                                        REFINE_OPS_BOX_PENALTY + REFINE_OPS_BOX_GRADIENT, REFINE_OPS_BOX_PENALTY,
+                                        REFINE_OPS_BOX_GRADIENT),
+                         "peak_basis": "%d SMs x %d FP32 lanes x 2 x 2070 MHz (max SM clock)"
+                                       % (sms, FP32_LANES_PER_SM),
+                         "forward_only_ms": fwd_ms, "forward_and_backward_ms": both_ms},
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+            "gpu_launches": 2 * args.steps,
+        }
+        print(json.dumps(line))
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
@@ -666,6 +843,8 @@ def main(argv=None):
         return run_batch(args)
     if args.workload in SERVE_WORKLOADS:
         return run_serve(args)
+    if args.workload in REFINE_WORKLOADS:
+        return run_refine(args)
     return run_kpx(args)
 
 

@@ -330,6 +330,81 @@ kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspace* ws, con
                            int32_t* steps, int32_t* out_len, float* out_cost);
 
 /* ------------------------------------------------------------------------
+ * Trajectory refinement (an optional post-pass over returned trajectories;
+ * the paper has none, and the planner never calls it).  For the 12D
+ * quadcopter with RK4 only (else KPX_E_INVALID).
+ *
+ * A trajectory is a control sequence u[s] (thrust, 3 torques) held for
+ * steps[s] RK4 steps each, s < n_segments, from the state x0.  Its
+ * objective, with p_k the position after step k and N = sum of the steps:
+ *   J = sum_s steps[s] h (1 + w_effort e(u[s]))              effort + duration
+ *     + w_obs sum_{k=1..N} sum_b sp(margin - d_b(p_k))       obstacle penalty
+ *     + w_goal |p_N - goal|^2                                goal pull
+ * where e is the planner's effort term, sp(z) = log(1 + exp(beta z)) / beta,
+ * and d_b is the signed distance from p_k to box b (negative inside).  Box
+ * terms with beta (margin - d) < -30 are dropped (each is below 1e-13/beta).
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    float w_obs;      /* weight of the obstacle penalty */
+    float beta;       /* softplus sharpness (1 / length), > 0 */
+    float margin;     /* clearance at which the penalty is log(2)/beta per box */
+    float w_goal;     /* weight of |p_N - goal|^2 */
+    float goal[3];
+    float w_effort;   /* effort weight of the edge cost */
+} kpx_refine_cost;
+
+/* Device bytes of the checkpoint workspace kpx_refine_eval needs for a
+ * gradient: count trajectories of at most max_total_steps steps. */
+size_t kpx_refine_workspace_size(int32_t count, int32_t max_total_steps);
+
+/* J (cost_out[count]) and, when grad_u != NULL, dJ/du (grad_u[count]
+ * [max_segments][4]; rows past n_segments are 0) for count trajectories, on
+ * cuda_stream, asynchronously.  Device arrays: obstacles[n_obstacles][6]
+ * (lo xyz, hi xyz; n_obstacles <= 4096), x0[count][12], u[count]
+ * [max_segments][4] (16-byte aligned, as is grad_u), steps[count]
+ * [max_segments], n_segments[count].  The gradient is the adjoint
+ * (reverse-mode) rollout with the state checkpointed every 32 steps in
+ * workspace (>= kpx_refine_workspace_size(count, max_total_steps) bytes,
+ * caller-owned).  A trajectory with more than max_total_steps steps or an
+ * invalid segment count gets J = NaN and a zero gradient.  order (device,
+ * may be NULL): a permutation of 0..count-1 giving the order in which the
+ * trajectories are taken up; the results stay in index order.  Longest
+ * first (by total steps) balances the launch. */
+kpx_status kpx_refine_eval(const kpx_dynamics* dyn, const kpx_refine_cost* cost, const float* obstacles,
+                           int32_t n_obstacles, int32_t count, int32_t max_segments, const float* x0,
+                           const float* u, const int32_t* steps, const int32_t* n_segments, const int32_t* order,
+                           int32_t max_total_steps, float* cost_out, float* grad_u, void* workspace,
+                           size_t workspace_bytes, void* cuda_stream);
+
+/* Re-validation of count trajectories with the planner's own FP32 RK4
+ * stepper from x0: valid[i] = 1 when every state after a step satisfies the
+ * state bounds, lies in the workspace box and in no obstacle box, and the
+ * final position lies in the goal ball; cost_out[i] = the sum of all the
+ * segments' effort+duration edge costs accumulated in FP64 (w_effort);
+ * x_end[count][12] (may be NULL) = the final states.  Same array layouts as
+ * kpx_refine_eval; asynchronous on cuda_stream. */
+kpx_status kpx_refine_validate(const kpx_dynamics* dyn, const kpx_workspace* ws, const float* obstacles,
+                               int32_t n_obstacles, const kpx_goal* goal, float w_effort, int32_t count,
+                               int32_t max_segments, const float* x0, const float* u, const int32_t* steps,
+                               const int32_t* n_segments, int32_t* valid, double* cost_out, float* x_end,
+                               void* cuda_stream);
+
+/* One projected Adam step (b1 0.9, b2 0.999, eps 1e-8, step t >= 1, rate lr)
+ * on the controls u[count][max_segments][4], each scaled to [-1, 1] by the
+ * control box of dyn: z = (u - mid) / half; z -= lr mhat / (sqrt(vhat) +
+ * eps); z is clipped to [-1, 1].  m1, m2: the moment arrays (same shape,
+ * zero before step 1), updated in place.  Rows past n_segments are left as
+ * they are.  Asynchronous on cuda_stream. */
+kpx_status kpx_refine_adam(const kpx_dynamics* dyn, int32_t count, int32_t max_segments, const int32_t* n_segments,
+                           float* u, const float* grad_u, float* m1, float* m2, int32_t t, float lr,
+                           void* cuda_stream);
+
+/* Where cost[i] < cost_best[i], copies the row u[i] to u_best[i] and cost[i]
+ * to cost_best[i] (NaN never wins).  Asynchronous on cuda_stream. */
+kpx_status kpx_refine_keep_best(int32_t count, int32_t max_segments, const float* u, const float* cost,
+                                float* u_best, float* cost_best, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Introspection and step-by-step API (tests, debugging, checkpointing).
  * ---------------------------------------------------------------------- */
 

@@ -36,7 +36,9 @@ EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_traject
             "kpx_destroy", "kpx_status_str", "kpx_last_error", "kpx_get_layout", "kpx_debug_step",
             "kpx_snapshot", "kpx_restore", "kpx_plan_static", "kpx_batch_workspace_size", "kpx_batch_create",
             "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error",
-            "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info")
+            "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info",
+            "kpx_refine_workspace_size", "kpx_refine_eval", "kpx_refine_validate", "kpx_refine_adam",
+            "kpx_refine_keep_best")
 
 
 class kpx_dynamics(C.Structure):

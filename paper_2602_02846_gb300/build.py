@@ -1,8 +1,10 @@
 """Builds libkpx.so (the CUDA planner behind include/kpx.h) in-tree for sm_103a.
 
 nvcc cross-compiles without a GPU; the translation units compile in parallel.
-FP contraction is off (-fmad=false): fused multiply-adds appear only where
-the kernels write fmaf(), which keeps re-materialised rollouts bit-identical.
+FP contraction is off (-fmad=false) in every unit that runs the planner's
+arithmetic: fused multiply-adds appear only where the kernels write fmaf(),
+which keeps re-materialised rollouts bit-identical.  The refinement gradient
+kernels (kpx_adjoint.cu) contract freely.
 """
 from __future__ import annotations
 
@@ -18,10 +20,16 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkpx.so")
-SOURCES = ["kpx_kernels.cu", "kpx_fused.cu", "kpx_batch.cu", "kpx_api.cu"]
+SOURCES = ["kpx_kernels.cu", "kpx_fused.cu", "kpx_batch.cu", "kpx_adjoint.cu", "kpx_refine.cu", "kpx_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-fmad=false", "-Xcompiler", "-fPIC,-ffp-contract=off",
-         "-I", INCLUDE, "-I", CSRC]
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
+# the refinement gradient kernels reproduce nothing bit for bit, so they may
+# contract into FMAs; every other unit keeps the planner's arithmetic
+FMAD = {"kpx_adjoint.cu": "-fmad=true"}
+
+
+def flags_for(src: str) -> list:
+    return [FMAD.get(src, "-fmad=false"), *FLAGS]
 
 
 def nvcc() -> str:
@@ -54,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra: list | None = None)
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-        cmd = [cc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [cc, *ARCH, *flags_for(src), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         r = subprocess.run(cmd, capture_output=True, text=True)

@@ -444,23 +444,8 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     p->ws_bytes = workspace_bytes;
     DevParams& P = p->P;
     memset(&P, 0, sizeof(P));
-    P.dyn = dyn->kind;
-    P.integ = dyn->integ;
-    P.n = n;
-    P.m = m;
-    P.h = dyn->h;
-    P.k_min = dyn->k_min;
-    P.k_max = dyn->k_max;
-    for (int i = 0; i < 8; ++i) {
-        P.u_lo[i] = i < m ? dyn->u_lo[i] : 0.0f;
-        P.u_hi[i] = i < m ? dyn->u_hi[i] : 0.0f;
-        P.param[i] = dyn->param[i];
-    }
-    for (int i = 0; i < 16; ++i) {
-        P.x_lo[i] = i < n ? dyn->x_lo[i] : -INFINITY;
-        P.x_hi[i] = i < n ? dyn->x_hi[i] : INFINITY;
-        P.start[i] = i < n ? start[i] : 0.0f;
-    }
+    fill_dynamics(P, dyn);
+    for (int i = 0; i < 16; ++i) P.start[i] = i < n ? start[i] : 0.0f;
     for (int a = 0; a < 3; ++a) {
         P.ws_lo[a] = ws->lo[a];
         P.ws_hi[a] = ws->hi[a];
@@ -469,16 +454,6 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = cost->kind;
     P.w_effort = cost->w_effort;
-    if (dyn->kind == KPX_QUAD12) {
-        P.mg = dyn->param[0] * dyn->param[1];
-        P.inv_mg = 1.0f / P.mg;
-        P.inv_mass = 1.0f / dyn->param[0];
-        P.inv_tau_max = 1.0f / dyn->param[5];
-        for (int i = 0; i < 3; ++i) {
-            P.J[i] = dyn->param[2 + i];
-            P.inv_J[i] = 1.0f / dyn->param[2 + i];
-        }
-    }
     P.n_axes = cfg->n_axes;
     int64_t R = 1;
     for (int a = 0; a < cfg->n_axes; ++a) {
@@ -1158,23 +1133,8 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     pl.ws_bytes = kStaticScratchBytes;
     DevParams& P = pl.P;
     memset(&P, 0, sizeof(P));
-    P.dyn = dyn->kind;
-    P.integ = dyn->integ;
-    P.n = n;
-    P.m = m;
-    P.h = dyn->h;
-    P.k_min = dyn->k_min;
-    P.k_max = dyn->k_max;
-    for (int i = 0; i < 8; ++i) {
-        P.u_lo[i] = i < m ? dyn->u_lo[i] : 0.0f;
-        P.u_hi[i] = i < m ? dyn->u_hi[i] : 0.0f;
-        P.param[i] = dyn->param[i];
-    }
-    for (int i = 0; i < 16; ++i) {
-        P.x_lo[i] = i < n ? dyn->x_lo[i] : -INFINITY;
-        P.x_hi[i] = i < n ? dyn->x_hi[i] : INFINITY;
-        P.start[i] = i < n ? start[i] : 0.0f;
-    }
+    fill_dynamics(P, dyn);
+    for (int i = 0; i < 16; ++i) P.start[i] = i < n ? start[i] : 0.0f;
     for (int a = 0; a < 3; ++a) {
         P.ws_lo[a] = ws->lo[a];
         P.ws_hi[a] = ws->hi[a];
@@ -1183,16 +1143,6 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = cost->kind;
     P.w_effort = cost->w_effort;
-    if (dyn->kind == KPX_QUAD12) {
-        P.mg = dyn->param[0] * dyn->param[1];
-        P.inv_mg = 1.0f / P.mg;
-        P.inv_mass = 1.0f / dyn->param[0];
-        P.inv_tau_max = 1.0f / dyn->param[5];
-        for (int i = 0; i < 3; ++i) {
-            P.J[i] = dyn->param[2 + i];
-            P.inv_J[i] = 1.0f / dyn->param[2 + i];
-        }
-    }
     P.n_axes = cfg->n_axes;
     int64_t R = 1;
     for (int a = 0; a < cfg->n_axes; ++a) {

@@ -146,6 +146,39 @@ inline void fill_region_by_component(DevParams& P) {
     }
 }
 
+// The dynamics fields of the parameter block (kind, integrator, step, control
+// and state boxes, constants); the planner and the refinement kernels share
+// them, so their FP32 rollouts are the same arithmetic.
+inline void fill_dynamics(DevParams& P, const kpx_dynamics* dyn) {
+    const int n = dyn->kind == KPX_QUAD12 ? 12 : 6, m = dyn->kind == KPX_QUAD12 ? 4 : 3;
+    P.dyn = dyn->kind;
+    P.integ = dyn->integ;
+    P.n = n;
+    P.m = m;
+    P.h = dyn->h;
+    P.k_min = dyn->k_min;
+    P.k_max = dyn->k_max;
+    for (int i = 0; i < 8; ++i) {
+        P.u_lo[i] = i < m ? dyn->u_lo[i] : 0.0f;
+        P.u_hi[i] = i < m ? dyn->u_hi[i] : 0.0f;
+        P.param[i] = dyn->param[i];
+    }
+    for (int i = 0; i < 16; ++i) {
+        P.x_lo[i] = i < n ? dyn->x_lo[i] : -__builtin_huge_valf();
+        P.x_hi[i] = i < n ? dyn->x_hi[i] : __builtin_huge_valf();
+    }
+    if (dyn->kind == KPX_QUAD12) {
+        P.mg = dyn->param[0] * dyn->param[1];
+        P.inv_mg = 1.0f / P.mg;
+        P.inv_mass = 1.0f / dyn->param[0];
+        P.inv_tau_max = 1.0f / dyn->param[5];
+        for (int i = 0; i < 3; ++i) {
+            P.J[i] = dyn->param[2 + i];
+            P.inv_J[i] = 1.0f / dyn->param[2 + i];
+        }
+    }
+}
+
 // Many problems in one launch per phase (kpx_batch.cu).
 struct BatchHeader {
     unsigned long long prop_ticket[6];  // per dynamics class
@@ -204,5 +237,44 @@ int fused_cluster_size(const DevParams& P);
 // the graph's conditional handle (1: phase kernels needed)
 cudaError_t launch_fused(const DevParams& P, int n_iter, cudaGraphConditionalHandle handle, int use_handle,
                          cudaStream_t s);
+
+// trajectory refinement (kpx_adjoint.cu: objective, adjoint gradient and
+// optimiser kernels; kpx_refine.cu: re-validation and the C ABI)
+constexpr int REFINE_CKPT_STEPS = 32;  // integration steps per checkpoint interval
+constexpr int REFINE_CKPT_WORDS = 16;  // 12 state floats, segment index, step in segment, pad
+constexpr int REFINE_MAX_OBS = 4096;   // boxes staged in shared memory
+
+struct RefineParams {
+    // dynamics (the quadcopter's constants)
+    float h, inv_mass, g, J[3], inv_J[3], mg, tau_max;
+    // objective
+    float w_obs, beta, inv_beta, margin, w_goal, goal[3], w_effort;
+    int32_t count, max_segments, n_obs, max_total_steps, n_ckpt;
+    const float* obs;       // [n_obs][6]
+    const float* x0;        // [count][12]
+    const float* u;         // [count][max_segments][4]
+    const int32_t* steps;   // [count][max_segments]
+    const int32_t* n_seg;   // [count]
+    const int32_t* order;   // [count] processing order (null: index order)
+    float* cost;            // [count]
+    float* grad;            // [count][max_segments][4] (null: objective only)
+    float* ckpt;            // [count][n_ckpt][REFINE_CKPT_WORDS]
+};
+
+struct AdamParams {
+    int32_t count, max_segments;
+    const int32_t* n_seg;
+    float* u;
+    const float* grad;
+    float* m1;
+    float* m2;
+    float lo[4], hi[4];
+    float lr, b1, b2, eps, c1, c2;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+
+cudaError_t launch_refine_eval(const RefineParams& R, cudaStream_t s);
+cudaError_t launch_refine_adam(const AdamParams& A, cudaStream_t s);
+cudaError_t launch_refine_keep_best(int32_t count, int32_t max_segments, const float* u, const float* cost,
+                                    float* u_best, float* cost_best, cudaStream_t s);
 
 }  // namespace kpx

@@ -302,11 +302,12 @@ def voxel_connected(obstacles: np.ndarray, start, goal, ws_lo=(0, 0, 0), ws_hi=(
 
 
 def quad_obstacles(seed: int, clutter: int = 964, edge=(0.01, 0.03), certify: bool = True,
-                   start=(0.05, 0.5, 0.5), goal=(0.95, 0.5, 0.5)) -> np.ndarray:
+                   start=(0.05, 0.5, 0.5), goal=(0.95, 0.5, 0.5), walls: bool = True) -> np.ndarray:
     """Building world: 9 walls at x = 0.1 i (36 boxes) with 0.04 x 0.04
     openings in alternating corners, plus ``clutter`` random boxes kept 0.04
     away from each opening axis and 0.08 away from start and goal.  The scene
-    is redrawn (next sub-seed) until a 0.005 voxel BFS connects start to goal."""
+    is redrawn (next sub-seed) until a 0.005 voxel BFS connects start to goal.
+    walls=False keeps only the clutter (an open cluttered room)."""
     attempt = 0
     while True:
         rng = np.random.default_rng([0x5CE7E, 3, seed, attempt])
@@ -314,7 +315,8 @@ def quad_obstacles(seed: int, clutter: int = 964, edge=(0.01, 0.03), certify: bo
         axes = []
         for i, (cy, cz) in enumerate(quad_openings()):
             x = 0.1 * (i + 1)
-            boxes += _wall_boxes(x, cy, cz)
+            if walls:
+                boxes += _wall_boxes(x, cy, cz)
             axes.append((np.array([x - 0.05, cy, cz]), np.array([x + 0.05, cy, cz])))
         s = np.asarray(start, dtype=np.float64)
         g = np.asarray(goal, dtype=np.float64)
@@ -340,7 +342,7 @@ def quad_obstacles(seed: int, clutter: int = 964, edge=(0.01, 0.03), certify: bo
 
 def quad_scene(seed: int = 0, clutter: int = 964, tree_cap: int = 1 << 22, lam: int = 128,
                grid_pos: int = 16, grid_vel: int = 4, planner_seed: Optional[int] = None,
-               iterations: int = 200, i_max: int = 10, certify: bool = True) -> Problem:
+               iterations: int = 200, i_max: int = 10, certify: bool = True, walls: bool = True) -> Problem:
     """12D quadcopter, state (p, phi/theta/psi ZYX, v, omega), control
     (thrust T, torques tau): p' = v, v' = (T/m) R e3 - g e3,
     (phi,theta,psi)' = W(phi,theta) omega, omega' = J^-1 (tau - omega x J omega);
@@ -350,7 +352,7 @@ def quad_scene(seed: int = 0, clutter: int = 964, tree_cap: int = 1 << 22, lam: 
     sum (tau_i/tau_max)^2, w = 1."""
     start = [0.05, 0.5, 0.5] + [0.0] * 9
     goal = [0.95, 0.5, 0.5]
-    obs = quad_obstacles(seed, clutter, certify=certify) if clutter >= 0 else np.zeros((0, 6), np.float32)
+    obs = quad_obstacles(seed, clutter, certify=certify, walls=walls) if clutter >= 0 else np.zeros((0, 6), np.float32)
     inf = F32_INF
     q = math.pi / 4
     mg = QUAD_MASS * QUAD_G
@@ -420,3 +422,29 @@ def poisson_requests(rate: float, duration: float, seed: int = 0, iterations: in
         if t >= duration:
             return out
         out.append((t, mixed_problem(rng, int(rng.integers(3)), iterations)))
+
+
+def refine_batch(count: int = 4096, seed: int = 0, segments=(64, 512), steps=(10, 60), n_obstacles: int = 1000):
+    """Control sequences of the refinement workload for the 12D quadcopter:
+    ``count`` trajectories from the quadcopter start state, each with a
+    segment count drawn from ``segments`` and per-segment step counts from
+    ``steps`` (both inclusive), thrust mg + U(-0.5, 0.5) and torques
+    U(-0.001, 0.001) held per segment, among the 1,000-box building
+    (``n_obstacles`` boxes of it).  Returns dict(problem, x0, u, steps, n_seg,
+    obstacles); rows past a trajectory's segment count are zero."""
+    prob = quad_scene(seed, certify=False)
+    rng = np.random.default_rng([0x2EF1E, 5, seed])
+    S = int(segments[1])
+    n_seg = rng.integers(segments[0], segments[1] + 1, count).astype(np.int32)
+    st = rng.integers(steps[0], steps[1] + 1, (count, S)).astype(np.int32)
+    mg = float(np.float32(QUAD_MASS * QUAD_G))
+    u = np.zeros((count, S, 4), np.float32)
+    u[:, :, 0] = mg + rng.uniform(-0.5, 0.5, (count, S))
+    u[:, :, 1:] = rng.uniform(-0.001, 0.001, (count, S, 3))
+    mask = np.arange(S)[None, :] < n_seg[:, None]
+    u *= mask[:, :, None]
+    st *= mask
+    x0 = np.tile(np.asarray(prob.start, np.float32), (count, 1))
+    obs = np.asarray(prob.obstacles, np.float32)[:n_obstacles]
+    return dict(problem=prob, x0=x0, u=u, steps=st, n_seg=n_seg, obstacles=obs)
+
