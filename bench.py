@@ -118,6 +118,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-memory-gb", type=float, default=32.0, help="device arena of the request loop")
     ap.add_argument("--serve-slots", type=int, default=64, help="request-loop slots per dynamics class")
     ap.add_argument("--serve-round", type=int, default=4, help="iterations per request-loop round")
+    ap.add_argument("--refine-count", type=int, default=0, help="trajectories of the refinement workload "
+                                                                 "(0: the workload's 4,096)")
     return ap.parse_args(argv)
 
 
@@ -698,7 +700,9 @@ def run_serve(args):
 
 
 def run_refine_reference(args):
-    spec = REFINE_WORKLOADS[args.workload]
+    spec = dict(REFINE_WORKLOADS[args.workload])
+    if args.refine_count:
+        spec["count"] = args.refine_count
     batch = scenes.refine_batch(spec["count"], seed=args.seed)
     budget = max(1.0, args.cpu_seconds / max(1, args.steps))
     refine_oracle_sample(batch, 0.1)
@@ -734,7 +738,9 @@ def run_refine(args):
     import paper_2602_02846_gb300 as kpx
     from paper_2602_02846_gb300 import refine
     kpx.load()
-    spec = REFINE_WORKLOADS[args.workload]
+    spec = dict(REFINE_WORKLOADS[args.workload])
+    if args.refine_count:
+        spec["count"] = args.refine_count
     data = scenes.refine_batch(spec["count"], seed=args.seed + 1000 * rank)
     prob = data["problem"]
     batch = refine.Batch(prob, data["x0"], data["u"], data["steps"], data["n_seg"], obstacles=data["obstacles"],
