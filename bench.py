@@ -111,6 +111,7 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="batch workloads: keep the default launch choices")
     ap.add_argument("--no-fused", action="store_true",
                     help="run every iteration as the seven phase kernels (KPX_FLAG_NO_FUSED; same results)")
     ap.add_argument("--ttfs-seeds", type=int, default=8, help="problems (scene seeds) for time-to-first-solution")
@@ -505,6 +506,16 @@ def run_batch(args):
     batch.reset()
     batch.iterate(iters)
     valid_per_step, ops_per_step = totals()
+    # launch choices per dynamics class, timed on this state (results unchanged)
+    tuned = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        rep = batch.autotune(iters=4, blocks=(0, 2), scales=(0.5, 1.0, 2.0))
+        names = {scenes.DI6: "di6", scenes.DUBINS6: "dubins6", scenes.QUAD12: "quad12"}
+        tuned = {"%s/%s" % (names[c[0]], "rk4" if c[1] else "euler"):
+                 {"propagate_blocks_per_sm": v["blocks"], "grid_scale": v["scale"], "ms_4_iterations": v["ms"]}
+                 for c, v in rep.items()}
+        tuned["seconds"] = time.perf_counter() - t0
     for _ in range(max(0, args.warmup - 1)):
         batch.reset()
         batch.iterate(iters)
@@ -602,6 +613,7 @@ def run_batch(args):
                 "note": "the same problems planned one after another with kpx_create/kpx_iterate (identical "
                         "results, so equal solution cost)"},
             "batch_speedup_vs_plain": None if plain_ms is None else plain_ms / (ms / args.steps),
+            "autotuned": tuned,
             "roofline": {"bound": "alu", "kernel": "k_b_propagate (whole iteration time: a lower bound)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None},

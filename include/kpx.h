@@ -202,6 +202,24 @@ kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, 
  * problem, same workspace), without host copies.  Asynchronous. */
 kpx_status kpx_reset(kpx_planner* p);
 
+/* Launch choices that leave every result unchanged (an autotuner picks
+ * them by timing):
+ *   propagate_blocks_per_sm: resident propagate blocks per SM of the
+ *     persistent grid (0: as many as fit; capped at that);
+ *   grid_scale: obstacle-grid cell edge as a multiple of the mean box extent
+ *     per axis (1: the default; 0: keep the current).  The broad phase is
+ *     exact at any cell size, so only the split between cell lookups and
+ *     box tests moves.
+ * kpx_set_launch applies them to one planner; kpx_batch_set_launch to every
+ * problem of dynamics class (kind, integ) in a batch (KPX_E_INVALID if there
+ * is none).  A new grid is rebuilt asynchronously on the stream, between
+ * iterations. */
+typedef struct {
+    int32_t propagate_blocks_per_sm;
+    float grid_scale;
+} kpx_launch_config;
+kpx_status kpx_set_launch(kpx_planner* p, const kpx_launch_config* lc);
+
 /* How kpx_iterate launches (the graphs are built on first use): n
  * iterations go out as CUDA graphs of 16, 8, 4, 2 and 1 iterations, largest
  * first (*max_iterations_per_launch = 16; 0 when graphs are unavailable and
@@ -291,6 +309,7 @@ typedef struct {
 kpx_status kpx_batch_assign(kpx_batch* b, int32_t index, const kpx_problem* problem, int32_t iter_limit,
                             void* device_workspace, size_t workspace_bytes);
 kpx_status kpx_batch_release(kpx_batch* b, int32_t index);
+kpx_status kpx_batch_set_launch(kpx_batch* b, int32_t kind, int32_t integ, const kpx_launch_config* lc);
 kpx_status kpx_batch_poll(kpx_batch* b, kpx_slot_state* out);
 kpx_status kpx_batch_destroy(kpx_batch* b);
 const char* kpx_batch_last_error(const kpx_batch* b);

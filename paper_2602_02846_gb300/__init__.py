@@ -38,7 +38,7 @@ EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_traject
             "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error",
             "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info",
             "kpx_refine_workspace_size", "kpx_refine_eval", "kpx_refine_validate", "kpx_refine_adam",
-            "kpx_refine_keep_best")
+            "kpx_refine_keep_best", "kpx_set_launch", "kpx_batch_set_launch")
 
 
 class kpx_dynamics(C.Structure):
@@ -115,6 +115,10 @@ class kpx_problem(C.Structure):
     _fields_ = [("dyn", C.POINTER(kpx_dynamics)), ("ws", C.POINTER(kpx_workspace)),
                 ("obs", C.POINTER(kpx_obstacles)), ("start", C.POINTER(C.c_float)), ("goal", C.POINTER(kpx_goal)),
                 ("cost", C.POINTER(kpx_cost)), ("cfg", C.POINTER(kpx_config))]
+
+
+class kpx_launch_config(C.Structure):
+    _fields_ = [("propagate_blocks_per_sm", C.c_int32), ("grid_scale", C.c_float)]
 
 
 class kpx_slot_state(C.Structure):
@@ -198,6 +202,10 @@ def load(path: Optional[str] = None):
         L.kpx_batch_poll.restype = C.c_int
         L.kpx_graph_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.kpx_graph_info.restype = C.c_int
+        L.kpx_set_launch.argtypes = [vp, C.POINTER(kpx_launch_config)]
+        L.kpx_set_launch.restype = C.c_int
+        L.kpx_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(kpx_launch_config)]
+        L.kpx_batch_set_launch.restype = C.c_int
         _lib = L
         return L
 
@@ -337,6 +345,11 @@ class Planner:
 
     def reset(self):
         self._check(load().kpx_reset(self.h))
+
+    def set_launch(self, blocks_per_sm: int = 0, grid_scale: float = 0.0):
+        """kpx_set_launch: launch choices that leave results unchanged."""
+        lc = kpx_launch_config(int(blocks_per_sm), float(grid_scale))
+        self._check(load().kpx_set_launch(self.h, C.byref(lc)))
 
     def graph_info(self):
         """kpx_graph_info: (max iterations per graph launch, fused)."""
@@ -552,6 +565,69 @@ class BatchPlanner:
                         "t_start_ns": int(s.t_start_ns), "t_first_solution_ns": int(s.t_first_solution_ns),
                         "t_last_ns": int(s.t_last_ns), "t_poll_ns": int(s.t_poll_ns)})
         return out
+
+    def set_launch(self, dyn: int, integ: int, blocks_per_sm: int = 0, grid_scale: float = 0.0):
+        """kpx_batch_set_launch for every problem of dynamics class (dyn, integ)."""
+        lc = kpx_launch_config(int(blocks_per_sm), float(grid_scale))
+        st = load().kpx_batch_set_launch(self.h, int(dyn), int(integ), C.byref(lc))
+        if st != KPX_OK:
+            raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
+
+    def autotune(self, iters: int = 4, blocks=(0, 1, 2, 3), scales=(0.5, 1.0, 2.0)):
+        """Per dynamics class, times ``iters`` batched iterations from the
+        current state for every (blocks per SM, grid scale) pair, one class at
+        a time with the others at their chosen settings, and keeps the
+        fastest.  The batch's state is restored after each trial, so
+        planning continues from where it was.  Every choice gives the same
+        results.  Needs the batch's problems in its own workspace (not in
+        slots reassigned elsewhere).  Returns {(dyn, integ): dict(blocks,
+        scale, ms, trials)}."""
+        import torch
+        classes = sorted({(int(p.dyn), int(p.integ)) for p in self.problems})
+        base = {c: (0, 1.0) for c in classes}
+        chosen = dict(base)
+        snap = self.workspace.clone()
+        s = self.stream
+
+        def apply_settings(settings):
+            # the restored workspace holds the snapshot's grids: bring the host
+            # side back to that scale, then to the trial's (the blocks per SM
+            # are host-only and are set once, so the captured graphs stay)
+            for c in classes:
+                self.set_launch(c[0], c[1], settings[c][0], base[c][1])
+                self.set_launch(c[0], c[1], settings[c][0], settings[c][1])
+
+        def run(settings):
+            with torch.cuda.stream(s):
+                self.workspace.copy_(snap)
+            apply_settings(settings)
+            self.iterate(iters)  # builds the graphs for these launch shapes
+            with torch.cuda.stream(s):
+                self.workspace.copy_(snap)
+            apply_settings(settings)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(s)
+            self.iterate(iters)
+            b.record(s)
+            b.synchronize()
+            return a.elapsed_time(b)
+
+        report = {}
+        for c in classes:
+            trials = []
+            for bps in blocks:
+                for sc in scales:
+                    trial = dict(chosen)
+                    trial[c] = (bps, sc)
+                    trials.append((run(trial), bps, sc))
+            ms, bps, sc = min(trials)
+            chosen[c] = (bps, sc)
+            report[c] = dict(blocks=bps, scale=sc, ms=ms, trials=[(b_, s_, t_) for t_, b_, s_ in trials])
+        with torch.cuda.stream(s):
+            self.workspace.copy_(snap)
+        apply_settings(chosen)
+        s.synchronize()
+        return report
 
     def member(self, i: int) -> "Planner":
         if i in self._members:

@@ -33,6 +33,8 @@ struct kpx_planner {
     bool graph_fused = false;  // graphs start with the fused kernel
     cudaStream_t capture_stream = nullptr;
     cudaGraphExec_t graphs[kGraphLevels] = {};  // graphs[k]: 2^k iterations
+    float grid_scale = 1.0f;     // obstacle-grid cell edge / mean box extent
+    std::vector<float> host_obs; // the boxes (lo xyz, hi xyz), to rebuild the grid
 };
 
 // Many problems iterated together (one launch per phase for all of them).
@@ -42,6 +44,7 @@ struct kpx_batch {
     std::vector<int> member_of_index;    // caller's index -> position in members
     int n_classes = 0;
     int cls_kind[6] = {}, cls_lo[6] = {}, cls_hi[6] = {};
+    int cls_bps[6] = {};  // propagate blocks per SM per class (0: as many as fit)
     kpx::BatchParams BP{};
     cudaStream_t stream = nullptr;
     std::string err;
@@ -170,7 +173,11 @@ bool host_point_valid(const DevParams& P, const float* x, const float* obs, int 
 // (at most GRID_MAX_AXIS per axis and GRID_MAX_CELLS in all), coarsened until
 // the cell lists fit the reserved entries.  Uses the same FP32 cell map as
 // the device, so the entry count here is the one the device build produces.
-void choose_grid(DevParams& P, const float* aabb, int n_obs) {
+// Obstacle grid: cells of about `scale` x the mean box extent per axis
+// (capped by GRID_MAX_AXIS, GRID_MAX_CELLS and the entry budget).  Any grid
+// gives the same verdicts (the broad phase is exact); the scale only moves
+// work between cell lookups and box tests.
+void choose_grid(DevParams& P, const float* aabb, int n_obs, float scale = 1.0f) {
     P.grid_cap = (int32_t)grid_entry_budget(n_obs);
     int g[3] = {1, 1, 1};
     float W[3];
@@ -183,7 +190,7 @@ void choose_grid(DevParams& P, const float* aabb, int n_obs) {
                 double e = (double)aabb[6 * b + 3 + a] - (double)aabb[6 * b + a];
                 sum += e < (double)W[a] ? e : (double)W[a];
             }
-            double mean = sum / n_obs;
+            double mean = sum / n_obs * (double)scale;
             if (mean < (double)W[a] / GRID_MAX_AXIS) mean = (double)W[a] / GRID_MAX_AXIS;
             int ga = (int)((double)W[a] / mean);
             g[a] = ga < 1 ? 1 : (ga > GRID_MAX_AXIS ? GRID_MAX_AXIS : ga);
@@ -481,7 +488,8 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     P.n_win_tiles = L.n_win_tiles;
     P.n_prune_tiles = L.n_prune_tiles;
     bind_pointers(p);
-    choose_grid(P, obs->aabb, n_obs);
+    choose_grid(P, obs->aabb, n_obs, p->grid_scale);
+    p->host_obs.assign(obs->aabb, obs->aabb + 6 * (size_t)n_obs);
     if (!host_point_valid(P, P.start, obs->aabb, n_obs)) return reject(KPX_E_INVALID, "start state is not in X_valid");
     return KPX_OK;
 }
@@ -525,7 +533,8 @@ cudaError_t capture_batch(kpx_batch* b, int count, cudaGraphExec_t* exec) {
     if (e != cudaSuccess) return e;
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < count && le == cudaSuccess; ++i)
-        le = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->capture_stream);
+        le = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->cls_bps,
+                                    b->capture_stream);
     e = cudaStreamEndCapture(b->capture_stream, &g);
     if (le != cudaSuccess) e = le;
     if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
@@ -673,6 +682,37 @@ kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, 
     if (out_cost) {
         uint32_t bits = (uint32_t)(h.goal_key >> 32);
         memcpy(out_cost, &bits, sizeof(float));
+    }
+    return KPX_OK;
+}
+
+// Re-chooses the obstacle grid at `scale` and enqueues its rebuild (the
+// boxes are already on the device); no-op when the scale is unchanged.
+cudaError_t regrid(kpx_planner* p, float scale) {
+    if (scale == p->grid_scale) return cudaSuccess;
+    p->grid_scale = scale;
+    choose_grid(p->P, p->host_obs.data(), p->P.n_obs, scale);
+    return launch_grid_build(p->P, p->stream);
+}
+
+bool launch_config_ok(const kpx_launch_config* lc) {
+    return lc && lc->propagate_blocks_per_sm >= 0 && lc->propagate_blocks_per_sm <= 64 &&
+           std::isfinite(lc->grid_scale) && lc->grid_scale >= 0.0f && lc->grid_scale <= 64.0f;
+}
+
+kpx_status kpx_set_launch(kpx_planner* p, const kpx_launch_config* lc) {
+    if (!p || !launch_config_ok(lc)) return KPX_E_INVALID;
+    if (lc->grid_scale > 0.0f) {
+        cudaError_t e = regrid(p, lc->grid_scale);
+        if (e != cudaSuccess) return cuda_fail(p, e, "grid rebuild");
+    }
+    if (lc->propagate_blocks_per_sm != p->P.prop_bps) {
+        p->P.prop_bps = lc->propagate_blocks_per_sm;
+        drop_graphs(p);  // the captured launch shapes and parameters change
+        p->graph_state = 0;
+    } else if (lc->grid_scale > 0.0f) {
+        drop_graphs(p);  // the graphs hold the parameter block by value
+        p->graph_state = 0;
     }
     return KPX_OK;
 }
@@ -893,7 +933,7 @@ kpx_status kpx_batch_iterate(kpx_batch* b, int32_t n_iters) {
     if (b->graph_state == 0 && n_iters > 0) {
         // the first iteration runs plainly (it also computes the launch shapes),
         // then the iteration is captured once as a graph
-        e = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->stream);
+        e = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->cls_bps, b->stream);
         ++it;
         b->graph_state = -1;
         if (e == cudaSuccess && cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking) == cudaSuccess) {
@@ -910,7 +950,7 @@ kpx_status kpx_batch_iterate(kpx_batch* b, int32_t n_iters) {
         for (; e == cudaSuccess && it < n_iters; ++it) e = cudaGraphLaunch(b->graph_one, b->stream);
     }
     for (; e == cudaSuccess && it < n_iters; ++it)
-        e = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->stream);
+        e = launch_batch_iteration(b->BP, b->n_classes, b->cls_kind, b->cls_lo, b->cls_hi, b->cls_bps, b->stream);
     if (e != cudaSuccess) {
         b->err = std::string("batch iteration: ") + cudaGetErrorString(e);
         return KPX_E_CUDA;
@@ -935,6 +975,7 @@ kpx_status kpx_batch_assign(kpx_batch* b, int32_t index, const kpx_problem* prob
     }
     kpx_planner tmp;
     tmp.stream = b->stream;
+    tmp.grid_scale = p->grid_scale;  // the class's launch settings stay with the slot
     std::string msg;
     void* ws = device_workspace ? device_workspace : p->ws;
     const size_t ws_bytes = device_workspace ? workspace_bytes : p->ws_bytes;
@@ -949,6 +990,7 @@ kpx_status kpx_batch_assign(kpx_batch* b, int32_t index, const kpx_problem* prob
     p->L = tmp.L;
     p->ws = tmp.ws;
     p->ws_bytes = tmp.ws_bytes;
+    p->host_obs = std::move(tmp.host_obs);
     p->P.iter_limit = iter_limit;
     cudaError_t e = upload_and_init(p, problem->obs, b->staging[k]);
     if (e == cudaSuccess)
@@ -992,6 +1034,44 @@ kpx_status kpx_batch_poll(kpx_batch* b, kpx_slot_state* out) {
     }
     static_assert(sizeof(SlotState) == sizeof(kpx_slot_state), "slot state layouts differ");
     for (int i = 0; i < b->B; ++i) memcpy(&out[i], &b->poll_buf[b->member_of_index[i]], sizeof(kpx_slot_state));
+    return KPX_OK;
+}
+
+kpx_status kpx_batch_set_launch(kpx_batch* b, int32_t kind, int32_t integ, const kpx_launch_config* lc) {
+    if (!b || !launch_config_ok(lc)) return KPX_E_INVALID;
+    int c = 0;
+    while (c < b->n_classes && b->cls_kind[c] != kind * 2 + integ) ++c;
+    if (c == b->n_classes) {
+        b->err = "the batch has no problem of that dynamics class";
+        return KPX_E_INVALID;
+    }
+    if (lc->grid_scale > 0.0f) {
+        for (int k = b->cls_lo[c]; k < b->cls_hi[c]; ++k) {
+            kpx_planner* p = b->members[k];
+            if (lc->grid_scale == p->grid_scale) continue;
+            cudaError_t e = cudaSuccess;
+            if (p->P.iter_limit < 0) {  // vacant slot: the next assignment builds its grid
+                p->grid_scale = lc->grid_scale;
+            } else {
+                e = regrid(p, lc->grid_scale);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(const_cast<DevParams*>(b->BP.Ps) + k, &p->P, sizeof(DevParams),
+                                        cudaMemcpyHostToDevice, b->stream);
+            }
+            if (e != cudaSuccess) {
+                b->err = std::string("batch set_launch: ") + cudaGetErrorString(e);
+                return KPX_E_CUDA;
+            }
+            drop_member_graphs(p);
+        }
+    }
+    if (lc->propagate_blocks_per_sm != b->cls_bps[c]) {
+        b->cls_bps[c] = lc->propagate_blocks_per_sm;
+        if (b->graph_one) cudaGraphExecDestroy(b->graph_one);
+        if (b->graph_many) cudaGraphExecDestroy(b->graph_many);
+        b->graph_one = b->graph_many = nullptr;
+        b->graph_state = 0;
+    }
     return KPX_OK;
 }
 

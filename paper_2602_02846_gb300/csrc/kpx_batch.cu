@@ -229,14 +229,15 @@ int b_sm_count() {
 }
 
 template <int DYN, int INTEG>
-cudaError_t launch_b_propagate_t(const BatchParams& BP, cudaStream_t s) {
+cudaError_t launch_b_propagate_t(const BatchParams& BP, int bps, cudaStream_t s) {
     static int per_sm = 0;
     if (!per_sm) {
         int v = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_b_propagate<DYN, INTEG>, PROP_THREADS, 0);
         per_sm = v < 1 ? 1 : v;
     }
-    k_b_propagate<DYN, INTEG><<<b_sm_count() * per_sm, PROP_THREADS, 0, s>>>(BP);
+    const int use = bps > 0 && bps < per_sm ? bps : per_sm;
+    k_b_propagate<DYN, INTEG><<<b_sm_count() * use, PROP_THREADS, 0, s>>>(BP);
     return cudaGetLastError();
 }
 
@@ -267,7 +268,7 @@ cudaError_t launch_batch_poll(const BatchParams& base, cudaStream_t s) {
 // One batched iteration: begin, snapshot, propagate per class, mark, scan,
 // prefix, append per class, prune, end.
 cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const int* cls_kind, const int* cls_lo,
-                                   const int* cls_hi, cudaStream_t s) {
+                                   const int* cls_hi, const int* cls_bps, cudaStream_t s) {
     k_b_begin<<<1, 1024, 0, s>>>(base);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -277,7 +278,7 @@ cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const
         bp.lo = cls_lo[c];
         bp.hi = cls_hi[c];
         bp.cls = c;
-        e = [&]() -> cudaError_t { KPX_CLASS_DISPATCH(launch_b_propagate_t, cls_kind[c], bp, s); }();
+        e = [&]() -> cudaError_t { KPX_CLASS_DISPATCH(launch_b_propagate_t, cls_kind[c], bp, cls_bps[c], s); }();
     }
     if (e != cudaSuccess) return e;
     k_b_mark<<<dim3(8, base.B), 256, 0, s>>>(base);

@@ -65,6 +65,7 @@ struct DevParams {
     int32_t flags, n_obs;
     int32_t va_cap;
     int32_t iter_limit;   // batch slots: iterate while iter < iter_limit (0: no limit, -1: vacant)
+    int32_t prop_bps;     // host side: propagate blocks per SM (0: as many as fit)
     int64_t slot_cap, mask_words;
     int32_t n_win_tiles, n_prune_tiles;
     // obstacle grid: cell(c, axis a) = clamp(floor((c - ws_lo[a]) * grid_inv[a]), 0, grid_n[a] - 1)
@@ -209,8 +210,9 @@ struct BatchParams {
 
 cudaError_t launch_batch_poll(const BatchParams& base, cudaStream_t s);
 
+// cls_bps: per class, propagate blocks per SM (0: as many as fit)
 cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const int* cls_kind, const int* cls_lo,
-                                   const int* cls_hi, cudaStream_t s);
+                                   const int* cls_hi, const int* cls_bps, cudaStream_t s);
 
 // launchers (kpx_kernels.cu); each returns the launch status
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s);

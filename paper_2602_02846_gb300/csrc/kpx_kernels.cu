@@ -346,7 +346,8 @@ int propagate_occupancy(const DevParams& P) { KPX_DISPATCH(propagate_occupancy_t
 
 template <int DYN, int INTEG>
 cudaError_t launch_propagate_t(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s) {
-    const int per_sm = propagate_blocks_per_sm<DYN, INTEG>();
+    const int fit = propagate_blocks_per_sm<DYN, INTEG>();
+    const int per_sm = P.prop_bps > 0 && P.prop_bps < fit ? P.prop_bps : fit;
     const int grid = persistent_blocks((P.slot_cap + PROP_THREADS - 1) / PROP_THREADS, per_sm);
     kpx_debug_records r{};
     int on = 0;

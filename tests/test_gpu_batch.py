@@ -100,3 +100,48 @@ def test_large_mixed_batch_sampled(kpx):
         _same(_arrays(single), _arrays(batch.member(i)), "problem %d" % i)
         single.close()
     batch.close()
+
+
+def _results(pl):
+    """Everything but the box-test counter (a work count that the obstacle
+    grid's cell size changes by design)."""
+    a = _arrays(pl)
+    a["totals"] = a["totals"][:4]
+    return a
+
+
+def test_launch_settings_leave_results_unchanged(kpx):
+    """Propagate grid size and obstacle-grid cell size, set before or during
+    a run, change no result."""
+    prob = scenes.quad_scene(1, clutter=100, certify=False, tree_cap=1 << 15, lam=4)
+    ref = kpx.Planner(prob, flags=kpx.KPX_FLAG_NO_FUSED)
+    ref.iterate(10)
+    want = _results(ref)
+    tests_ref = ref.header().total_box_tests
+    ref.close()
+    moved = False
+    for bps, scale in [(1, 0.5), (2, 2.0), (0, 4.0)]:
+        pl = kpx.Planner(prob, flags=kpx.KPX_FLAG_NO_FUSED)
+        pl.set_launch(bps, scale)
+        pl.iterate(4)
+        pl.set_launch(0, 1.0)
+        pl.iterate(6)
+        _same(want, _results(pl), "blocks %d scale %g" % (bps, scale))
+        moved |= pl.header().total_box_tests != tests_ref
+        pl.close()
+    assert moved  # the grid scale does change the work
+
+
+def test_autotune_keeps_results(kpx):
+    probs = _mixed_problems()
+    ref = kpx.BatchPlanner(probs)
+    ref.iterate(7)
+    tuned = kpx.BatchPlanner(probs)
+    tuned.iterate(3)
+    report = tuned.autotune(iters=2, blocks=(0, 2), scales=(0.5, 2.0))
+    assert set(report) == {(int(p.dyn), int(p.integ)) for p in probs}
+    tuned.iterate(4)
+    for i in range(len(probs)):
+        _same(_results(ref.member(i)), _results(tuned.member(i)), "problem %d" % i)
+    ref.close()
+    tuned.close()
