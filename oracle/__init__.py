@@ -140,6 +140,7 @@ def _declare(L):
     L.kpo_destroy.argtypes = [vp]
     L.kpo_revalidate.argtypes = [C.POINTER(Problem), C.c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
     L.kpo_revalidate.restype = C.c_int32
+    L.kpo_remap_regions.argtypes = [C.POINTER(Problem), C.c_int32, vp, vp, vp, vp, vp, vp, vp]
     L.kpo_box_distance.argtypes = [vp, vp, vp]
     L.kpo_box_distance.restype = C.c_double
     L.kpo_refine_cost.argtypes = [C.POINTER(Problem), C.POINTER(Refine), vp, C.c_int32, vp, vp, vp, C.c_int32]
@@ -442,6 +443,23 @@ class Planner:
             return None
         L = int(ln[0])
         return dict(states=st[:L + 1].copy(), controls=ct[:L].copy(), steps=sp[:L].copy(), cost=float(cost[0]))
+
+
+def remap_regions(prob, x, key, set_):
+    """Region ids, region keys, dominated flags and cell margins of the
+    nodes (x[n_nodes][n], key, set) under prob's region grid."""
+    P = as_oracle(prob)
+    x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1, P.n))
+    key = np.ascontiguousarray(key, dtype=np.uint64)
+    st = np.ascontiguousarray(set_, dtype=np.uint8)
+    nn = x.shape[0]
+    region = np.zeros(nn, np.int32)
+    rk = np.zeros(P.R, np.uint64)
+    dom = np.zeros(nn, np.uint8)
+    mg = np.zeros(nn)
+    lib().kpo_remap_regions(P.ref, nn, x.ctypes.data, key.ctypes.data, st.ctypes.data, region.ctypes.data,
+                            rk.ctypes.data, dom.ctypes.data, mg.ctypes.data)
+    return dict(region=region, region_key=rk, dominated=dom.astype(bool), margin=mg)
 
 
 # ---------------------------------------------------------------------------

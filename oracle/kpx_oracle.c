@@ -764,6 +764,26 @@ int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, 
 }
 
 /* ------------------------------------------------------------------------
+ * Region remap (adaptive delta): the definition in kpx_oracle.h, written
+ * out node by node.
+ * ---------------------------------------------------------------------- */
+void kpo_remap_regions(const kpo_problem* P, int32_t n_nodes, const double* x, const uint64_t* key,
+                       const uint8_t* set, int32_t* region, uint64_t* region_key, uint8_t* dominated,
+                       double* margin) {
+    int64_t R = 1;
+    for (int a = 0; a < P->n_axes; ++a) R *= P->ax_bins[a];
+    for (int64_t r = 0; r < R; ++r) region_key[r] = KPO_KEY_INF;
+    for (int32_t i = 0; i < n_nodes; ++i) {
+        double mg;
+        region[i] = kpo_region(P, x + (int64_t)i * P->n, &mg);
+        if (margin) margin[i] = mg;
+        if (set[i] != KPO_SET_T && key[i] < region_key[region[i]]) region_key[region[i]] = key[i];
+    }
+    for (int32_t i = 0; i < n_nodes; ++i)
+        dominated[i] = (set[i] != KPO_SET_T && key[i] != region_key[region[i]]) ? 1 : 0;
+}
+
+/* ------------------------------------------------------------------------
  * Refinement objective and its gradient (TEST INFRASTRUCTURE: the reference
  * for the adjoint kernel).  The objective is defined in kpx_oracle.h.  The
  * gradient is plain reverse mode: the forward pass keeps every state, the

@@ -151,6 +151,17 @@ int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, 
                        const int32_t* steps, double* max_seg_err, double* min_clearance,
                        double* goal_slack, double* cost, double* openloop_err);
 
+/* A new region decomposition between iterations (adaptive delta; the
+ * paper's remark on adaptive decompositions).  Reading: with P's grid, every
+ * node's region is its state's region; a region's key is the minimum key
+ * over its non-terminal nodes (set 1 or 2; KPO key order); a non-terminal
+ * node whose key is not its region's key is dominated; terminal nodes keep
+ * their set.  x[n_nodes][n]; region_key[R] with R = P's region count;
+ * margin[i] = the node's distance to a cell boundary (as kpo_region). */
+void kpo_remap_regions(const kpo_problem* P, int32_t n_nodes, const double* x, const uint64_t* key,
+                       const uint8_t* set, int32_t* region, uint64_t* region_key, uint8_t* dominated,
+                       double* margin);
+
 /* ------------------------------------------------------------------------
  * Refinement objective of a control sequence (the adjoint post-pass; the
  * paper has no refinement, so the objective is a reading):

@@ -15,6 +15,7 @@ import oracle
 from tests import test_oracle_dynamics as dyn
 from tests import test_oracle_geometry as geo
 from tests import test_oracle_refine as ref
+from tests import test_oracle_remap as rmp
 from tests import test_oracle_sampling as smp
 from tests import test_oracle_steps as stp
 
@@ -100,6 +101,11 @@ MUTATIONS = [
     ("softplus_scale", "return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t))) / beta;",
      "return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t)));", [ref.test_penalty_value_by_hand]),
     ("validate_no_check", "if (!kpo_point_valid(P, x)) ok = 0;", "(void)0;", [ref.test_validate_controls]),
+    # region remap (adaptive delta)
+    ("remap_terminal_holds_region", "if (set[i] != KPO_SET_T && key[i] < region_key[region[i]])",
+     "if (key[i] < region_key[region[i]])", [rmp.test_remap_hand_example]),
+    ("remap_terminal_dominated", "dominated[i] = (set[i] != KPO_SET_T && key[i] != region_key[region[i]])",
+     "dominated[i] = (key[i] != region_key[region[i]])", [rmp.test_remap_hand_example]),
 ]
 
 
