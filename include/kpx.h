@@ -139,6 +139,8 @@ typedef struct {
     int32_t i_max;
     uint64_t seed;
     int32_t flags;         /* KPX_FLAG_* */
+    int32_t region_capacity; /* regions the workspace holds (0: this grid's count); room for a finer grid
+                                given later to kpx_set_regions */
 } kpx_config;
 
 /* Counters after the last completed iteration. */
@@ -219,6 +221,23 @@ typedef struct {
     float grid_scale;
 } kpx_launch_config;
 kpx_status kpx_set_launch(kpx_planner* p, const kpx_launch_config* lc);
+
+/* Replaces the region decomposition between iterations (adaptive delta:
+ * the paper's remark on non-uniform and adaptive decompositions allows the
+ * grid to be refined over time).  The new grid (same axis rules as
+ * kpx_config) must have at most the planner's region capacity (else
+ * KPX_E_INVALID).  On the device, asynchronously:
+ *   - every node's region becomes its state's region under the new grid;
+ *   - each region's key becomes the minimum key over the non-terminal nodes
+ *     (V_A and V_I) in it; a region with none is empty;
+ *   - a non-terminal node is dominated when its key is not its region's key
+ *     (the next PruneNodes sends it to V_T); terminal nodes stay terminal;
+ *   - the memoised "ancestor dominated" bits are cleared, so PruneNodes
+ *     re-derives them;
+ *   - the sets and the next V_A list are left to the next PruneNodes.
+ * Under a refinement (each new region inside one old region) no
+ * non-terminal node becomes dominated.  kpx_reset keeps the new grid. */
+kpx_status kpx_set_regions(kpx_planner* p, int32_t n_axes, const kpx_region_axis* axes);
 
 /* How kpx_iterate launches (the graphs are built on first use): n
  * iterations go out as CUDA graphs of 16, 8, 4, 2 and 1 iterations, largest

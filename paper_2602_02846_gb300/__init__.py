@@ -11,6 +11,7 @@ loaded, a RuntimeError is raised.  There is no CPU fallback.
 from __future__ import annotations
 
 import ctypes as C
+import dataclasses
 import os
 import threading
 from typing import Optional
@@ -38,7 +39,7 @@ EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_traject
             "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error",
             "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info",
             "kpx_refine_workspace_size", "kpx_refine_eval", "kpx_refine_validate", "kpx_refine_adam",
-            "kpx_refine_keep_best", "kpx_set_launch", "kpx_batch_set_launch")
+            "kpx_refine_keep_best", "kpx_set_launch", "kpx_batch_set_launch", "kpx_set_regions")
 
 
 class kpx_dynamics(C.Structure):
@@ -71,7 +72,7 @@ class kpx_region_axis(C.Structure):
 class kpx_config(C.Structure):
     _fields_ = [("tree_cap", C.c_int32), ("samples_per_node", C.c_int32), ("n_axes", C.c_int32),
                 ("axis", kpx_region_axis * 8), ("i_max", C.c_int32), ("seed", C.c_uint64),
-                ("flags", C.c_int32)]
+                ("flags", C.c_int32), ("region_capacity", C.c_int32)]
 
 
 class kpx_iter_stats(C.Structure):
@@ -202,6 +203,8 @@ def load(path: Optional[str] = None):
         L.kpx_batch_poll.restype = C.c_int
         L.kpx_graph_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.kpx_graph_info.restype = C.c_int
+        L.kpx_set_regions.argtypes = [vp, C.c_int32, C.POINTER(kpx_region_axis)]
+        L.kpx_set_regions.restype = C.c_int
         L.kpx_set_launch.argtypes = [vp, C.POINTER(kpx_launch_config)]
         L.kpx_set_launch.restype = C.c_int
         L.kpx_batch_set_launch.argtypes = [vp, C.c_int32, C.c_int32, C.POINTER(kpx_launch_config)]
@@ -253,6 +256,7 @@ def problem_structs(prob, flags: int = 0):
     cfg.i_max = int(prob.i_max)
     cfg.seed = int(prob.seed) & 0xFFFFFFFFFFFFFFFF
     cfg.flags = int(flags)
+    cfg.region_capacity = int(prob.region_capacity)
     obs = np.ascontiguousarray(np.asarray(prob.obstacles, dtype=np.float32).reshape(-1, 6))
     o = kpx_obstacles()
     o.aabb = obs.ctypes.data_as(C.POINTER(C.c_float))
@@ -345,6 +349,15 @@ class Planner:
 
     def reset(self):
         self._check(load().kpx_reset(self.h))
+
+    def set_regions(self, axes):
+        """kpx_set_regions: a new region decomposition (scenes.RegionAxis list)."""
+        arr = (kpx_region_axis * max(1, len(axes)))()
+        for i, ax in enumerate(axes):
+            arr[i].state_dim, arr[i].bins = int(ax.state_dim), int(ax.bins)
+            arr[i].lo, arr[i].hi, arr[i].wrap = float(ax.lo), float(ax.hi), int(bool(ax.wrap))
+        self._check(load().kpx_set_regions(self.h, len(axes), arr))
+        self.prob = dataclasses.replace(self.prob, axes=list(axes)) if dataclasses.is_dataclass(self.prob) else self.prob
 
     def set_launch(self, blocks_per_sm: int = 0, grid_scale: float = 0.0):
         """kpx_set_launch: launch choices that leave results unchanged."""

@@ -69,6 +69,42 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 bool finite(float v) { return std::isfinite(v); }
 
+// Validates a region decomposition for an n-dimensional state; sets R to
+// its region count.  Returns an empty string when valid.
+std::string check_axes(int n, int32_t n_axes, const kpx_region_axis* axis, int64_t& R) {
+    if (n_axes < 1 || n_axes > 8 || !axis) return "n_axes must be in [1, 8]";
+    R = 1;
+    for (int a = 0; a < n_axes; ++a) {
+        const kpx_region_axis& ax = axis[a];
+        if (ax.state_dim < 0 || ax.state_dim >= n) return "region axis state_dim out of range";
+        if (ax.bins < 1 || ax.bins > (1 << 20)) return "region axis bins out of range";
+        if (!finite(ax.lo) || !finite(ax.hi) || !(ax.hi > ax.lo)) return "region axis needs finite lo < hi";
+        for (int b = 0; b < a; ++b)
+            if (axis[b].state_dim == ax.state_dim) return "a state component may appear in one region axis only";
+        R *= ax.bins;
+        if (R > (1 << 28)) return "too many regions (> 2^28)";
+    }
+    return "";
+}
+
+// the per-axis region fields of the parameter block
+void fill_axes(DevParams& P, int32_t n_axes, const kpx_region_axis* axis) {
+    P.n_axes = n_axes;
+    int64_t R = 1;
+    for (int a = 0; a < n_axes; ++a) {
+        const kpx_region_axis& ax = axis[a];
+        P.ax_dim[a] = ax.state_dim;
+        P.ax_bins[a] = ax.bins;
+        P.ax_wrap[a] = ax.wrap ? 1 : 0;
+        P.ax_lo[a] = ax.lo;
+        const float width = ax.hi - ax.lo;
+        P.ax_scale[a] = (float)ax.bins / width;
+        R *= ax.bins;
+    }
+    fill_region_by_component(P);
+    P.R = (int32_t)R;
+}
+
 // Validates the scalar configuration; returns an empty string when valid.
 std::string check_config(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs) {
     if (!dyn || !cfg) return "null dynamics or config";
@@ -92,18 +128,11 @@ std::string check_config(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t
     }
     if (cfg->tree_cap < 1 || cfg->tree_cap > (1 << 28)) return "tree_cap must be in [1, 2^28]";
     if (cfg->samples_per_node < 0 || cfg->samples_per_node > 65536) return "samples_per_node must be in [0, 65536]";
-    if (cfg->n_axes < 1 || cfg->n_axes > 8) return "n_axes must be in [1, 8]";
-    int64_t R = 1;
-    for (int a = 0; a < cfg->n_axes; ++a) {
-        const kpx_region_axis& ax = cfg->axis[a];
-        if (ax.state_dim < 0 || ax.state_dim >= n) return "region axis state_dim out of range";
-        if (ax.bins < 1 || ax.bins > (1 << 20)) return "region axis bins out of range";
-        if (!finite(ax.lo) || !finite(ax.hi) || !(ax.hi > ax.lo)) return "region axis needs finite lo < hi";
-        for (int b = 0; b < a; ++b)
-            if (cfg->axis[b].state_dim == ax.state_dim) return "a state component may appear in one region axis only";
-        R *= ax.bins;
-        if (R > (1 << 28)) return "too many regions (> 2^28)";
-    }
+    int64_t R = 0;
+    std::string msg = check_axes(n, cfg->n_axes, cfg->axis, R);
+    if (!msg.empty()) return msg;
+    if (cfg->region_capacity != 0 && (cfg->region_capacity < R || cfg->region_capacity > (1 << 28)))
+        return "region_capacity must be 0 or in [the grid's region count, 2^28]";
     if (cfg->i_max < 0 || cfg->i_max > 254) return "i_max must be in [0, 254]";
     if (n_obs < 0 || n_obs > 6000) return "obstacle count must be in [0, 6000]";
     return "";
@@ -115,6 +144,8 @@ Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs
     const int64_t N = cfg->tree_cap;
     int64_t R = 1;
     for (int a = 0; a < cfg->n_axes; ++a) R *= cfg->axis[a].bins;
+    if (cfg->region_capacity > R) R = cfg->region_capacity;  // room for a finer grid later
+    L.region_cap = R;
     L.va_cap = (int32_t)(N < R ? N : R);
     L.slot_cap = cfg->samples_per_node > 0 ? (int64_t)L.va_cap * cfg->samples_per_node : N;
     L.mask_words = (L.slot_cap + 31) / 32;
@@ -461,21 +492,8 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = cost->kind;
     P.w_effort = cost->w_effort;
-    P.n_axes = cfg->n_axes;
-    int64_t R = 1;
-    for (int a = 0; a < cfg->n_axes; ++a) {
-        const kpx_region_axis& ax = cfg->axis[a];
-        P.ax_dim[a] = ax.state_dim;
-        P.ax_bins[a] = ax.bins;
-        P.ax_wrap[a] = ax.wrap ? 1 : 0;
-        P.ax_lo[a] = ax.lo;
-        const float width = ax.hi - ax.lo;
-        P.ax_scale[a] = (float)ax.bins / width;
-        R *= ax.bins;
-    }
-    fill_region_by_component(P);
+    fill_axes(P, cfg->n_axes, cfg->axis);
     P.N = cfg->tree_cap;
-    P.R = (int32_t)R;
     P.lambda_fixed = cfg->samples_per_node;
     P.i_max = cfg->i_max;
     P.seed_lo = (uint32_t)(cfg->seed & 0xFFFFFFFFull);
@@ -683,6 +701,21 @@ kpx_status kpx_best_trajectory(kpx_planner* p, int32_t capacity, float* states, 
         uint32_t bits = (uint32_t)(h.goal_key >> 32);
         memcpy(out_cost, &bits, sizeof(float));
     }
+    return KPX_OK;
+}
+
+kpx_status kpx_set_regions(kpx_planner* p, int32_t n_axes, const kpx_region_axis* axes) {
+    if (!p) return KPX_E_INVALID;
+    int64_t R = 0;
+    std::string msg = check_axes(p->P.n, n_axes, axes, R);
+    if (!msg.empty()) return fail(p, KPX_E_INVALID, msg);
+    if (R > p->L.region_cap) return fail(p, KPX_E_INVALID, "the new grid needs more regions than the workspace holds "
+                                                          "(kpx_config.region_capacity)");
+    fill_axes(p->P, n_axes, axes);
+    drop_graphs(p);  // the graphs hold the parameter block by value
+    p->graph_state = 0;
+    cudaError_t e = launch_remap_regions(p->P, p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "region remap");
     return KPX_OK;
 }
 
@@ -1223,21 +1256,8 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = cost->kind;
     P.w_effort = cost->w_effort;
-    P.n_axes = cfg->n_axes;
-    int64_t R = 1;
-    for (int a = 0; a < cfg->n_axes; ++a) {
-        const kpx_region_axis& ax = cfg->axis[a];
-        P.ax_dim[a] = ax.state_dim;
-        P.ax_bins[a] = ax.bins;
-        P.ax_wrap[a] = ax.wrap ? 1 : 0;
-        P.ax_lo[a] = ax.lo;
-        const float width = ax.hi - ax.lo;
-        P.ax_scale[a] = (float)ax.bins / width;
-        R *= ax.bins;
-    }
-    fill_region_by_component(P);
+    fill_axes(P, cfg->n_axes, cfg->axis);
     P.N = cfg->tree_cap;
-    P.R = (int32_t)R;
     P.lambda_fixed = cfg->samples_per_node;
     P.i_max = cfg->i_max;
     P.seed_lo = (uint32_t)(cfg->seed & 0xFFFFFFFFull);

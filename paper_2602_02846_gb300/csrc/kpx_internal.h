@@ -124,6 +124,7 @@ struct Layout {
     int64_t slot_cap, mask_words;
     int32_t n_win_tiles, n_prune_tiles;
     int32_t traj_rows;
+    int64_t region_cap;  // regions the arrays hold
 };
 
 // fills the per-component region fields from the per-axis ones
@@ -227,6 +228,9 @@ cudaError_t launch_append(const DevParams& P, cudaStream_t s);
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s);
 cudaError_t launch_end(const DevParams& P, cudaStream_t s);
 cudaError_t launch_path(const DevParams& P, cudaStream_t s);
+// a new region decomposition (already in P): node regions, region keys and
+// owners, dominated bits (kpx_set_regions)
+cudaError_t launch_remap_regions(const DevParams& P, cudaStream_t s);
 cudaError_t launch_gather(const DevParams& P, int32_t first_row, int32_t rows, cudaStream_t s);
 // computes the cached launch shapes (SM count, occupancy) outside any capture
 void prepare_launches(const DevParams& P);

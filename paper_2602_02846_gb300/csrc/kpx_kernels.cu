@@ -306,6 +306,45 @@ __global__ void k_gather(DevParams P, int first, int rows) {
     row[P.n + P.m] = __int_as_float((int)P.K[node]);
 }
 
+// ---------------------------------------------------------------------------
+// a new region decomposition (adaptive delta): every node's region under
+// the new grid; each region's key = the minimum key of its non-terminal
+// nodes; a non-terminal node that does not hold its region's key is
+// dominated; the memoised ancestor bits are cleared for PruneNodes to
+// re-derive.  Terminal nodes keep their set byte.
+// ---------------------------------------------------------------------------
+__global__ void k_remap_clear(DevParams P) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += (int64_t)gridDim.x * blockDim.x) {
+        P.region_key[r] = KEY_INF;
+        P.region_owner[r] = -1;
+    }
+}
+
+template <int N>
+__global__ void k_remap_assign(DevParams P) {
+    const int n_nodes = P.hdr->n_nodes;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += gridDim.x * blockDim.x) {
+        float x[N];
+#pragma unroll
+        for (int d = 0; d < N; ++d) x[d] = P.x[(int64_t)d * P.N + i];
+        const int r = region_of<N>(P, x);
+        P.region[i] = r;
+        if ((P.set[i] & SET_MASK) != SET_T) atomicMin((unsigned long long*)&P.region_key[r], (unsigned long long)P.key[i]);
+    }
+}
+
+__global__ void k_remap_mark(DevParams P) {
+    const int n_nodes = P.hdr->n_nodes;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += gridDim.x * blockDim.x) {
+        const uint8_t sb = P.set[i];
+        if ((sb & SET_MASK) == SET_T) continue;
+        const int r = P.region[i];
+        const bool owner = P.key[i] == P.region_key[r];
+        if (owner) P.region_owner[r] = i;
+        P.set[i] = (uint8_t)((sb & SET_MASK) | (owner ? 0 : SET_DOM));
+    }
+}
+
 int sm_count() {
     static int cached[64] = {};
     int dev = 0;
@@ -417,6 +456,17 @@ cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
 
 cudaError_t launch_end(const DevParams& P, cudaStream_t s) {
     k_end<<<1, 1, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_remap_regions(const DevParams& P, cudaStream_t s) {
+    k_remap_clear<<<persistent_blocks((P.R + 255) / 256, 4), 256, 0, s>>>(P);
+    const int blocks = persistent_blocks((P.N + 255) / 256, 4);
+    if (P.n == 12)
+        k_remap_assign<12><<<blocks, 256, 0, s>>>(P);
+    else
+        k_remap_assign<6><<<blocks, 256, 0, s>>>(P);
+    k_remap_mark<<<blocks, 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,7 @@ class Problem:
     i_max: int = 10
     seed: int = 0
     iterations: int = 200
+    region_capacity: int = 0         # regions the planner's workspace holds (0: this grid's count)
 
     @property
     def n(self) -> int:
