@@ -8,8 +8,14 @@
 // cluster (up to 16 CTAs on 16 SMs).  A hardware cluster barrier
 // (barrier.cluster, release/acquire) stands where the phase kernels have a
 // kernel boundary, and the kernel loops over the iterations of one graph
-// launch on the device.  Every unit of work is the function the phase kernels
-// call (kpx_phases.cuh), so the results are bit-identical to theirs.
+// launch on the device.  The rollouts, the row writes of UpdateTree and
+// PruneNodes are the functions the phase kernels call (kpx_phases.cuh), so
+// the results are bit-identical to theirs.  Two things differ in how the
+// work is arranged.  Each lane keeps its candidate's rollout in registers,
+// and a winner appends its own row at its rank: no re-materialisation.  The
+// V_U filter reads one region key per candidate, and the ranks in slot order
+// come from a prefix over the warps' winner counts, exchanged through
+// distributed shared memory: no region loop, no bitmask scan.
 //
 // Before each iteration the leader thread checks that the iteration fits: at
 // most one 32-slot chunk per warp, and a tree of at most FUSED_MAX_NODES
@@ -36,6 +42,30 @@ __device__ __forceinline__ void cluster_barrier() {
 
 __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(volatile const int32_t*)p; }
 
+// distributed shared memory: a word of CTA `cta`'s copy of a shared array
+__device__ __forceinline__ uint32_t dsmem_addr(const uint32_t* p, uint32_t cta) {
+    const uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(local), "r"(cta));
+    return remote;
+}
+
+__device__ __forceinline__ void dsmem_store(const uint32_t* p, uint32_t cta, uint32_t v) {
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(dsmem_addr(p, cta)), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t dsmem_load(const uint32_t* p, uint32_t cta) {
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(p, cta)) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
 // Leader only: decide whether the next iteration runs here; if so, begin it.
 // remaining: iterations this graph launch still owes (including this one).
 __device__ __forceinline__ void fused_begin(const DevParams& P, kpx_device_header* H, int remaining,
@@ -58,18 +88,19 @@ __device__ __forceinline__ void fused_begin(const DevParams& P, kpx_device_heade
 template <int DYN, int INTEG>
 __global__ void __launch_bounds__(FUSED_THREADS, 1)
     k_fused(DevParams P, int n_iter, cudaGraphConditionalHandle handle, int use_handle) {
-    __shared__ uint32_t s_tile, s_prefix;
+    __shared__ uint32_t s_prefix;
     __shared__ uint32_t s_warp[FUSED_THREADS / 32];
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
-    (void)s_tile;
+    __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // CTA 0's: winners per chunk
+    const int lane = threadIdx.x & 31;
     kpx_device_header* H = P.hdr;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     const int n_cta = (int)gridDim.x;  // the grid is one cluster
     const int64_t gtid = (int64_t)blockIdx.x * FUSED_THREADS + threadIdx.x;
     const int64_t gthreads = (int64_t)n_cta * FUSED_THREADS;
+    const int n_chunks = n_cta * (FUSED_THREADS / 32);  // one per warp of the cluster
     const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) != 0;
-    const kpx_debug_records no_rec{};
     if (leader) fused_begin(P, H, n_iter, gthreads);
     int done = 0;
     for (;;) {
@@ -85,40 +116,52 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
             for (int64_t r = gtid; r < P.R; r += gthreads) P.region_snap[r] = P.region_key[r];
             cluster_barrier();
         }
-        // propagate (Alg. 2): one chunk per warp, warp-major across the CTAs
+        // propagate (Alg. 2): one chunk of 32 slots per warp, warp-major
+        // across the CTAs; each lane keeps its candidate in registers
+        const int64_t chunk = (int64_t)(threadIdx.x >> 5) * n_cta + blockIdx.x;
+        const int64_t slot = chunk * 32 + lane;
+        Candidate<DYN, INTEG> C;
+        C.ok = false;
         {
             uint32_t steps = 0, tests = 0, n_valid = 0;
-            const int64_t chunk = (int64_t)(threadIdx.x >> 5) * n_cta + blockIdx.x;
-            if (chunk * 32 < n_slots)
-                propagate_chunk<DYN, INTEG>(P, n_slots, lam, iter, va, early, chunk, no_rec, 0, steps, tests,
-                                            n_valid);
+            if (slot < n_slots) {
+                roll_candidate<DYN, INTEG>(P, lam, iter, va, early, slot, C, steps, tests);
+                n_valid = C.ok ? 1u : 0u;
+            }
             flush_propagate_counters(H, steps, tests, n_valid);
         }
         cluster_barrier();
-        // mark
-        for (int64_t r = gtid; r < P.R; r += gthreads) mark_region(P, (int)r);
+        // the V_U filter and the winner ranks in slot order: a valid
+        // candidate is its region's winner when the region holds its key;
+        // each warp publishes its winner count to CTA 0 (distributed shared
+        // memory), indexed by chunk
+        const bool won = C.ok && __ldcg(&P.region_key[C.r]) == C.key;
+        const uint32_t word = __ballot_sync(FULL, won);
+        if (lane == 0) dsmem_store(s_cnt + chunk, 0, (uint32_t)__popc(word));
         cluster_barrier();
-        // scan: tiles in CTA order (every CTA of the cluster is resident, so
-        // each look-back wait ends)
         {
-            const int64_t live_words = (n_slots + 31) / 32;
-            const int64_t n_tiles = (live_words + WIN_TILE_WORDS - 1) / WIN_TILE_WORDS;
-            for (int64_t t = blockIdx.x; t < n_tiles; t += n_cta)
-                scan_tile(P, H, (uint32_t)t, n_tiles, live_words, s_warp, s_prefix);
-        }
-        cluster_barrier();
-        // append (UpdateTree) with the capacity rule
-        {
-            const int W = H->n_win;
+            uint32_t before = 0, total = 0;
+            for (int k = lane; k < n_chunks; k += 32) {
+                const uint32_t v = dsmem_load(s_cnt + k, 0);
+                total += v;
+                if (k < chunk) before += v;
+            }
+            before = warp_sum_u32(before);
+            total = warp_sum_u32(total);
+            const int W = (int)total;
             const int n_old = H->n_nodes;
             const int room = P.N - n_old;
             const int kept = W < room ? W : room;
             if (leader) {
+                H->n_win = W;
                 H->n_kept = kept;
                 if (W > kept) set_status(H, KPX_TREE_FULL);
             }
-            for (int64_t w = gtid; w < W; w += gthreads)
-                append_winner<DYN, INTEG>(P, H, (int)w, kept, n_old, lam, iter, va);
+            // UpdateTree (Alg. 4): each winner appends itself at its rank
+            if (won) {
+                const int rank = (int)(before + __popc(word & ((1u << lane) - 1u)));
+                append_row<DYN, INTEG>(P, H, rank, kept, n_old, C.R, C.c, C.r);
+            }
         }
         cluster_barrier();
         // prune (Alg. 3) + compaction of the next V_A

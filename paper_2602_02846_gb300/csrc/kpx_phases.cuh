@@ -138,6 +138,52 @@ __device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P, bool al
 // propagate (Alg. 2): 32 consecutive slots, one per lane.  Slot = rank j of
 // the parent in V_A times lambda plus sample s.
 // ---------------------------------------------------------------------------
+// One slot's rollout: the candidate's validity, region, cost and packed
+// key, with the region's atomicMin done.  Kept by the caller (the fused
+// kernel appends a winner straight from it).
+template <int DYN, int INTEG>
+struct Candidate {
+    LaneRollout<DYN, INTEG> R;
+    bool ok;
+    int r;
+    float c;
+    uint64_t key;
+};
+
+template <int DYN, int INTEG>
+__device__ __forceinline__ void roll_candidate(const DevParams& P, int lam, uint32_t iter, const int32_t* va,
+                                               bool early, int64_t slot, Candidate<DYN, INTEG>& C, uint32_t& steps,
+                                               uint32_t& tests) {
+    constexpr int n = Dims<DYN>::n;
+    C.R.start(P, va, lam, iter, slot);
+    bool ok = true;
+    while (ok && C.R.k < C.R.K) {
+        ++steps;
+        ok = early ? C.R.template advance<false>(P, tests) : C.R.template advance<true>(P, tests);
+    }
+    C.r = -1;
+    C.c = 0.0f;
+    C.key = KEY_INF;
+    if (ok) {
+        C.r = region_of<n>(P, C.R.x);
+        C.c = C.R.cost(P);
+        C.key = pack_key(C.c, (uint32_t)P.N + (uint32_t)slot);
+        if (early) {
+            // collision-after-cost: only a possible winner is checked against obstacles
+            ok = C.key < __ldcg(&P.region_key[C.r]);
+            if (ok) {
+                float x0[n];
+#pragma unroll
+                for (int d = 0; d < n; ++d) x0[d] = P.x[(int64_t)d * P.N + C.R.node];
+                ok = obstacle_pass<DYN, INTEG>(P, x0, C.R.u, C.R.K, steps, tests);
+            }
+        }
+        if (ok && C.key < __ldcg(&P.region_key[C.r]))
+            atomicMin((unsigned long long*)&P.region_key[C.r], (unsigned long long)C.key);
+    }
+    C.ok = ok;
+}
+
 template <int DYN, int INTEG>
 __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_slots, int lam, uint32_t iter,
                                                 const int32_t* va, bool early, int64_t chunk,
@@ -146,41 +192,18 @@ __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_sl
     constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
     const int64_t slot = chunk * 32 + (threadIdx.x & 31);
     if (slot >= n_slots) return;
-    LaneRollout<DYN, INTEG> R;
-    R.start(P, va, lam, iter, slot);
-    bool ok = true;
-    while (ok && R.k < R.K) {
-        ++steps;
-        ok = early ? R.template advance<false>(P, tests) : R.template advance<true>(P, tests);
-    }
-    int r = -1;
-    uint64_t key = KEY_INF;
-    if (ok) {
-        r = region_of<n>(P, R.x);
-        key = pack_key(R.cost(P), (uint32_t)P.N + (uint32_t)slot);
-        if (early) {
-            // collision-after-cost: only a possible winner is checked against obstacles
-            ok = key < __ldcg(&P.region_key[r]);
-            if (ok) {
-                float x0[n];
-#pragma unroll
-                for (int d = 0; d < n; ++d) x0[d] = P.x[(int64_t)d * P.N + R.node];
-                ok = obstacle_pass<DYN, INTEG>(P, x0, R.u, R.K, steps, tests);
-            }
-        }
-        if (ok && key < __ldcg(&P.region_key[r]))
-            atomicMin((unsigned long long*)&P.region_key[r], (unsigned long long)key);
-    }
-    n_valid += ok ? 1u : 0u;
+    Candidate<DYN, INTEG> C;
+    roll_candidate<DYN, INTEG>(P, lam, iter, va, early, slot, C, steps, tests);
+    n_valid += C.ok ? 1u : 0u;
     if (rec_on && slot < rec.capacity) {
-        rec.valid[slot] = ok ? 1 : 0;
-        rec.region[slot] = ok ? r : -1;
-        rec.key[slot] = ok ? key : KEY_INF;
-        rec.K[slot] = R.K;
+        rec.valid[slot] = C.ok ? 1 : 0;
+        rec.region[slot] = C.ok ? C.r : -1;
+        rec.key[slot] = C.ok ? C.key : KEY_INF;
+        rec.K[slot] = C.R.K;
 #pragma unroll
-        for (int d = 0; d < n; ++d) rec.x[(int64_t)d * rec.capacity + slot] = R.x[d];
+        for (int d = 0; d < n; ++d) rec.x[(int64_t)d * rec.capacity + slot] = C.R.x[d];
 #pragma unroll
-        for (int d = 0; d < m; ++d) rec.u[(int64_t)d * rec.capacity + slot] = R.u[d];
+        for (int d = 0; d < m; ++d) rec.u[(int64_t)d * rec.capacity + slot] = C.R.u[d];
     }
 }
 
@@ -267,23 +290,13 @@ __device__ __forceinline__ void scan_tile(const DevParams& P, kpx_device_header*
 // capacity restore their region from the snapshot.  Goal nodes lower the
 // solution key.
 // ---------------------------------------------------------------------------
+// The row writes of winner w (rank in slot order) with rollout Rw, cost c,
+// region r: appended at n_old + w when w < kept, else the capacity rule
+// restores the region's key.
 template <int DYN, int INTEG>
-__device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_header* H, int w, int kept, int n_old,
-                                              int lam, uint32_t iter, const int32_t* va) {
+__device__ __forceinline__ void append_row(const DevParams& P, kpx_device_header* H, int w, int kept, int n_old,
+                                           const LaneRollout<DYN, INTEG>& Rw, float c, int r) {
     constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
-    const int slot = P.win_slot[w];
-    LaneRollout<DYN, INTEG> Rw;
-    Rw.start(P, va, lam, iter, (int64_t)slot);
-    uint32_t te_unused = 0;
-    for (int k = 0; k < Rw.K; ++k) Rw.template advance<false>(P, te_unused);
-    const float c = Rw.cost(P);
-    const int r = region_of<n>(P, Rw.x);
-    const uint64_t cand_key = pack_key(c, (uint32_t)P.N + (uint32_t)slot);
-    if (P.region_key[r] != cand_key) {
-        set_status(H, KPX_E_INTERNAL);
-        H->err_info[1] = (uint32_t)slot;
-        return;
-    }
     if (w < kept) {
         const int id = n_old + w;
 #pragma unroll
@@ -307,6 +320,26 @@ __device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_hea
     } else {
         P.region_key[r] = P.region_snap[r];
     }
+}
+
+template <int DYN, int INTEG>
+__device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_header* H, int w, int kept, int n_old,
+                                              int lam, uint32_t iter, const int32_t* va) {
+    constexpr int n = Dims<DYN>::n;
+    const int slot = P.win_slot[w];
+    LaneRollout<DYN, INTEG> Rw;
+    Rw.start(P, va, lam, iter, (int64_t)slot);
+    uint32_t te_unused = 0;
+    for (int k = 0; k < Rw.K; ++k) Rw.template advance<false>(P, te_unused);
+    const float c = Rw.cost(P);
+    const int r = region_of<n>(P, Rw.x);
+    const uint64_t cand_key = pack_key(c, (uint32_t)P.N + (uint32_t)slot);
+    if (P.region_key[r] != cand_key) {
+        set_status(H, KPX_E_INTERNAL);
+        H->err_info[1] = (uint32_t)slot;
+        return;
+    }
+    append_row<DYN, INTEG>(P, H, w, kept, n_old, Rw, c, r);
 }
 
 // ---------------------------------------------------------------------------
