@@ -246,6 +246,7 @@ void choose_grid(DevParams& P, const float* aabb, int n_obs, float scale = 1.0f)
             }
             entries += cells;
         }
+        P.grid_entries = (int32_t)(entries < P.grid_cap ? entries : P.grid_cap);
         if (entries <= P.grid_cap || (g[0] == 1 && g[1] == 1 && g[2] == 1)) break;
         int big = g[0] >= g[1] && g[0] >= g[2] ? 0 : (g[1] >= g[2] ? 1 : 2);
         g[big] = (g[big] + 1) / 2;

@@ -196,17 +196,36 @@ __device__ __forceinline__ bool bounds_ok(const DevParams& P, const float (&x)[N
 // point's cell are tested (the list holds every box overlapping the cell,
 // so the verdict equals testing all boxes).  The point must lie in the
 // workspace box.  `tests` accumulates the number of boxes examined.
-__device__ __forceinline__ bool hits_obstacle(const DevParams& P, float px, float py, float pz, uint32_t& tests) {
+// Where the grid is read from: the workspace (global memory, read-only path)
+// or a copy in shared memory (the fused kernel stages small grids).
+struct GridView {
+    const int32_t* cell_start;
+    const float4* cell_box;
+};
+
+template <bool SMEM, typename T>
+__device__ __forceinline__ T grid_ld(const T* p) {
+    if constexpr (SMEM)
+        return *p;
+    else
+        return __ldg(p);
+}
+
+template <bool SMEM = false>
+__device__ __forceinline__ bool hits_obstacle_in(const DevParams& P, const GridView& G, float px, float py, float pz,
+                                                 uint32_t& tests) {
     if (P.n_obs == 0) return false;
     const int cx = grid_cell(px, P.ws_lo[0], P.grid_inv[0], P.grid_n[0]);
     const int cy = grid_cell(py, P.ws_lo[1], P.grid_inv[1], P.grid_n[1]);
     const int cz = grid_cell(pz, P.ws_lo[2], P.grid_inv[2], P.grid_n[2]);
     const int c = (cz * P.grid_n[1] + cy) * P.grid_n[0] + cx;
-    const int e0 = __ldg(P.cell_start + c);
-    const int e1 = min(__ldg(P.cell_start + c + 1), P.grid_cap);  // the build guarantees <= grid_cap
+    // the build keeps every offset within grid_entries <= grid_cap; a
+    // shared-memory copy holds exactly grid_entries boxes
+    const int e0 = grid_ld<SMEM>(G.cell_start + c);
+    const int e1 = min(grid_ld<SMEM>(G.cell_start + c + 1), SMEM ? P.grid_entries : P.grid_cap);
     for (int e = e0; e < e1; ++e) {
-        const float4 lo = __ldg(P.cell_box + 2 * e);
-        const float4 hi = __ldg(P.cell_box + 2 * e + 1);
+        const float4 lo = grid_ld<SMEM>(G.cell_box + 2 * e);
+        const float4 hi = grid_ld<SMEM>(G.cell_box + 2 * e + 1);
         const bool in = (px >= lo.x) & (px <= hi.x) & (py >= lo.y) & (py <= hi.y) & (pz >= lo.z) & (pz <= hi.z);
         if (in) {
             tests += (uint32_t)(e - e0 + 1);
@@ -215,6 +234,10 @@ __device__ __forceinline__ bool hits_obstacle(const DevParams& P, float px, floa
     }
     tests += (uint32_t)(e1 - e0);
     return false;
+}
+
+__device__ __forceinline__ bool hits_obstacle(const DevParams& P, float px, float py, float pz, uint32_t& tests) {
+    return hits_obstacle_in<false>(P, GridView{P.cell_start, P.cell_box}, px, py, pz, tests);
 }
 
 // --------------------------------------------------------------------------
@@ -290,8 +313,8 @@ struct Stepper<KPX_DUBINS6, KPX_RK4> {
 
 // Obstacle pass alone over a re-integrated segment (used after an early cost
 // check; same integration arithmetic as rollout()).
-template <int DYN, int INTEG>
-__device__ __forceinline__ bool obstacle_pass(const DevParams& P, float (&x)[Dims<DYN>::n],
+template <int DYN, int INTEG, bool SMEM = false>
+__device__ __forceinline__ bool obstacle_pass(const DevParams& P, const GridView& G, float (&x)[Dims<DYN>::n],
                                               const float (&u)[Dims<DYN>::m], int K, uint32_t& steps,
                                               uint32_t& tests) {
     Stepper<DYN, INTEG> st;
@@ -299,7 +322,7 @@ __device__ __forceinline__ bool obstacle_pass(const DevParams& P, float (&x)[Dim
     for (int k = 0; k < K; ++k) {
         st.advance(P, x, u);
         ++steps;
-        if (hits_obstacle(P, x[0], x[1], x[2], tests)) return false;
+        if (hits_obstacle_in<SMEM>(P, G, x[0], x[1], x[2], tests)) return false;
     }
     return true;
 }
@@ -394,8 +417,8 @@ struct LaneRollout {
 
     // One step; returns whether the new point is valid (bounds, and the
     // obstacles when OBST).
-    template <bool OBST>
-    __device__ __forceinline__ bool advance(const DevParams& P, uint32_t& tests) {
+    template <bool OBST, bool SMEM = false>
+    __device__ __forceinline__ bool advance_in(const DevParams& P, const GridView& G, uint32_t& tests) {
         const float p0 = x[0], p1 = x[1], p2 = x[2];
         st.advance(P, x, u);
         ++k;
@@ -404,8 +427,13 @@ struct LaneRollout {
             len = len + sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         }
         if (!bounds_ok(P, x)) return false;
-        if (OBST && hits_obstacle(P, x[0], x[1], x[2], tests)) return false;
+        if (OBST && hits_obstacle_in<SMEM>(P, G, x[0], x[1], x[2], tests)) return false;
         return true;
+    }
+
+    template <bool OBST>
+    __device__ __forceinline__ bool advance(const DevParams& P, uint32_t& tests) {
+        return advance_in<OBST, false>(P, GridView{P.cell_start, P.cell_box}, tests);
     }
 
     __device__ __forceinline__ float cost(const DevParams& P) const { return cost0 + edge_cost<m>(P, K, len, u); }

@@ -17,6 +17,9 @@
 // come from a prefix over the warps' winner counts, exchanged through
 // distributed shared memory: no region loop, no bitmask scan.
 //
+// A small obstacle grid is copied into shared memory at the start: the
+// cluster barriers discard the L1 cache, and every rollout step reads the grid.
+//
 // Before each iteration the leader thread checks that the iteration fits: at
 // most one 32-slot chunk per warp, and a tree of at most FUSED_MAX_NODES
 // nodes.  When it does not fit, the kernel stops and leaves the number of
@@ -34,6 +37,14 @@ namespace {
 constexpr int FUSED_THREADS = 256;  // = WIN_THREADS = PRUNE_THREADS (block-wide units)
 constexpr int FUSED_MAX_CLUSTER = 16;
 constexpr int FUSED_MAX_NODES = 32768;
+// obstacle grids up to this size are copied into shared memory: every cluster
+// barrier (acquire) discards the L1 cache, and the rollouts read the grid at
+// every step
+constexpr size_t FUSED_GRID_SMEM_MAX = 180 * 1024;
+
+__host__ __device__ inline size_t grid_start_bytes(int32_t n_cells) {
+    return ((size_t)(n_cells + 1) * sizeof(int32_t) + 15) / 16 * 16;
+}
 static_assert(FUSED_THREADS == WIN_THREADS && FUSED_THREADS == PRUNE_THREADS, "block-wide units");
 
 __device__ __forceinline__ void cluster_barrier() {
@@ -87,7 +98,8 @@ __device__ __forceinline__ void fused_begin(const DevParams& P, kpx_device_heade
 
 template <int DYN, int INTEG>
 __global__ void __launch_bounds__(FUSED_THREADS, 1)
-    k_fused(DevParams P, int n_iter, cudaGraphConditionalHandle handle, int use_handle) {
+    k_fused(DevParams P, int n_iter, cudaGraphConditionalHandle handle, int use_handle, int grid_smem) {
+    extern __shared__ __align__(16) unsigned char fused_grid[];
     __shared__ uint32_t s_prefix;
     __shared__ uint32_t s_warp[FUSED_THREADS / 32];
     __shared__ int32_t s_parent[PRUNE_TILE];
@@ -101,6 +113,15 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     const int64_t gthreads = (int64_t)n_cta * FUSED_THREADS;
     const int n_chunks = n_cta * (FUSED_THREADS / 32);  // one per warp of the cluster
     const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) != 0;
+    GridView G{P.cell_start, P.cell_box};
+    if (grid_smem) {  // the obstacle grid is read-only while planning
+        int32_t* sc = reinterpret_cast<int32_t*>(fused_grid);
+        float4* sb = reinterpret_cast<float4*>(fused_grid + grid_start_bytes(P.n_cells));
+        for (int i = threadIdx.x; i <= P.n_cells; i += FUSED_THREADS) sc[i] = P.cell_start[i];
+        for (int i = threadIdx.x; i < 2 * P.grid_entries; i += FUSED_THREADS) sb[i] = P.cell_box[i];
+        __syncthreads();
+        G = GridView{sc, sb};
+    }
     if (leader) fused_begin(P, H, n_iter, gthreads);
     int done = 0;
     for (;;) {
@@ -125,7 +146,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         {
             uint32_t steps = 0, tests = 0, n_valid = 0;
             if (slot < n_slots) {
-                roll_candidate<DYN, INTEG>(P, lam, iter, va, early, slot, C, steps, tests);
+                if (grid_smem)
+                    roll_candidate<DYN, INTEG, true>(P, G, lam, iter, va, early, slot, C, steps, tests);
+                else
+                    roll_candidate<DYN, INTEG, false>(P, G, lam, iter, va, early, slot, C, steps, tests);
                 n_valid = C.ok ? 1u : 0u;
             }
             flush_propagate_counters(H, steps, tests, n_valid);
@@ -194,9 +218,15 @@ int fused_cluster_size_t(const DevParams&, int) {
             cudaSuccess) {
             cudaGetLastError();
         }
+        if (cudaFuncSetAttribute(k_fused<DYN, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)FUSED_GRID_SMEM_MAX) != cudaSuccess) {
+            cudaGetLastError();
+            return size;  // 0: unavailable
+        }
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(FUSED_MAX_CLUSTER);
         cfg.blockDim = dim3(FUSED_THREADS);
+        cfg.dynamicSmemBytes = FUSED_GRID_SMEM_MAX;  // the cluster must fit with a staged grid
         int cl = 0;
         if (cudaOccupancyMaxPotentialClusterSize(&cl, (const void*)k_fused<DYN, INTEG>, &cfg) != cudaSuccess) {
             cudaGetLastError();
@@ -215,10 +245,12 @@ cudaError_t launch_fused_t(const DevParams& P, int n_iter, cudaGraphConditionalH
                            cudaStream_t s) {
     const int cl = fused_cluster_size_t<DYN, INTEG>(P, 0);
     if (cl == 0) return cudaErrorNotSupported;
+    const size_t grid_bytes = grid_start_bytes(P.n_cells) + (size_t)P.grid_entries * 2 * sizeof(float4);
+    const int grid_smem = P.n_obs > 0 && grid_bytes <= FUSED_GRID_SMEM_MAX ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cl);
     cfg.blockDim = dim3(FUSED_THREADS);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = grid_smem ? grid_bytes : 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -227,7 +259,7 @@ cudaError_t launch_fused_t(const DevParams& P, int n_iter, cudaGraphConditionalH
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_fused<DYN, INTEG>, P, n_iter, handle, use_handle);
+    return cudaLaunchKernelEx(&cfg, k_fused<DYN, INTEG>, P, n_iter, handle, use_handle, grid_smem);
 }
 
 #define KPX_FUSED_DISPATCH(FN, P, ...)                                                   \

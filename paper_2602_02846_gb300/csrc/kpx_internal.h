@@ -73,6 +73,7 @@ struct DevParams {
     float grid_inv[3];
     int32_t n_cells;
     int32_t grid_cap;     // entries reserved in cell_box
+    int32_t grid_entries; // entries the grid build writes (computed on the host, <= grid_cap)
     // device arrays (inside the caller's workspace)
     kpx_device_header* hdr;
     float* x;

@@ -150,16 +150,18 @@ struct Candidate {
     uint64_t key;
 };
 
-template <int DYN, int INTEG>
-__device__ __forceinline__ void roll_candidate(const DevParams& P, int lam, uint32_t iter, const int32_t* va,
-                                               bool early, int64_t slot, Candidate<DYN, INTEG>& C, uint32_t& steps,
-                                               uint32_t& tests) {
+// G: where the obstacle grid is read (SMEM: a shared-memory copy)
+template <int DYN, int INTEG, bool SMEM = false>
+__device__ __forceinline__ void roll_candidate(const DevParams& P, const GridView& G, int lam, uint32_t iter,
+                                               const int32_t* va, bool early, int64_t slot, Candidate<DYN, INTEG>& C,
+                                               uint32_t& steps, uint32_t& tests) {
     constexpr int n = Dims<DYN>::n;
     C.R.start(P, va, lam, iter, slot);
     bool ok = true;
     while (ok && C.R.k < C.R.K) {
         ++steps;
-        ok = early ? C.R.template advance<false>(P, tests) : C.R.template advance<true>(P, tests);
+        ok = early ? C.R.template advance_in<false, SMEM>(P, G, tests)
+                   : C.R.template advance_in<true, SMEM>(P, G, tests);
     }
     C.r = -1;
     C.c = 0.0f;
@@ -175,7 +177,7 @@ __device__ __forceinline__ void roll_candidate(const DevParams& P, int lam, uint
                 float x0[n];
 #pragma unroll
                 for (int d = 0; d < n; ++d) x0[d] = P.x[(int64_t)d * P.N + C.R.node];
-                ok = obstacle_pass<DYN, INTEG>(P, x0, C.R.u, C.R.K, steps, tests);
+                ok = obstacle_pass<DYN, INTEG, SMEM>(P, G, x0, C.R.u, C.R.K, steps, tests);
             }
         }
         if (ok && C.key < __ldcg(&P.region_key[C.r]))
@@ -193,7 +195,7 @@ __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_sl
     const int64_t slot = chunk * 32 + (threadIdx.x & 31);
     if (slot >= n_slots) return;
     Candidate<DYN, INTEG> C;
-    roll_candidate<DYN, INTEG>(P, lam, iter, va, early, slot, C, steps, tests);
+    roll_candidate<DYN, INTEG>(P, GridView{P.cell_start, P.cell_box}, lam, iter, va, early, slot, C, steps, tests);
     n_valid += C.ok ? 1u : 0u;
     if (rec_on && slot < rec.capacity) {
         rec.valid[slot] = C.ok ? 1 : 0;
