@@ -211,18 +211,27 @@ __device__ __forceinline__ T grid_ld(const T* p) {
         return __ldg(p);
 }
 
-template <bool SMEM = false>
-__device__ __forceinline__ bool hits_obstacle_in(const DevParams& P, const GridView& G, float px, float py, float pz,
-                                                 uint32_t& tests) {
-    if (P.n_obs == 0) return false;
+// The entry range [e0, e1) of the point's cell.  Every coordinate, NaN and
+// infinities included, maps to a cell of the grid, so the read stays in
+// range for any point.
+template <bool SMEM>
+__device__ __forceinline__ void cell_range(const DevParams& P, const GridView& G, float px, float py, float pz,
+                                           int& e0, int& e1) {
     const int cx = grid_cell(px, P.ws_lo[0], P.grid_inv[0], P.grid_n[0]);
     const int cy = grid_cell(py, P.ws_lo[1], P.grid_inv[1], P.grid_n[1]);
     const int cz = grid_cell(pz, P.ws_lo[2], P.grid_inv[2], P.grid_n[2]);
     const int c = (cz * P.grid_n[1] + cy) * P.grid_n[0] + cx;
     // the build keeps every offset within grid_entries <= grid_cap; a
     // shared-memory copy holds exactly grid_entries boxes
-    const int e0 = grid_ld<SMEM>(G.cell_start + c);
-    const int e1 = min(grid_ld<SMEM>(G.cell_start + c + 1), SMEM ? P.grid_entries : P.grid_cap);
+    e0 = grid_ld<SMEM>(G.cell_start + c);
+    e1 = min(grid_ld<SMEM>(G.cell_start + c + 1), SMEM ? P.grid_entries : P.grid_cap);
+}
+
+// Tests the point against the boxes e0..e1-1 in order and stops at the
+// first that contains it; `tests` accumulates the boxes examined.
+template <bool SMEM>
+__device__ __forceinline__ bool walk_cell(const GridView& G, float px, float py, float pz, int e0, int e1,
+                                          uint32_t& tests) {
     for (int e = e0; e < e1; ++e) {
         const float4 lo = grid_ld<SMEM>(G.cell_box + 2 * e);
         const float4 hi = grid_ld<SMEM>(G.cell_box + 2 * e + 1);
@@ -232,8 +241,17 @@ __device__ __forceinline__ bool hits_obstacle_in(const DevParams& P, const GridV
             return true;
         }
     }
-    tests += (uint32_t)(e1 - e0);
+    tests += (uint32_t)(e1 > e0 ? e1 - e0 : 0);
     return false;
+}
+
+template <bool SMEM = false>
+__device__ __forceinline__ bool hits_obstacle_in(const DevParams& P, const GridView& G, float px, float py, float pz,
+                                                 uint32_t& tests) {
+    if (P.n_obs == 0) return false;
+    int e0, e1;
+    cell_range<SMEM>(P, G, px, py, pz, e0, e1);
+    return walk_cell<SMEM>(G, px, py, pz, e0, e1, tests);
 }
 
 __device__ __forceinline__ bool hits_obstacle(const DevParams& P, float px, float py, float pz, uint32_t& tests) {
@@ -259,11 +277,14 @@ __device__ __forceinline__ float edge_cost(const DevParams& P, int K, float path
     return dur * fmaf(P.w_effort, e, 1.0f);
 }
 
-// One integrator per (system, scheme).  The generic stepper applies step();
-// the Dubins RK4 stepper uses that yaw, pitch and speed move linearly under a
-// constant control: the two RK4 midpoint stages coincide (k2 = k3) and the
-// end-of-step angles are the next step's start angles, so one step needs two
-// new sine/cosine pairs instead of eight.
+// One integrator per (system, scheme).  The generic stepper applies step().
+// The Dubins RK4 stepper uses that yaw and pitch turn at a constant rate
+// under a constant control: the two RK4 midpoint stages coincide (k2 = k3),
+// and the sine and cosine at the midpoint and at the end of a step follow
+// from those at its start by two rotations through the half-step angle,
+// whose sine and cosine are evaluated once per rollout.  A step thus needs
+// no sine or cosine evaluation; the angles of the state itself are still
+// advanced by one rounding per step.
 template <int DYN, int INTEG>
 struct Stepper {
     static constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
@@ -273,26 +294,38 @@ struct Stepper {
     }
 };
 
+// (s, c) <- sin and cos of (a + d), from those of a and of d
+__device__ __forceinline__ void rotate(float& s, float& c, float sd, float cd) {
+    const float s1 = fmaf(s, cd, c * sd);
+    const float c1 = fmaf(c, cd, -(s * sd));
+    s = s1;
+    c = c1;
+}
+
 template <>
 struct Stepper<KPX_DUBINS6, KPX_RK4> {
     static constexpr int n = 6, m = 3;
-    float sp, cp, sg, cg;  // sin/cos of yaw and pitch at the current state
-    __device__ __forceinline__ void init(const DevParams&, const float (&x)[n], const float (&)[m]) {
+    float sp, cp, sg, cg;      // sin/cos of yaw and pitch at the current state
+    float sdp, cdp, sdg, cdg;  // sin/cos of the half-step turns h u0 / 2 and h u1 / 2
+    __device__ __forceinline__ void init(const DevParams& P, const float (&x)[n], const float (&u)[m]) {
         fast_sincos(x[3], sp, cp);
         fast_sincos(x[4], sg, cg);
+        const float hh = 0.5f * P.h;
+        sincosf(hh * u[0], &sdp, &cdp);
+        sincosf(hh * u[1], &sdg, &cdg);
     }
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
         const float h = P.h;
         const float hh = 0.5f * h;
         const float h6 = h * (1.0f / 6.0f);
         const float vs = x[5];
-        const float ym = fmaf(hh, u[0], x[3]), gm = fmaf(hh, u[1], x[4]), vm = fmaf(hh, u[2], x[5]);
-        const float ye = fmaf(h, u[0], x[3]), ge = fmaf(h, u[1], x[4]), ve = fmaf(h, u[2], x[5]);
-        float spm, cpm, sgm, cgm, spe, cpe, sge, cge;
-        fast_sincos(ym, spm, cpm);
-        fast_sincos(gm, sgm, cgm);
-        fast_sincos(ye, spe, cpe);
-        fast_sincos(ge, sge, cge);
+        const float vm = fmaf(hh, u[2], x[5]), ve = fmaf(h, u[2], x[5]);
+        float spm = sp, cpm = cp, sgm = sg, cgm = cg;
+        rotate(spm, cpm, sdp, cdp);
+        rotate(sgm, cgm, sdg, cdg);
+        float spe = spm, cpe = cpm, sge = sgm, cge = cgm;
+        rotate(spe, cpe, sdp, cdp);
+        rotate(sge, cge, sdg, cdg);
         // f = v (cos yaw cos pitch, sin yaw cos pitch, sin pitch) at start, mid, end
         const float as = vs * cg, am = vm * cgm, ae = ve * cge;
         const float fx = fmaf(4.0f, am * cpm, fmaf(as, cp, ae * cpe));
@@ -301,8 +334,8 @@ struct Stepper<KPX_DUBINS6, KPX_RK4> {
         x[0] = fmaf(h6, fx, x[0]);
         x[1] = fmaf(h6, fy, x[1]);
         x[2] = fmaf(h6, fz, x[2]);
-        x[3] = ye;
-        x[4] = ge;
+        x[3] = fmaf(h, u[0], x[3]);
+        x[4] = fmaf(h, u[1], x[4]);
         x[5] = ve;
         sp = spe;
         cp = cpe;
@@ -415,10 +448,8 @@ struct LaneRollout {
         k = 0;
     }
 
-    // One step; returns whether the new point is valid (bounds, and the
-    // obstacles when OBST).
-    template <bool OBST, bool SMEM = false>
-    __device__ __forceinline__ bool advance_in(const DevParams& P, const GridView& G, uint32_t& tests) {
+    // One integration step and its path length, no checks.
+    __device__ __forceinline__ void integrate(const DevParams& P) {
         const float p0 = x[0], p1 = x[1], p2 = x[2];
         st.advance(P, x, u);
         ++k;
@@ -426,6 +457,13 @@ struct LaneRollout {
             const float dx = x[0] - p0, dy = x[1] - p1, dz = x[2] - p2;
             len = len + sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         }
+    }
+
+    // One step; returns whether the new point is valid (bounds, and the
+    // obstacles when OBST).
+    template <bool OBST, bool SMEM = false>
+    __device__ __forceinline__ bool advance_in(const DevParams& P, const GridView& G, uint32_t& tests) {
+        integrate(P);
         if (!bounds_ok(P, x)) return false;
         if (OBST && hits_obstacle_in<SMEM>(P, G, x[0], x[1], x[2], tests)) return false;
         return true;

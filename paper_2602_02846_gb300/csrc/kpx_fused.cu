@@ -137,21 +137,30 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
             for (int64_t r = gtid; r < P.R; r += gthreads) P.region_snap[r] = P.region_key[r];
             cluster_barrier();
         }
-        // propagate (Alg. 2): one chunk of 32 slots per warp, warp-major
-        // across the CTAs; each lane keeps its candidate in registers
+        // propagate (Alg. 2): one chunk of 32 / g slots per warp, warp-major
+        // across the CTAs; g lanes share a rollout when the slots fill at
+        // most half of the cluster's threads.  The lane that keeps a
+        // candidate holds it in registers.
+        const int g = early ? 1 : coop_lanes(n_slots, gthreads);
         const int64_t chunk = (int64_t)(threadIdx.x >> 5) * n_cta + blockIdx.x;
-        const int64_t slot = chunk * 32 + lane;
+        const int64_t slot = chunk * (32 / g) + lane / g;
         Candidate<DYN, INTEG> C;
         C.ok = false;
         {
             uint32_t steps = 0, tests = 0, n_valid = 0;
-            if (slot < n_slots) {
+            const bool live = slot < n_slots;
+            if (g > 1) {  // all lanes of the warp take part
+                if (grid_smem)
+                    roll_candidate_coop<DYN, INTEG, true>(P, G, lam, iter, va, live, slot, g, C, steps, tests);
+                else
+                    roll_candidate_coop<DYN, INTEG, false>(P, G, lam, iter, va, live, slot, g, C, steps, tests);
+            } else if (live) {
                 if (grid_smem)
                     roll_candidate<DYN, INTEG, true>(P, G, lam, iter, va, early, slot, C, steps, tests);
                 else
                     roll_candidate<DYN, INTEG, false>(P, G, lam, iter, va, early, slot, C, steps, tests);
-                n_valid = C.ok ? 1u : 0u;
             }
+            n_valid = C.ok ? 1u : 0u;
             flush_propagate_counters(H, steps, tests, n_valid);
         }
         cluster_barrier();

@@ -103,7 +103,10 @@ struct DevParams {
 
 // FP32 cell index along one axis, identical on host and device (one
 // rounding per operation, no contraction).  Monotone in c, so a box that
-// contains a point always lists the point's cell.
+// contains a point always lists the point's cell.  t is clamped to
+// [0, n - 1] in floating point first (fmaxf maps NaN to 0), so truncation
+// equals floor and every input, NaN and infinities included, lands in a
+// cell: the same index as clamp(floor(t), 0, n - 1).
 __host__ __device__ inline int grid_cell(float c, float lo, float inv, int n) {
 #ifdef __CUDA_ARCH__
     const float t = __fmul_rn(__fsub_rn(c, lo), inv);
@@ -111,9 +114,7 @@ __host__ __device__ inline int grid_cell(float c, float lo, float inv, int n) {
     volatile float d = c - lo;
     const float t = d * inv;
 #endif
-    int i = (int)floorf(t);
-    i = i < 0 ? 0 : i;
-    return i > n - 1 ? n - 1 : i;
+    return (int)fminf(fmaxf(t, 0.0f), (float)(n - 1));
 }
 
 // Workspace layout (byte offsets from the workspace base).

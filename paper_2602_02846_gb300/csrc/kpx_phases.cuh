@@ -186,6 +186,90 @@ __device__ __forceinline__ void roll_candidate(const DevParams& P, const GridVie
     C.ok = ok;
 }
 
+// Lanes per rollout for n_slots rollouts on `threads` threads: the largest
+// power of two up to 32 with n_slots * g <= threads (1 when the slots fill
+// more than half of the threads).
+__device__ __forceinline__ int coop_lanes(int64_t n_slots, int64_t threads) {
+    int g = 1;
+    while (g < 32 && n_slots * (int64_t)(2 * g) <= threads) g *= 2;
+    return g;
+}
+
+// Rollouts shared by the g lanes of aligned groups of a warp (g a power of
+// two, 2..32; called by all 32 lanes, `live` false for a group without a
+// slot): every lane of a group integrates the group's rollout, and after
+// each block of g steps lane gl = lane % g checks the block's step gl
+// (bounds, then obstacles).  The block's first failing step ends the
+// rollout.  A rollout of K steps thus waits on ceil(K / g) rounds of checks
+// instead of K.  The blocks are warp-uniform (the warp runs until its
+// longest rollout ends, the groups predicated) so that the warp never splits
+// into groups that would then issue one after another.  Verdict, end state,
+// cost and the step and box-test counts equal those of roll_candidate()
+// with early reject off; lane 0 of a group keeps the candidate and the
+// counts, the other lanes neither.
+template <int DYN, int INTEG, bool SMEM>
+__device__ __forceinline__ void roll_candidate_coop(const DevParams& P, const GridView& G, int lam, uint32_t iter,
+                                                    const int32_t* va, bool live, int64_t slot, int g,
+                                                    Candidate<DYN, INTEG>& C, uint32_t& steps, uint32_t& tests) {
+    constexpr int n = Dims<DYN>::n;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane & (g - 1);
+    const int base = lane - gl;
+    const uint32_t gbits = g == 32 ? FULL : (1u << g) - 1u;
+    C.R.K = 0;
+    C.R.k = 0;
+    if (live) C.R.start(P, va, lam, iter, slot);
+    bool run = live;  // the group's rollout has not ended
+    bool ok = live;
+    uint32_t n_steps = 0, n_tests = 0;
+    const int k_warp = (int)__reduce_max_sync(FULL, (uint32_t)(live ? C.R.K : 0));
+    for (int k0 = 0; k0 < k_warp; k0 += g) {  // warp-uniform
+        const int nb = run ? min(g, C.R.K - k0) : 0;  // uniform within the group
+        float mx[n];
+#pragma unroll
+        for (int d = 0; d < n; ++d) mx[d] = 0.0f;
+        for (int i = 0; i < nb; ++i) {
+            C.R.integrate(P);
+#pragma unroll
+            for (int d = 0; d < n; ++d) mx[d] = i == gl ? C.R.x[d] : mx[d];
+        }
+        bool bad = false;
+        uint32_t t = 0;
+        if (gl < nb) bad = !bounds_ok(P, mx) || hits_obstacle_in<SMEM>(P, G, mx[0], mx[1], mx[2], t);
+        const uint32_t b = (__ballot_sync(FULL, bad) >> base) & gbits;
+        const int f = b ? __ffs(b) - 1 : nb;  // the block's first failing step
+        uint32_t tt = gl <= f ? t : 0u;
+        for (int o = g >> 1; o > 0; o >>= 1) tt += __shfl_xor_sync(FULL, tt, o);
+        if (run) {
+            n_tests += tt;
+            if (f < nb) {
+                n_steps += (uint32_t)(f + 1);
+                ok = false;
+                run = false;
+            } else {
+                n_steps += (uint32_t)nb;
+                run = C.R.k < C.R.K;
+            }
+        }
+    }
+    C.r = -1;
+    C.c = 0.0f;
+    C.key = KEY_INF;
+    ok = ok && gl == 0;
+    if (gl == 0) {
+        steps += n_steps;
+        tests += n_tests;
+    }
+    if (ok) {
+        C.r = region_of<n>(P, C.R.x);
+        C.c = C.R.cost(P);
+        C.key = pack_key(C.c, (uint32_t)P.N + (uint32_t)slot);
+        if (C.key < __ldcg(&P.region_key[C.r]))
+            atomicMin((unsigned long long*)&P.region_key[C.r], (unsigned long long)C.key);
+    }
+    C.ok = ok;
+}
+
 template <int DYN, int INTEG>
 __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_slots, int lam, uint32_t iter,
                                                 const int32_t* va, bool early, int64_t chunk,
