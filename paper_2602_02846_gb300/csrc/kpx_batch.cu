@@ -53,7 +53,7 @@ __device__ void block_prefix(int B, int64_t* out, F value_of) {
 
 // per-problem counters, then the chunk and scan-tile numbering
 __global__ void __launch_bounds__(1024) k_b_begin(BatchParams BP) {
-    for (int p = threadIdx.x; p < BP.B; p += blockDim.x) begin_counters(BP.Ps[p]);
+    for (int p = threadIdx.x; p < BP.B; p += blockDim.x) begin_counters(BP.Ps[p], BP.Ps[p].hdr);
     __syncthreads();
     block_prefix(BP.B, BP.chunk_prefix, [&](int p) {
         const int64_t n = BP.Ps[p].hdr->n_slots;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(1024) k_b_begin(BatchParams BP) {
 // region snapshot where the capacity rule could trigger (grid.y = problem)
 __global__ void k_b_snapshot(BatchParams BP) {
     const DevParams& P = BP.Ps[blockIdx.y];
-    if (!begin_needs_snapshot(P)) return;
+    if (!begin_needs_snapshot(P, P.hdr)) return;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
         P.region_snap[r] = P.region_key[r];
 }
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_b_prune(BatchParams BP) {
 
 __global__ void k_b_end(BatchParams BP) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < BP.B) end_counters(BP.Ps[p]);
+    if (p < BP.B) end_counters(BP.Ps[p], BP.Ps[p].hdr);
 }
 
 __global__ void k_b_poll(BatchParams BP) {

@@ -53,6 +53,15 @@ __device__ __forceinline__ void cluster_barrier() {
 
 __device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(volatile const int32_t*)p; }
 
+// distributed shared memory: a generic pointer to CTA `cta`'s copy of a
+// shared variable (plain loads, stores and atomics reach it)
+template <typename T>
+__device__ __forceinline__ T* dsmem_generic(T* p, uint32_t cta) {
+    uint64_t remote;
+    asm volatile("mapa.u64 %0, %1, %2;" : "=l"(remote) : "l"(reinterpret_cast<uint64_t>(p)), "r"(cta));
+    return reinterpret_cast<T*>(remote);
+}
+
 // distributed shared memory: a word of CTA `cta`'s copy of a shared array
 __device__ __forceinline__ uint32_t dsmem_addr(const uint32_t* p, uint32_t cta) {
     const uint32_t local = (uint32_t)__cvta_generic_to_shared(p);
@@ -89,8 +98,8 @@ __device__ __forceinline__ void fused_begin(const DevParams& P, kpx_device_heade
         if (n_slots > max_slots || H->n_nodes > FUSED_MAX_NODES) {
             H->graph_pending = remaining;  // too large: the phase kernels take over
         } else {
-            ctl = 1 | (begin_needs_snapshot(P) ? 2 : 0);
-            begin_counters(P);
+            ctl = 1 | (begin_needs_snapshot(P, H) ? 2 : 0);
+            begin_counters(P, H);
         }
     }
     H->graph_ctl = ctl;
@@ -105,8 +114,22 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // CTA 0's: winners per chunk
+    // While the launch runs, the header lives in CTA 0's shared memory: the
+    // leader's bookkeeping and every CTA's reads and counter atomics reach it
+    // over distributed shared memory instead of L2 (each cluster barrier's
+    // acquire would otherwise send every header read back to L2).  It is
+    // copied in here and written back before the kernel exits.
+    __shared__ __align__(16) kpx_device_header s_hdr;
+    constexpr int HDR_WORDS = (int)(sizeof(kpx_device_header) / sizeof(uint32_t));
+    static_assert(sizeof(kpx_device_header) % sizeof(uint32_t) == 0, "header size");
+    if (blockIdx.x == 0) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(P.hdr);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&s_hdr);
+        for (int i = threadIdx.x; i < HDR_WORDS; i += FUSED_THREADS) dst[i] = src[i];
+        __syncthreads();
+    }
+    kpx_device_header* H = dsmem_generic(&s_hdr, 0);
     const int lane = threadIdx.x & 31;
-    kpx_device_header* H = P.hdr;
     const bool leader = blockIdx.x == 0 && threadIdx.x == 0;
     const int n_cta = (int)gridDim.x;  // the grid is one cluster
     const int64_t gtid = (int64_t)blockIdx.x * FUSED_THREADS + threadIdx.x;
@@ -210,12 +233,19 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         cluster_barrier();
         ++done;
         if (leader) {
-            end_counters(P);
+            end_counters(P, H);
             H->fused_iterations += 1;
             fused_begin(P, H, n_iter - done, gthreads);
         }
     }
-    if (leader && use_handle) cudaGraphSetConditional(handle, H->graph_pending > 0 ? 1u : 0u);
+    // every CTA has read the header for the last time; CTA 0 writes it back
+    cluster_barrier();
+    if (blockIdx.x == 0) {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(&s_hdr);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(P.hdr);
+        for (int i = threadIdx.x; i < HDR_WORDS; i += FUSED_THREADS) dst[i] = src[i];
+        if (leader && use_handle) cudaGraphSetConditional(handle, s_hdr.graph_pending > 0 ? 1u : 0u);
+    }
 }
 
 template <int DYN, int INTEG>

@@ -162,8 +162,8 @@ __global__ void __launch_bounds__(1024) k_grid_scan(DevParams P) {
 // left it: j >= n_iter - graph_pending.
 __global__ void k_begin(DevParams P, int j, int n_iter) {
     const bool allowed = n_iter == 0 || j >= n_iter - P.hdr->graph_pending;
-    const bool snap = begin_needs_snapshot(P, allowed);  // reads counters begin_counters leaves alone
-    if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P, allowed);
+    const bool snap = begin_needs_snapshot(P, P.hdr, allowed);  // reads counters begin_counters leaves alone
+    if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P, P.hdr, allowed);
     if (!snap) return;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
     flush_prune_counters(H, cA, cI, cT);
 }
 
-__global__ void k_end(DevParams P) { end_counters(P); }
+__global__ void k_end(DevParams P) { end_counters(P, P.hdr); }
 
 // ---------------------------------------------------------------------------
 // solution extraction: parent walk from the best goal node.

@@ -81,6 +81,26 @@ __device__ __forceinline__ uint32_t lookback(uint64_t* tiles, uint32_t tile, uin
     return excl;
 }
 
+// goal_key = min(goal_key, k) by compare-and-swap.  The header may live in
+// another CTA's shared memory (the fused kernel); there a 64-bit atomicMin
+// through a generic address lost updates under contention on GB300, while
+// 64-bit compare-and-swap held.  Each failed swap means another thread
+// lowered the key, so the loop ends; it is bounded all the same.
+__device__ __forceinline__ void goal_key_min(kpx_device_header* H, uint64_t k) {
+    unsigned long long* p = reinterpret_cast<unsigned long long*>(&H->goal_key);
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(p);
+    for (int it = 0; k < old; ++it) {
+        if (it == (1 << 20)) {
+            set_status(H, KPX_E_INTERNAL);
+            H->err_info[0] = 0x20000u;
+            break;
+        }
+        const unsigned long long prev = atomicCAS(p, old, (unsigned long long)k);
+        if (prev == old) break;
+        old = prev;
+    }
+}
+
 __device__ __forceinline__ const int32_t* va_current(const DevParams& P, const kpx_device_header* H) {
     return H->va_sel ? P.va1 : P.va0;
 }
@@ -97,8 +117,7 @@ __device__ __forceinline__ bool problem_runs(const DevParams& P, const kpx_devic
     return H->status == KPX_OK && P.iter_limit >= 0 && (P.iter_limit == 0 || H->iter < P.iter_limit);
 }
 
-__device__ __forceinline__ void begin_counters(const DevParams& P, bool allowed = true) {
-    kpx_device_header* H = P.hdr;
+__device__ __forceinline__ void begin_counters(const DevParams& P, kpx_device_header* H, bool allowed = true) {
     if (!allowed || !problem_runs(P, H)) {
         // a stopped (tree full) or idle planner is a no-op: its header stays
         // as its last iteration left it
@@ -126,8 +145,8 @@ __device__ __forceinline__ void begin_counters(const DevParams& P, bool allowed 
 // The capacity rule can only trigger when the largest possible number of
 // winners (one per region, at most one per slot) overflows the tree.
 // Computed from counters that begin_counters does not write.
-__device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P, bool allowed = true) {
-    const kpx_device_header* H = P.hdr;
+__device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P, const kpx_device_header* H,
+                                                     bool allowed = true) {
     if (!allowed || !problem_runs(P, H)) return false;
     const int64_t n_slots = (int64_t)H->count_A * begin_lambda(P, H->count_A);
     const int64_t max_new = n_slots < P.R ? n_slots : P.R;
@@ -402,7 +421,7 @@ __device__ __forceinline__ void append_row(const DevParams& P, kpx_device_header
         const int old = P.region_owner[r];
         if (old >= 0) P.set[old] = (uint8_t)(P.set[old] | SET_DOM);
         P.region_owner[r] = id;
-        if (in_goal(P, Rw.x[0], Rw.x[1], Rw.x[2])) atomicMin((unsigned long long*)&H->goal_key, (unsigned long long)k);
+        if (in_goal(P, Rw.x[0], Rw.x[1], Rw.x[2])) goal_key_min(H, k);
     } else {
         P.region_key[r] = P.region_snap[r];
     }
@@ -557,8 +576,7 @@ __device__ __forceinline__ void flush_prune_counters(kpx_device_header* H, int& 
 // ---------------------------------------------------------------------------
 // end (one thread per problem): commit the counters of the iteration.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void end_counters(const DevParams& P) {
-    kpx_device_header* H = P.hdr;
+__device__ __forceinline__ void end_counters(const DevParams& P, kpx_device_header* H) {
     if (!H->active) return;
     H->n_nodes += H->n_kept;
     H->count_A = H->count_A_next;
