@@ -453,16 +453,20 @@ __device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_hea
 // over [0, total): nodes appended this iteration are active by Alg. 4.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
-                                           int n_old, int total, int32_t* s_parent, uint8_t* s_set, uint32_t* s_warp,
-                                           uint32_t& s_prefix, int& cA, int& cI, int& cT) {
+                                           int n_old, int total, int32_t* s_parent, uint8_t* s_set,
+                                           uint8_t* s_icount, uint32_t* s_warp, uint32_t& s_prefix, int& cA,
+                                           int& cI, int& cT) {
     const int i_max = P.i_max;
     const int tile0 = (int)tile * PRUNE_TILE;
-    // the tile's parent ids and set bytes: ancestor walks that stay inside
-    // the tile read shared memory (parents precede children)
+    // the tile's parent ids, set bytes and inactivity counts, read in one
+    // pass: ancestor walks that stay inside the tile read shared memory
+    // (parents precede children), and a node's own bytes come from here
     for (int k = threadIdx.x; k < PRUNE_TILE; k += PRUNE_THREADS) {
         const int i = tile0 + k;
-        s_parent[k] = i < n_old ? P.parent[i] : -1;
-        s_set[k] = i < n_old ? P.set[i] : 0;
+        const bool in = i < n_old;
+        s_parent[k] = in ? P.parent[i] : -1;
+        s_set[k] = in ? P.set[i] : 0;
+        s_icount[k] = in ? P.icount[i] : 0;
     }
     __syncthreads();
     const int base = tile0 + threadIdx.x * PRUNE_PER_THREAD;
@@ -476,7 +480,7 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
             ++cA;
             continue;
         }
-        const uint8_t sb = P.set[i];
+        const uint8_t sb = s_set[i - tile0];
         const int st = sb & SET_MASK;
         if (st == SET_T) {  // V_T is permanent
             ++cT;
@@ -486,7 +490,7 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
         // owner: "best" is "not dominated"
         const bool dominated = (sb & SET_DOM) != 0;
         const bool best = !dominated;
-        int ic = P.icount[i];
+        int ic = s_icount[i - tile0];
         const int ic0 = ic;
         int nst = st;
         bool anc = (sb & SET_ANC) != 0;
