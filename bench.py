@@ -370,22 +370,20 @@ def run_kpx(args):
     valid_all = allreduce(valid_per_step * args.steps, "sum", dev)
     value = valid_all / (ms_max / 1e3)
 
-    # launches of one step, counted graph by graph (kpx_graph_info): a graph
-    # of g iterations is 1 fused launch, plus 7 g phase launches when the
-    # fused kernel left iterations to them; 7 per iteration without graphs
+    # launches of one step (kpx_graph_info): one graph launch per kpx_iterate
+    # call, holding 1 fused launch plus 7 phase launches per iteration the
+    # fused kernel left to the loop; 7 per iteration without the fused kernel
     max_g, fused = pl.graph_info()
     plan = kpx.Planner.launch_plan(iters, max_g) if max_g else [1] * iters
     pl.reset()
-    launches_per_step = 1  # k_init (reset)
-    graph_launches = 0
     for g in plan:
         pl.iterate(g)
-        if fused:
-            graph_launches += 1
-            launches_per_step += 1 + (7 * g if pl.header().graph_pending > 0 else 0)
-        else:
-            launches_per_step += 7 * g
     fused_iters = int(pl.header().fused_iterations)
+    graph_launches = len(plan) if max_g else 0
+    if fused:
+        launches_per_step = 1 + len(plan) + 7 * (iters - fused_iters)  # k_init (reset) first
+    else:
+        launches_per_step = 1 + 7 * iters
 
     # per-phase device time over one step (same launches, CUDA events on the planner's stream)
     phase_ms = [0.0] * 7

@@ -239,16 +239,19 @@ kpx_status kpx_set_launch(kpx_planner* p, const kpx_launch_config* lc);
  * non-terminal node becomes dominated.  kpx_reset keeps the new grid. */
 kpx_status kpx_set_regions(kpx_planner* p, int32_t n_axes, const kpx_region_axis* axes);
 
-/* How kpx_iterate launches (the graphs are built on first use): n
- * iterations go out as CUDA graphs of 16, 8, 4, 2 and 1 iterations, largest
- * first (*max_iterations_per_launch = 16; 0 when graphs are unavailable and
- * every iteration is seven plain launches).  *fused = 1 when each graph
- * starts with the fused single-launch kernel, which runs its iterations in
- * one thread-block cluster while an iteration has at most one 32-slot chunk
- * per warp of the cluster and the tree at most 32,768 nodes; the remaining
- * iterations of that graph then run as the phase kernels.  A graph of g
- * iterations launches 1 kernel if the header's graph_pending is 0 after it,
- * else 1 + 7 g. */
+/* How kpx_iterate launches (the graph is built on first use): each call
+ * kpx_iterate(n) is one launch of one CUDA graph per planner
+ * (*max_iterations_per_launch = INT32_MAX; 0 when no graph can be made and
+ * every iteration is seven plain launches).  The graph's first node writes
+ * n into the header's graph_pending.  *fused = 1 when a fused
+ * single-launch kernel follows: it runs iterations in one thread-block
+ * cluster while an iteration has at most one 32-slot chunk per warp of the
+ * cluster and the tree at most 32,768 nodes, and leaves the iterations it
+ * did not run in graph_pending.  A loop (a WHILE conditional node) then runs
+ * the seven phase kernels once per iteration left, counting graph_pending
+ * down to 0.  A launch of n iterations thus starts 1 + 7 m kernels, m = the
+ * iterations the fused kernel left (the header's fused_iterations counts the
+ * ones it ran); without the fused kernel, 7 n. */
 kpx_status kpx_graph_info(kpx_planner* p, int32_t* max_iterations_per_launch, int32_t* fused);
 
 /* Waits for the planner's stream and releases the host handle; the device

@@ -371,14 +371,12 @@ class Planner:
         return int(mx.value), bool(fu.value)
 
     @staticmethod
-    def launch_plan(n_iters: int, max_per_launch: int = 16):
-        """Iterations per graph launch of kpx_iterate(n_iters): largest power
-        of two first (kpx_graph_info)."""
+    def launch_plan(n_iters: int, max_per_launch: int):
+        """Iterations per graph launch of kpx_iterate(n_iters) (kpx_graph_info:
+        one launch per call, up to max_per_launch iterations each)."""
         out, left = [], int(n_iters)
         while left > 0 and max_per_launch > 0:
-            g = max_per_launch
-            while g > left:
-                g //= 2
+            g = min(left, max_per_launch)
             out.append(g)
             left -= g
         return out

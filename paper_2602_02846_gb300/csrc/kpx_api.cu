@@ -17,10 +17,6 @@
 
 using namespace kpx;
 
-// kpx_iterate launches iterations as CUDA graphs of 2^k iterations,
-// k < kGraphLevels, largest first (each graph built on first use).
-constexpr int kGraphLevels = 5;
-
 struct kpx_planner {
     DevParams P;
     Layout L;
@@ -28,11 +24,14 @@ struct kpx_planner {
     char* ws;
     size_t ws_bytes;
     std::string err;
-    // iterations captured as CUDA graphs (built on first use; launched on `stream`)
-    int graph_state = 0;  // 0 not decided, 1 graphs, -1 unavailable (plain launches)
-    bool graph_fused = false;  // graphs start with the fused kernel
+    // kpx_iterate's CUDA graph (built on first use; launched on `stream`)
+    int graph_state = 0;  // 0 not decided, 1 graph, -1 unavailable (plain launches)
+    bool graph_fused = false;  // the graph starts with the fused kernel
     cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graphs[kGraphLevels] = {};  // graphs[k]: 2^k iterations
+    cudaGraph_t loop_graph = nullptr;      // kept: its count node is updated before each launch
+    cudaGraphExec_t loop_exec = nullptr;
+    cudaGraphNode_t count_node = nullptr;  // memset node: the launch's iteration count
+    int32_t count_value = 1;               // the count node's current value
     float grid_scale = 1.0f;     // obstacle-grid cell edge / mean box extent
     std::vector<float> host_obs; // the boxes (lo xyz, hi xyz), to rebuild the grid
 };
@@ -302,12 +301,9 @@ kpx_status read_header(kpx_planner* p, kpx_device_header* h) {
     return KPX_OK;
 }
 
-constexpr int kGraphIterations = 8;
-
-// One iteration of the phase kernels.  j, n_iter: iteration j of a graph
-// launch of n_iter iterations that starts with the fused kernel (0, 0: none).
-cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s, int j = 0, int n_iter = 0) {
-    cudaError_t e = launch_begin(P, s, j, n_iter);
+// One iteration of the phase kernels (plain launches).
+cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s) {
+    cudaError_t e = launch_begin(P, s);
     if (e == cudaSuccess) e = launch_propagate(P, nullptr, s);
     if (e == cudaSuccess) e = launch_mark(P, s);
     if (e == cudaSuccess) e = launch_scan(P, s);
@@ -317,78 +313,123 @@ cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s, int j = 0, int
     return e;
 }
 
-cudaError_t capture_iterations(kpx_planner* p, int count, cudaGraphExec_t* exec) {
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeRelaxed);
-    if (e != cudaSuccess) return e;
-    cudaError_t le = cudaSuccess;
-    for (int i = 0; i < count && le == cudaSuccess; ++i) le = enqueue_iteration(p->P, p->capture_stream);
-    e = cudaStreamEndCapture(p->capture_stream, &g);
-    if (le != cudaSuccess) e = le;
-    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
-    if (g) cudaGraphDestroy(g);
+// Iterations of the phase kernels per trip of the graph's loop: a trip
+// costs a few microseconds on top of its kernels, so it carries several
+// iterations (those past graph_pending are no-ops).
+constexpr int kLoopIterations = 8;
+
+// One iteration of the phase kernels in the body of the graph's loop: it
+// runs only while iterations are owed, and its last kernel counts it off
+// graph_pending (the body's last iteration sets the loop's handle).
+cudaError_t enqueue_loop_iteration(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s) {
+    cudaError_t e = launch_begin(P, s, true);
+    if (e == cudaSuccess) e = launch_propagate(P, nullptr, s);
+    if (e == cudaSuccess) e = launch_mark(P, s);
+    if (e == cudaSuccess) e = launch_scan(P, s);
+    if (e == cudaSuccess) e = launch_append(P, s);
+    if (e == cudaSuccess) e = launch_prune(P, s);
+    if (e == cudaSuccess) e = launch_end_loop(P, h, last, s);
     return e;
 }
 
-// A graph launch of `count` iterations that starts with the fused kernel
-// (kpx_fused.cu): it runs iterations while the problem is small and leaves
-// the rest (header graph_pending) to the phase kernels, captured into the
-// body of a conditional node that runs only when the fused kernel sets its
-// handle.  Iteration j of the body runs only if j >= count - graph_pending.
-cudaError_t capture_fused_iterations(kpx_planner* p, int count, cudaGraphExec_t* exec) {
+// The count node's parameters: n written to the header's graph_pending.
+cudaMemsetParams count_params(const kpx_planner* p, int n) {
+    cudaMemsetParams m = {};
+    m.dst = &p->P.hdr->graph_pending;
+    m.value = (unsigned int)n;
+    m.elementSize = sizeof(int32_t);
+    m.width = 1;
+    m.height = 1;
+    m.pitch = sizeof(int32_t);
+    return m;
+}
+
+// kpx_iterate(n) is one launch of one graph per planner:
+//   count node (memset: graph_pending = n)
+//   -> the fused kernel (kpx_fused.cu), when the device can run its cluster:
+//      iterations while the problem is small; the rest stay in graph_pending
+//   -> WHILE node: up to kLoopIterations iterations of the phase kernels
+//      per trip, until graph_pending is 0 (each iteration's last kernel
+//      counts it off).
+// With the fused kernel the loop's handle starts at 0 and the fused kernel
+// sets it; without it the handle starts at 1 (n >= 1).  Only the count
+// node changes between launches.
+cudaError_t build_loop_graph(kpx_planner* p, bool fused) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaGraphCreate(&g, 0);
     if (e != cudaSuccess) return e;
     cudaGraphConditionalHandle h = 0;
-    cudaGraphNode_t fused_node = nullptr, cond_node = nullptr;
+    cudaGraphNode_t count = nullptr, dep = nullptr, loop = nullptr;
     cudaError_t le = cudaSuccess;
-    e = cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault);
-    if (e == cudaSuccess)
-        e = cudaStreamBeginCaptureToGraph(p->capture_stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    e = cudaGraphConditionalHandleCreate(&h, g, fused ? 0u : 1u, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
-        le = launch_fused(p->P, count, h, 1, p->capture_stream);
-        cudaGraph_t out = nullptr;
-        e = cudaStreamEndCapture(p->capture_stream, &out);
-        if (le != cudaSuccess) e = le;
+        const cudaMemsetParams m = count_params(p, 1);
+        e = cudaGraphAddMemsetNode(&count, g, nullptr, 0, &m);
     }
-    size_t n_nodes = 1;
-    if (e == cudaSuccess) e = cudaGraphGetNodes(g, &fused_node, &n_nodes);  // the fused kernel: the only node
-    if (e == cudaSuccess && n_nodes != 1) e = cudaErrorUnknown;
+    dep = count;
+    if (e == cudaSuccess && fused) {
+        e = cudaStreamBeginCaptureToGraph(p->capture_stream, g, &count, nullptr, 1, cudaStreamCaptureModeRelaxed);
+        if (e == cudaSuccess) {
+            le = launch_fused(p->P, -1, h, 1, p->capture_stream);
+            cudaGraph_t out = nullptr;
+            e = cudaStreamEndCapture(p->capture_stream, &out);
+            if (le != cudaSuccess) e = le;
+        }
+        // the captured fused kernel: the graph's only kernel node
+        cudaGraphNode_t nodes[2] = {};
+        size_t n_nodes = 2;
+        if (e == cudaSuccess) e = cudaGraphGetNodes(g, nodes, &n_nodes);
+        if (e == cudaSuccess && n_nodes != 2) e = cudaErrorUnknown;
+        for (size_t k = 0; e == cudaSuccess && k < n_nodes; ++k) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[k], &t);
+            if (e == cudaSuccess && t == cudaGraphNodeTypeKernel) dep = nodes[k];
+        }
+        if (e == cudaSuccess && dep == count) e = cudaErrorUnknown;
+    }
     cudaGraphNodeParams cp = {};
     if (e == cudaSuccess) {
         cp.type = cudaGraphNodeTypeConditional;
         cp.conditional.handle = h;
-        cp.conditional.type = cudaGraphCondTypeIf;
+        cp.conditional.type = cudaGraphCondTypeWhile;
         cp.conditional.size = 1;
-        e = cudaGraphAddNode(&cond_node, g, &fused_node, nullptr, 1, &cp);
+        e = cudaGraphAddNode(&loop, g, &dep, nullptr, 1, &cp);
     }
     if (e == cudaSuccess) {
         cudaGraph_t body = cp.conditional.phGraph_out[0];
         e = cudaStreamBeginCaptureToGraph(p->capture_stream, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            for (int j = 0; j < count && le == cudaSuccess; ++j)
-                le = enqueue_iteration(p->P, p->capture_stream, j, count);
+            for (int u = 0; u < kLoopIterations && le == cudaSuccess; ++u)
+                le = enqueue_loop_iteration(p->P, h, u == kLoopIterations - 1, p->capture_stream);
             cudaGraph_t out = nullptr;
             e = cudaStreamEndCapture(p->capture_stream, &out);
             if (le != cudaSuccess) e = le;
         }
     }
-    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, g, 0);
-    cudaGraphDestroy(g);
-    return e;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->loop_exec, g, 0);
+    if (e != cudaSuccess) {
+        p->loop_exec = nullptr;
+        cudaGraphDestroy(g);
+        return e;
+    }
+    p->loop_graph = g;
+    p->count_node = count;
+    p->count_value = 1;
+    return cudaSuccess;
 }
 
 void drop_graphs(kpx_planner* p) {
-    for (int k = 0; k < kGraphLevels; ++k) {
-        if (p->graphs[k]) cudaGraphExecDestroy(p->graphs[k]);
-        p->graphs[k] = nullptr;
-    }
+    if (p->loop_exec) cudaGraphExecDestroy(p->loop_exec);
+    if (p->loop_graph) cudaGraphDestroy(p->loop_graph);
+    p->loop_exec = nullptr;
+    p->loop_graph = nullptr;
+    p->count_node = nullptr;
 }
 
-// Decides once how kpx_iterate launches: graphs that start with the fused
+// Decides once how kpx_iterate launches: a graph that starts with the fused
 // kernel when the device can run its cluster (and KPX_FLAG_NO_FUSED is
-// clear), else graphs of the phase kernels alone; plain launches (same
+// clear), else a graph of the phase kernels alone; plain launches (same
 // kernels, same order) when no graph can be made.
 void ensure_graphs(kpx_planner* p) {
     if (p->graph_state != 0) return;
@@ -404,20 +445,17 @@ void ensure_graphs(kpx_planner* p) {
     p->graph_state = 1;
 }
 
-// The graph of 2^k iterations, built on first use (nullptr: none can be
-// made; the planner falls back to plain launches).
-cudaGraphExec_t get_graph(kpx_planner* p, int k) {
-    if (p->graphs[k]) return p->graphs[k];
+// The planner's graph, built on first use (nullptr: none can be made; the
+// planner falls back to plain launches).
+cudaGraphExec_t get_graph(kpx_planner* p) {
+    if (p->loop_exec) return p->loop_exec;
     if (p->graph_fused) {
-        if (capture_fused_iterations(p, 1 << k, &p->graphs[k]) == cudaSuccess) return p->graphs[k];
+        if (build_loop_graph(p, true) == cudaSuccess) return p->loop_exec;
         cudaGetLastError();
-        p->graphs[k] = nullptr;
-        drop_graphs(p);  // the fused form is unavailable: every graph uses the phase kernels
-        p->graph_fused = false;
+        p->graph_fused = false;  // the fused form is unavailable: the phase kernels alone
     }
-    if (capture_iterations(p, 1 << k, &p->graphs[k]) == cudaSuccess) return p->graphs[k];
+    if (build_loop_graph(p, false) == cudaSuccess) return p->loop_exec;
     cudaGetLastError();
-    p->graphs[k] = nullptr;
     p->graph_state = -1;
     return nullptr;
 }
@@ -546,6 +584,10 @@ void drop_member_graphs(kpx_planner* p) {
     p->graph_state = 0;
 }
 
+// batched iterations go out as graphs of kGraphIterations iterations (and
+// single iterations for the remainder)
+constexpr int kGraphIterations = 8;
+
 cudaError_t capture_batch(kpx_batch* b, int count, cudaGraphExec_t* exec) {
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeRelaxed);
@@ -609,16 +651,21 @@ kpx_status kpx_iterate(kpx_planner* p, int32_t n_iters, kpx_iter_stats* out_last
     if (n_iters < 0) return fail(p, KPX_E_INVALID, "n_iters must be >= 0");
     if (n_iters > 0) ensure_graphs(p);
     int32_t it = 0;
-    while (p->graph_state == 1 && it < n_iters) {
-        int k = kGraphLevels - 1;
-        while ((1 << k) > n_iters - it) --k;
-        cudaGraphExec_t g = get_graph(p, k);
-        if (!g) break;  // plain launches for the rest
-        cudaError_t e = cudaGraphLaunch(g, p->stream);
-        if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
-        it += 1 << k;
+    if (p->graph_state == 1 && n_iters > 0) {
+        cudaGraphExec_t g = get_graph(p);
+        if (g) {
+            cudaError_t e = cudaSuccess;
+            if (n_iters != p->count_value) {  // the update costs a few microseconds: only on a change
+                const cudaMemsetParams m = count_params(p, n_iters);
+                e = cudaGraphExecMemsetNodeSetParams(g, p->count_node, &m);
+                if (e == cudaSuccess) p->count_value = n_iters;
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(g, p->stream);
+            if (e != cudaSuccess) return cuda_fail(p, e, "graph launch");
+            it = n_iters;
+        }
     }
-    for (; it < n_iters; ++it) {
+    for (; it < n_iters; ++it) {  // plain launches when no graph can be made
         cudaError_t e = enqueue_iteration(p->P, p->stream);
         if (e != cudaSuccess) return cuda_fail(p, e, "kernel launch");
     }
@@ -754,7 +801,7 @@ kpx_status kpx_set_launch(kpx_planner* p, const kpx_launch_config* lc) {
 kpx_status kpx_graph_info(kpx_planner* p, int32_t* max_iterations_per_launch, int32_t* fused) {
     if (!p || !max_iterations_per_launch || !fused) return KPX_E_INVALID;
     ensure_graphs(p);
-    *max_iterations_per_launch = p->graph_state == 1 ? (1 << (kGraphLevels - 1)) : 0;
+    *max_iterations_per_launch = p->graph_state == 1 ? INT32_MAX : 0;
     *fused = p->graph_state == 1 && p->graph_fused ? 1 : 0;
     return KPX_OK;
 }

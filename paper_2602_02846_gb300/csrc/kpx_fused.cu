@@ -24,8 +24,8 @@
 // most one 32-slot chunk per warp, and a tree of at most FUSED_MAX_NODES
 // nodes.  When it does not fit, the kernel stops and leaves the number of
 // iterations still owed to this graph launch in the header (graph_pending).
-// It then sets the graph's conditional handle, so that the phase kernels run
-// them (see capture_fused_iterations in kpx_api.cu).
+// It then sets the graph's conditional handle, so that the loop of phase
+// kernels that follows it runs them (build_loop_graph in kpx_api.cu).
 #include <cuda_runtime.h>
 
 #include "kpx_phases.cuh"
@@ -146,6 +146,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         __syncthreads();
         G = GridView{sc, sb};
     }
+    if (n_iter < 0) n_iter = s_hdr.graph_pending;  // read by the leader (CTA 0) only
     if (leader) fused_begin(P, H, n_iter, gthreads);
     int done = 0;
     for (;;) {

@@ -220,15 +220,18 @@ cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const
 // launchers (kpx_kernels.cu); each returns the launch status
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s);
 cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s);
-// j, n_iter: iteration j of a graph launch of n_iter iterations that starts
-// with the fused kernel (0, 0: unconditional)
-cudaError_t launch_begin(const DevParams& P, cudaStream_t s, int j = 0, int n_iter = 0);
+// loop: in the loop body of a planner's graph (runs only while graph_pending > 0)
+cudaError_t launch_begin(const DevParams& P, cudaStream_t s, bool loop = false);
 cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s);
 cudaError_t launch_mark(const DevParams& P, cudaStream_t s);
 cudaError_t launch_scan(const DevParams& P, cudaStream_t s);
 cudaError_t launch_append(const DevParams& P, cudaStream_t s);
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s);
 cudaError_t launch_end(const DevParams& P, cudaStream_t s);
+// the end of an iteration in the loop body of a planner's graph: counts the
+// iteration off graph_pending; the body's last sets the loop's handle (1: run
+// again)
+cudaError_t launch_end_loop(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s);
 cudaError_t launch_path(const DevParams& P, cudaStream_t s);
 // a new region decomposition (already in P): node regions, region keys and
 // owners, dominated bits (kpx_set_regions)
@@ -240,7 +243,8 @@ void prepare_launches(const DevParams& P);
 // fused iterations (kpx_fused.cu): CTAs of the single cluster that runs
 // them for this problem's dynamics (0: unavailable on this device)
 int fused_cluster_size(const DevParams& P);
-// up to n_iter iterations in one launch while the problem stays small; the
+// up to n_iter iterations in one launch while the problem stays small
+// (n_iter < 0: the count the header's graph_pending holds at launch); the
 // rest go to the phase kernels through graph_pending and, when use_handle,
 // the graph's conditional handle (1: phase kernels needed)
 cudaError_t launch_fused(const DevParams& P, int n_iter, cudaGraphConditionalHandle handle, int use_handle,

@@ -157,11 +157,11 @@ __global__ void __launch_bounds__(1024) k_grid_scan(DevParams P) {
 // begin: branching factor, slot count, tickets; region snapshot for the
 // capacity rule (only when an overflow is possible this iteration).
 // ---------------------------------------------------------------------------
-// In a graph launch whose first iterations ran in the fused kernel
-// (n_iter > 0), iteration j of the graph runs here only if the fused kernel
-// left it: j >= n_iter - graph_pending.
-__global__ void k_begin(DevParams P, int j, int n_iter) {
-    const bool allowed = n_iter == 0 || j >= n_iter - P.hdr->graph_pending;
+// In the loop body of a planner's graph (loop = 1) an iteration runs only
+// while iterations are owed (graph_pending > 0); otherwise every kernel of
+// the iteration is a no-op.
+__global__ void k_begin(DevParams P, int loop) {
+    const bool allowed = !loop || P.hdr->graph_pending > 0;
     const bool snap = begin_needs_snapshot(P, P.hdr, allowed);  // reads counters begin_counters leaves alone
     if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P, P.hdr, allowed);
     if (!snap) return;
@@ -274,6 +274,21 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
 }
 
 __global__ void k_end(DevParams P) { end_counters(P, P.hdr); }
+
+// The end of an iteration in the loop body of a planner's graph: an
+// iteration that ran (graph_pending > 0, as k_begin saw it) ends and is
+// counted off; once the problem has stopped (tree full, an error, its
+// iteration limit) the iterations still owed would be no-ops and are
+// dropped.  The body's last iteration lets the loop run again while
+// iterations are owed.  graph_pending only falls, so the loop ends.
+__global__ void k_end_loop(DevParams P, cudaGraphConditionalHandle h, int last) {
+    kpx_device_header* H = P.hdr;
+    if (H->graph_pending > 0) {
+        end_counters(P, H);
+        H->graph_pending = problem_runs(P, H) ? H->graph_pending - 1 : 0;
+    }
+    if (last) cudaGraphSetConditional(h, H->graph_pending > 0 ? 1u : 0u);
+}
 
 // ---------------------------------------------------------------------------
 // solution extraction: parent walk from the best goal node.
@@ -429,8 +444,8 @@ cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_begin(const DevParams& P, cudaStream_t s, int j, int n_iter) {
-    k_begin<<<persistent_blocks((P.R + 255) / 256, 2), 256, 0, s>>>(P, j, n_iter);
+cudaError_t launch_begin(const DevParams& P, cudaStream_t s, bool loop) {
+    k_begin<<<persistent_blocks((P.R + 255) / 256, 2), 256, 0, s>>>(P, loop ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -452,6 +467,11 @@ cudaError_t launch_append(const DevParams& P, cudaStream_t s) { KPX_DISPATCH(lau
 
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
     k_prune<<<persistent_blocks(P.n_prune_tiles, 4), PRUNE_THREADS, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_end_loop(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s) {
+    k_end_loop<<<1, 1, 0, s>>>(P, h, last ? 1 : 0);
     return cudaGetLastError();
 }
 
