@@ -57,6 +57,10 @@ CASES = {
     "di_capacity": (lambda: scenes.di_scene(4, grid_pos=16, tree_cap=700), 33, 0),
     "quad_small": (lambda: scenes.quad_scene(1, clutter=100, certify=False, tree_cap=1 << 15, lam=4), 21, 0),
     "dubins_early_reject": (lambda: scenes.dubins_scene(2, n_obstacles=120, tree_cap=1 << 16, lam=32), 19, 1),
+    # outgrows the fused kernel after a few iterations, then fills its tree
+    # inside the loop of phase kernels: the loop drops the iterations left
+    "quad_fills_in_loop": (lambda: scenes.quad_scene(0, clutter=120, certify=False, walls=False, tree_cap=1 << 16,
+                                                     lam=32), 40, 0),
 }
 
 
@@ -75,14 +79,35 @@ def test_fused_equals_phase_kernels(kpx, case):
         plain.iterate(n)
         done += n
         _same(_state(plain), _state(fused), "%s after %d iterations" % (case, done))
-    if case == "di_capacity":
+    if case in ("di_capacity", "quad_fills_in_loop"):
         assert fused.header().status == kpx.KPX_TREE_FULL
+    if case == "quad_fills_in_loop":
+        h = fused.header()
+        assert 0 < h.fused_iterations < h.iter < 40 and h.graph_pending == 0
     tf, tp = fused.best_trajectory(), plain.best_trajectory()
     assert (tf is None) == (tp is None)
     if tf is not None:
         assert np.array_equal(tf["states"], tp["states"]) and tf["cost"] == tp["cost"]
     fused.close()
     plain.close()
+
+
+def test_one_launch_per_call_and_count_updates(kpx):
+    """kpx_iterate(n) is one graph launch that runs exactly n iterations,
+    whatever the previous call's n was (the graph's count node changes only
+    when n does)."""
+    prob = scenes.dubins_scene(0)
+    pl = kpx.Planner(prob)
+    mx, fused = pl.graph_info()
+    assert fused and mx > 1000
+    assert kpx.Planner.launch_plan(200, mx) == [200]
+    done = 0
+    for n in (5, 5, 1, 37, 37, 2, 16):
+        pl.iterate(n)
+        done += n
+        h = pl.header()
+        assert h.iter == done and h.fused_iterations == done and h.graph_pending == 0
+    pl.close()
 
 
 def test_fused_reset_and_restore(kpx):
