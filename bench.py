@@ -63,6 +63,19 @@ PROPAGATE_DRAM_BYTES = {
 }
 FP32_LANES_PER_SM = 128
 
+
+def fma_fields(achieved):
+    """The device's FP32 FMA throughput measured now (kpx_fp32_fma_rate, one
+    launch outside any timed region) and the achieved rate's fraction of it:
+    the measured counterpart of the peak derived from unit counts and the
+    clock."""
+    import torch
+    import paper_2602_02846_gb300 as kpx
+    fma = kpx.fp32_fma_rate(2048, torch.cuda.current_stream())
+    return {"peak_measured_fma": fma, "frac_of_measured_fma": achieved / fma if fma else None,
+            "peak_measured_note": "FP32 FMA microbenchmark (kpx_fp32_fma_rate): 16 independent FMA "
+                                  "chains per thread, 32 warps per SM"}
+
 WORKLOADS = {
     "dubins6_forest300": dict(make=lambda seed: scenes.dubins_scene(seed),
                               desc="6D Dubins airplane, 300-column forest, RK4 h=0.02, 16^3x4 regions, "
@@ -480,6 +493,7 @@ def run_kpx(args):
                                          "kernel is ALU/latency-bound and its working set stays in L2",
                          "peak_basis": "%d SMs x %d FP32 lanes x 2 x %.0f MHz (max SM clock)"
                                        % (sms, FP32_LANES_PER_SM, peak_mhz),
+                         **fma_fields(achieved),
                          "launch_ms": launch_ms,
                          "phase_kernels": {"propagate_launch_ms": prop_launch_ms,
                                            "propagate_achieved_tflops": (ops_step / max(1, iters_done))
@@ -639,7 +653,7 @@ def run_batch(args):
             "autotuned": tuned,
             "roofline": {"bound": "alu", "kernel": "k_b_propagate (whole iteration time: a lower bound)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                         "traffic": None},
+                         "traffic": None, **fma_fields(achieved)},
             "ttfs": {"problems": B, "solved": len(first),
                      "p50_ms": float(np.percentile(first, 50)) if first else None,
                      "p99_ms": float(np.percentile(first, 99)) if first else None,
@@ -868,6 +882,7 @@ def run_refine(args):
                                         REFINE_OPS_BOX_GRADIENT),
                          "peak_basis": "%d SMs x %d FP32 lanes x 2 x 2070 MHz (max SM clock)"
                                        % (sms, FP32_LANES_PER_SM),
+                         **fma_fields(achieved),
                          "forward_only_ms": fwd_ms, "forward_and_backward_ms": both_ms},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
             "gpu_launches": 2 * args.steps,

@@ -446,6 +446,19 @@ kpx_status kpx_refine_keep_best(int32_t count, int32_t max_segments, const float
                                 float* u_best, float* cost_best, void* cuda_stream);
 
 /* ------------------------------------------------------------------------
+ * Measurement.
+ * ---------------------------------------------------------------------- */
+
+/* The device's FP32 fused multiply-add throughput, measured: one launch of
+ * 4 blocks of 256 threads per SM, each thread running 16 independent FMA
+ * chains of `iters` steps (1 <= iters <= 2^20), timed with CUDA events on
+ * cuda_stream after one untimed launch.  *tflops = 2 x FMAs / seconds / 1e12.
+ * Synchronises the stream; allocates no device memory.  The reference for
+ * the planner kernels' FP32 roofline beside the peak derived from unit
+ * counts and the clock. */
+kpx_status kpx_fp32_fma_rate(int32_t iters, double* tflops, void* cuda_stream);
+
+/* ------------------------------------------------------------------------
  * Introspection and step-by-step API (tests, debugging, checkpointing).
  * ---------------------------------------------------------------------- */
 

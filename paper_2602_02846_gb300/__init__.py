@@ -39,7 +39,8 @@ EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_traject
             "kpx_batch_iterate", "kpx_batch_member", "kpx_batch_reset", "kpx_batch_destroy", "kpx_batch_last_error",
             "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info",
             "kpx_refine_workspace_size", "kpx_refine_eval", "kpx_refine_validate", "kpx_refine_adam",
-            "kpx_refine_keep_best", "kpx_set_launch", "kpx_batch_set_launch", "kpx_set_regions")
+            "kpx_refine_keep_best", "kpx_set_launch", "kpx_batch_set_launch", "kpx_set_regions",
+            "kpx_fp32_fma_rate")
 
 
 class kpx_dynamics(C.Structure):
@@ -203,6 +204,8 @@ def load(path: Optional[str] = None):
         L.kpx_batch_poll.restype = C.c_int
         L.kpx_graph_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.kpx_graph_info.restype = C.c_int
+        L.kpx_fp32_fma_rate.argtypes = [C.c_int32, C.POINTER(C.c_double), vp]
+        L.kpx_fp32_fma_rate.restype = C.c_int
         L.kpx_set_regions.argtypes = [vp, C.c_int32, C.POINTER(kpx_region_axis)]
         L.kpx_set_regions.restype = C.c_int
         L.kpx_set_launch.argtypes = [vp, C.POINTER(kpx_launch_config)]
@@ -694,6 +697,18 @@ def kpx_plan_static(prob, n_iters: int, stream=None, capacity: int = 4096, flags
         return int(st), None
     k = ln.value
     return int(st), dict(states=states[:k + 1], controls=controls[:k], steps=steps[:k], cost=float(cost.value))
+
+
+def fp32_fma_rate(iters: int = 2048, stream=None) -> float:
+    """kpx_fp32_fma_rate: the device's measured FP32 FMA throughput in
+    TFLOP/s (one timed launch on `stream`, default the current stream)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    st = load().kpx_fp32_fma_rate(int(iters), C.byref(out), C.c_void_p(s.cuda_stream))
+    if st != KPX_OK:
+        raise KpxError(st, "kpx_fp32_fma_rate")
+    return float(out.value)
 
 
 def last_create_error() -> str:

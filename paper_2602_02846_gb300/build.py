@@ -20,12 +20,13 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libkpx.so")
-SOURCES = ["kpx_kernels.cu", "kpx_fused.cu", "kpx_batch.cu", "kpx_adjoint.cu", "kpx_refine.cu", "kpx_api.cu"]
+SOURCES = ["kpx_kernels.cu", "kpx_fused.cu", "kpx_batch.cu", "kpx_adjoint.cu", "kpx_refine.cu", "kpx_peak.cu",
+           "kpx_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 # the refinement gradient kernels reproduce nothing bit for bit, so they may
 # contract into FMAs; every other unit keeps the planner's arithmetic
-FMAD = {"kpx_adjoint.cu": "-fmad=true"}
+FMAD = {"kpx_adjoint.cu": "-fmad=true", "kpx_peak.cu": "-fmad=true"}
 
 
 def flags_for(src: str) -> list:
