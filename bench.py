@@ -128,6 +128,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-fused", action="store_true",
                     help="run every iteration as the seven phase kernels (KPX_FLAG_NO_FUSED; same results)")
     ap.add_argument("--ttfs-seeds", type=int, default=8, help="problems (scene seeds) for time-to-first-solution")
+    ap.add_argument("--ttfs-variant-seeds", type=int, default=100,
+                    help="problems (scene seeds) per solvable variant for time-to-first-solution (default bench)")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="length of the served request stream")
     ap.add_argument("--serve-memory-gb", type=float, default=32.0, help="device arena of the request loop")
     ap.add_argument("--serve-slots", type=int, default=64, help="request-loop slots per dynamics class")
@@ -462,9 +464,9 @@ def run_kpx(args):
     if args.ttfs_seeds > 0:
         seeds = [args.seed + 1000 * (rank + 1) + k for k in range(args.ttfs_seeds)]
         ttfs = ttfs_block(kpx, spec["make"], seeds, iters, dev, stream)
-        if args.workload == DEFAULT_WORKLOAD:
-            ttfs_variants = {name: dict(ttfs_block(kpx, v["make"], seeds + [s + 500 for s in seeds], 200, dev,
-                                                   stream), desc=v["desc"])
+        if args.workload == DEFAULT_WORKLOAD and args.ttfs_variant_seeds > 0:
+            vseeds = [args.seed + 1000 * (rank + 1) + 500 + k for k in range(args.ttfs_variant_seeds)]
+            ttfs_variants = {name: dict(ttfs_block(kpx, v["make"], vseeds, 200, dev, stream), desc=v["desc"])
                              for name, v in TTFS_VARIANTS.items()}
 
     cpu = None
