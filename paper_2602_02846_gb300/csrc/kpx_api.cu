@@ -528,6 +528,7 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
         P.ws_hi[a] = ws->hi[a];
         P.goal_c[a] = goal->center[a];
     }
+    set_position_box(P);
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = cost->kind;
     P.w_effort = cost->w_effort;
@@ -1301,6 +1302,7 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
         P.ws_hi[a] = ws->hi[a];
         P.goal_c[a] = goal->center[a];
     }
+    set_position_box(P);
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = cost->kind;
     P.w_effort = cost->w_effort;

@@ -115,7 +115,7 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
         fast_sincos(x[3], sph, cph);
         fast_sincos(x[4], sth, cth);
         fast_sincos(x[5], sps, cps);
-        const float inv_cth = 1.0f / cth;
+        const float inv_cth = __frcp_rn(cth);  // correctly rounded, as 1.0f / cth
         const float tth = sth * inv_cth;
         const float p = x[9], q = x[10], r = x[11];
         const float a = u[0] * P.inv_mass;
@@ -133,9 +133,9 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
         dx[6] = a * r13;
         dx[7] = a * r23;
         dx[8] = fmaf(a, r33, -P.param[1]);
-        dx[9] = fmaf(-(P.J[2] - P.J[1]) * q, r, u[1]) * P.inv_J[0];
-        dx[10] = fmaf(-(P.J[0] - P.J[2]) * r, p, u[2]) * P.inv_J[1];
-        dx[11] = fmaf(-(P.J[1] - P.J[0]) * p, q, u[3]) * P.inv_J[2];
+        dx[9] = fmaf(-P.dJ[0] * q, r, u[1]) * P.inv_J[0];
+        dx[10] = fmaf(-P.dJ[1] * r, p, u[2]) * P.inv_J[1];
+        dx[11] = fmaf(-P.dJ[2] * p, q, u[3]) * P.inv_J[2];
     }
 }
 
@@ -186,9 +186,9 @@ template <int N>
 __device__ __forceinline__ bool bounds_ok(const DevParams& P, const float (&x)[N]) {
     bool ok = true;
 #pragma unroll
-    for (int d = 0; d < N; ++d) ok &= (x[d] >= P.x_lo[d]) & (x[d] <= P.x_hi[d]);
+    for (int a = 0; a < 3; ++a) ok &= (x[a] >= P.pos_lo[a]) & (x[a] <= P.pos_hi[a]);  // workspace and bounds
 #pragma unroll
-    for (int a = 0; a < 3; ++a) ok &= (x[a] >= P.ws_lo[a]) & (x[a] <= P.ws_hi[a]);
+    for (int d = 3; d < N; ++d) ok &= (x[d] >= P.x_lo[d]) & (x[d] <= P.x_hi[d]);
     return ok;
 }
 

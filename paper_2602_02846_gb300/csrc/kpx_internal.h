@@ -51,6 +51,8 @@ struct DevParams {
     float w_effort;
     float mg, inv_mg, inv_tau_max, inv_mass;
     float inv_J[3], J[3];
+    float dJ[3];                 // J[2] - J[1], J[0] - J[2], J[1] - J[0] (FP32, as the device would round them)
+    float pos_lo[3], pos_hi[3];  // the workspace box intersected with the state bounds of x, y, z
     int32_t n_axes;
     int32_t ax_dim[8], ax_bins[8], ax_wrap[8];
     float ax_lo[8], ax_scale[8];
@@ -180,6 +182,21 @@ inline void fill_dynamics(DevParams& P, const kpx_dynamics* dyn) {
             P.J[i] = dyn->param[2 + i];
             P.inv_J[i] = 1.0f / dyn->param[2 + i];
         }
+        P.dJ[0] = P.J[2] - P.J[1];
+        P.dJ[1] = P.J[0] - P.J[2];
+        P.dJ[2] = P.J[1] - P.J[0];
+    }
+}
+
+// The position test of X_valid in one box per axis: x >= max(ws_lo, x_lo)
+// holds exactly when x >= ws_lo and x >= x_lo (a NaN bound stays NaN, so
+// every comparison with it still fails).  Call after the workspace and the
+// state bounds are set.
+inline void set_position_box(DevParams& P) {
+    for (int a = 0; a < 3; ++a) {
+        const float wl = P.ws_lo[a], wh = P.ws_hi[a], xl = P.x_lo[a], xh = P.x_hi[a];
+        P.pos_lo[a] = (wl != wl || xl != xl) ? __builtin_nanf("") : (wl > xl ? wl : xl);
+        P.pos_hi[a] = (wh != wh || xh != xh) ? __builtin_nanf("") : (wh < xh ? wh : xh);
     }
 }
 

@@ -173,6 +173,7 @@ extern "C" kpx_status kpx_refine_validate(const kpx_dynamics* dyn, const kpx_wor
         P.ws_hi[a] = ws->hi[a];
         P.goal_c[a] = goal->center[a];
     }
+    set_position_box(P);
     P.goal_r2 = goal->radius * goal->radius;
     P.cost_kind = KPX_COST_EFFORT_DURATION;
     P.w_effort = w_effort;
