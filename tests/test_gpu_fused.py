@@ -4,8 +4,8 @@ KPX_FLAG_NO_FUSED ends bit-identical.  The cases cover problems that stay
 small, problems that outgrow the fused kernel in the middle of a graph launch
 (the phase kernels take over the remaining iterations through the
 conditional node), the capacity rule inside the fused kernel, the early cost
-rejection, and iteration counts that mix the 16-iteration and 1-iteration
-graphs."""
+rejection, and calls of different sizes (each kpx_iterate call is one launch
+of the planner's graph, whose count node changes with the size)."""
 import numpy as np
 import pytest
 
@@ -71,8 +71,8 @@ def test_fused_equals_phase_kernels(kpx, case):
     flags = kpx.KPX_FLAG_EARLY_REJECT if early else 0
     fused = kpx.Planner(prob, flags=flags)
     plain = kpx.Planner(prob, flags=flags | kpx.KPX_FLAG_NO_FUSED)
-    # uneven call sizes: 16-iteration graphs, 1-iteration graphs, and calls
-    # that start in the middle of the problem's growth
+    # uneven call sizes, and calls that start in the middle of the
+    # problem's growth
     done = 0
     for n in (3, 16, iters - 19):
         fused.iterate(n)
