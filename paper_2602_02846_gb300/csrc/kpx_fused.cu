@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint8_t s_icount[PRUNE_TILE];
+    __shared__ uint8_t s_anc[PRUNE_TILE];
     __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // CTA 0's: winners per chunk
     // While the launch runs, the header lives in CTA 0's shared memory: the
     // leader's bookkeeping and every CTA's reads and counter atomics reach it
@@ -229,8 +230,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
             const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
             int cA = 0, cI = 0, cT = 0;
             for (int t = blockIdx.x; t < n_tiles; t += n_cta)
-                prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, s_parent, s_set, s_icount, s_warp, s_prefix, cA,
-                           cI, cT);
+                prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, s_parent, s_set, s_icount, s_anc, s_warp,
+                           s_prefix, cA, cI, cT);
             flush_prune_counters(H, cA, cI, cT);
         }
         cluster_barrier();

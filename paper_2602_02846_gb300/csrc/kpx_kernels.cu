@@ -255,6 +255,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint8_t s_icount[PRUNE_TILE];
+    __shared__ uint8_t s_anc[PRUNE_TILE];
     kpx_device_header* H = P.hdr;
     if (!H->active) return;
     const int n_old = H->n_nodes;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
         const uint32_t tile = s_tile;
         __syncthreads();
         if ((int)tile >= n_tiles) break;
-        prune_tile(P, H, tile, n_tiles, n_old, total, s_parent, s_set, s_icount, s_warp, s_prefix, cA, cI, cT);
+        prune_tile(P, H, tile, n_tiles, n_old, total, s_parent, s_set, s_icount, s_anc, s_warp, s_prefix, cA, cI, cT);
     }
     flush_prune_counters(H, cA, cI, cT);
 }

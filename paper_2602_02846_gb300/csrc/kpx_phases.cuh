@@ -447,6 +447,29 @@ __device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_hea
     append_row<DYN, INTEG>(P, H, w, kept, n_old, Rw, c, r);
 }
 
+// Rules 1-3 of Alg. 3 (literal order, first match wins) for a node that is
+// not terminal: set byte sb, inactivity count ic and set nst in/out.
+// Returns whether a rule decided the node; false leaves it to rule 4.
+// key(i) >= key(region(i)) always, with equality only for the region's
+// owner: "best" is "not dominated".
+__device__ __forceinline__ bool prune_rules_123(uint8_t sb, int i_max, int& ic, int& nst) {
+    const bool dominated = (sb & SET_DOM) != 0;
+    const bool best = !dominated;
+    if (best && nst == SET_I) {  // rule 1: region best while inactive
+        ++ic;
+        if (ic > i_max) {
+            nst = SET_A;
+            return true;
+        }
+    }
+    if (ic > i_max && best) return true;  // rule 2
+    if (dominated) {                      // rule 3: dominated
+        nst = SET_T;
+        return true;
+    }
+    return false;
+}
+
 // ---------------------------------------------------------------------------
 // prune (block-wide): PruneNodes (Alg. 3) over the tile's nodes below n_old,
 // literal rule order, then the tile's part of the compaction of V_A (Alg. 5)
@@ -454,8 +477,8 @@ __device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_hea
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
                                            int n_old, int total, int32_t* s_parent, uint8_t* s_set,
-                                           uint8_t* s_icount, uint32_t* s_warp, uint32_t& s_prefix, int& cA,
-                                           int& cI, int& cT) {
+                                           uint8_t* s_icount, uint8_t* s_anc, uint32_t* s_warp,
+                                           uint32_t& s_prefix, int& cA, int& cI, int& cT) {
     const int i_max = P.i_max;
     const int tile0 = (int)tile * PRUNE_TILE;
     // the tile's parent ids, set bytes and inactivity counts, read in one
@@ -469,47 +492,21 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
         s_icount[k] = in ? P.icount[i] : 0;
     }
     __syncthreads();
-    const int base = tile0 + threadIdx.x * PRUNE_PER_THREAD;
-    uint32_t amask = 0;
+    // rule 4 first, one node per thread at a stride: whether a strict
+    // ancestor is dominated, for the nodes that rules 1-3 leave undecided.
+    // A small tree's nodes thus walk in parallel across the warps instead of
+    // one after another within the warp that owns them below.
 #pragma unroll
     for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
-        const int i = base + q;
-        if (i >= total) break;
-        if (i >= n_old) {  // appended this iteration: in V_A
-            amask |= 1u << q;
-            ++cA;
-            continue;
-        }
-        const uint8_t sb = s_set[i - tile0];
-        const int st = sb & SET_MASK;
-        if (st == SET_T) {  // V_T is permanent
-            ++cT;
-            continue;
-        }
-        // key(i) >= key(region(i)) always, with equality only for the region's
-        // owner: "best" is "not dominated"
-        const bool dominated = (sb & SET_DOM) != 0;
-        const bool best = !dominated;
-        int ic = s_icount[i - tile0];
-        const int ic0 = ic;
-        int nst = st;
-        bool anc = (sb & SET_ANC) != 0;
-        bool done = false;
-        if (best && st == SET_I) {  // rule 1: region best while inactive
-            ++ic;
-            if (ic > i_max) {
-                nst = SET_A;
-                done = true;
-            }
-        }
-        if (!done && ic > i_max && best) done = true;  // rule 2
-        if (!done && dominated) {                       // rule 3: dominated
-            nst = SET_T;
-            done = true;
-        }
-        if (!done) {  // rule 4: any strict ancestor dominated
-            if (!anc) {
-                int p = s_parent[i - tile0];
+        const int k = threadIdx.x + q * PRUNE_THREADS;
+        const int i = tile0 + k;
+        bool anc = false;
+        if (i < n_old) {
+            const uint8_t sb = s_set[k];
+            int ic = s_icount[k], nst = sb & SET_MASK;
+            anc = (sb & SET_ANC) != 0;
+            if (nst != SET_T && !prune_rules_123(sb, i_max, ic, nst) && !anc) {
+                int p = s_parent[k];
                 while (p >= tile0) {  // inside the tile: shared memory (a stale set byte
                     // only lacks a monotone flag, which the walk re-derives)
                     const uint8_t sp = s_set[p - tile0];
@@ -524,8 +521,31 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
                     if (sp & (SET_DOM | SET_ANC)) anc = true;
                 }
             }
-            if (anc) nst = SET_I;
         }
+        s_anc[k] = anc ? 1 : 0;
+    }
+    __syncthreads();
+    const int base = tile0 + threadIdx.x * PRUNE_PER_THREAD;
+    uint32_t amask = 0;
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+        const int i = base + q;
+        if (i >= total) break;
+        if (i >= n_old) {  // appended this iteration: in V_A
+            amask |= 1u << q;
+            ++cA;
+            continue;
+        }
+        const uint8_t sb = s_set[i - tile0];
+        if ((sb & SET_MASK) == SET_T) {  // V_T is permanent
+            ++cT;
+            continue;
+        }
+        int ic = s_icount[i - tile0];
+        const int ic0 = ic;
+        int nst = sb & SET_MASK;
+        const bool anc = s_anc[i - tile0] != 0;
+        if (!prune_rules_123(sb, i_max, ic, nst) && anc) nst = SET_I;  // rule 4
         const uint8_t nb = (uint8_t)(nst | (anc ? SET_ANC : 0) | (sb & SET_DOM));
         if (nb != sb) P.set[i] = nb;
         if (ic != ic0) P.icount[i] = (uint8_t)ic;
