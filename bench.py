@@ -878,7 +878,9 @@ def run_refine(args):
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None,
                          "ops_note": "per RK4 step: forward %.0f + recomputation %.0f + adjoint %.0f, plus %.0f per "
-                                     "box (penalty %.0f + gradient %.0f)"
+                                     "box (penalty %.0f + gradient %.0f), every box charged at every step as the "
+                                     "objective defines it; the kernels reject far boxes after ~15 operations, so "
+                                     "this is the objective's rate, not the arithmetic executed"
                                      % (REFINE_OPS_RK4_STEP, REFINE_OPS_RK4_STEP, REFINE_OPS_RK4_ADJOINT,
                                         REFINE_OPS_BOX_PENALTY + REFINE_OPS_BOX_GRADIENT, REFINE_OPS_BOX_PENALTY,
                                         REFINE_OPS_BOX_GRADIENT),
