@@ -108,6 +108,7 @@ REFINE_OPS_RK4_STEP = 328.0        # 4 derivative evaluations (6 sin/cos + ~40 f
 REFINE_OPS_RK4_ADJOINT = 794.0     # 3 derivative + 4 vector-Jacobian evaluations + stage adjoints
 REFINE_OPS_BOX_PENALTY = 22.0      # signed distance + softplus
 REFINE_OPS_BOX_GRADIENT = 29.0     # signed distance + its gradient + sigmoid
+REFINE_OPS_BOX_TEST = 13.0         # the squared outside distance and its comparison (every candidate box)
 DEFAULT_WORKLOAD = "dubins6_forest300"
 
 
@@ -830,11 +831,22 @@ def run_refine(args):
     c.record(stream)
     torch.cuda.synchronize(dev)
     fwd_ms, both_ms = a.elapsed_time(b), b.elapsed_time(c)
-    ops = n_steps * (2 * REFINE_OPS_RK4_STEP + REFINE_OPS_RK4_ADJOINT
-                     + M * (REFINE_OPS_BOX_PENALTY + REFINE_OPS_BOX_GRADIENT))
+    # the arithmetic executed in one step: the RK4 steps (forward,
+    # recomputation, adjoint) and the box tests the kernels counted (the last
+    # evaluate above: candidates from the box grid, terms within the far
+    # distance)
+    f_cand, f_near, b_cand, b_near = refine.box_tests(batch)
+    ops = (n_steps * (2 * REFINE_OPS_RK4_STEP + REFINE_OPS_RK4_ADJOINT)
+           + (f_cand + b_cand) * REFINE_OPS_BOX_TEST
+           + f_near * (REFINE_OPS_BOX_PENALTY - REFINE_OPS_BOX_TEST + 1.0)
+           + b_near * (REFINE_OPS_BOX_GRADIENT - REFINE_OPS_BOX_TEST + 1.0))
+    # the objective as it defines the work: every box's term at every step
+    ops_objective = n_steps * (2 * REFINE_OPS_RK4_STEP + REFINE_OPS_RK4_ADJOINT
+                               + M * (REFINE_OPS_BOX_PENALTY + REFINE_OPS_BOX_GRADIENT))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count or SM_COUNT_FALLBACK
     peak = sms * FP32_LANES_PER_SM * 2 * 2070.0 * 1e6 / 1e12
     achieved = ops / (ms / args.steps / 1e3) / 1e12
+    objective_rate = ops_objective / (ms / args.steps / 1e3) / 1e12
     # end to end: controls, start states and step counts from pinned host
     # memory, objective and gradient back to the host
     e2e = None
@@ -877,13 +889,19 @@ def run_refine(args):
             "roofline": {"bound": "alu", "kernel": "k_refine_forward<true> + k_refine_backward (one step)",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None,
-                         "ops_note": "per RK4 step: forward %.0f + recomputation %.0f + adjoint %.0f, plus %.0f per "
-                                     "box (penalty %.0f + gradient %.0f), every box charged at every step as the "
-                                     "objective defines it; the kernels reject far boxes after ~15 operations, so "
-                                     "this is the objective's rate, not the arithmetic executed"
+                         "ops_note": "executed arithmetic: per RK4 step forward %.0f + recomputation %.0f + adjoint "
+                                     "%.0f; %.0f per candidate box (the box grid's, counted by the kernels), plus "
+                                     "%.0f (penalty) or %.0f (gradient) per box within the far distance"
                                      % (REFINE_OPS_RK4_STEP, REFINE_OPS_RK4_STEP, REFINE_OPS_RK4_ADJOINT,
-                                        REFINE_OPS_BOX_PENALTY + REFINE_OPS_BOX_GRADIENT, REFINE_OPS_BOX_PENALTY,
-                                        REFINE_OPS_BOX_GRADIENT),
+                                        REFINE_OPS_BOX_TEST, REFINE_OPS_BOX_PENALTY - REFINE_OPS_BOX_TEST + 1.0,
+                                        REFINE_OPS_BOX_GRADIENT - REFINE_OPS_BOX_TEST + 1.0),
+                         "box_tests_per_step": {"objective_candidates": f_cand, "objective_terms": f_near,
+                                                "gradient_candidates": b_cand, "gradient_terms": b_near,
+                                                "every_box": n_steps * M},
+                         "objective_rate_tflops": objective_rate,
+                         "objective_rate_note": "every box's term at every step, %.0f + %.0f operations each, over "
+                                                "the same time: the rate of the objective as defined"
+                                                % (REFINE_OPS_BOX_PENALTY, REFINE_OPS_BOX_GRADIENT),
                          "peak_basis": "%d SMs x %d FP32 lanes x 2 x 2070 MHz (max SM clock)"
                                        % (sms, FP32_LANES_PER_SM),
                          **fma_fields(achieved),

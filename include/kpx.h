@@ -394,8 +394,10 @@ typedef struct {
     float w_effort;   /* effort weight of the edge cost */
 } kpx_refine_cost;
 
-/* Device bytes of the checkpoint workspace kpx_refine_eval needs for a
- * gradient: count trajectories of at most max_total_steps steps. */
+/* Device bytes of the workspace kpx_refine_eval needs for a gradient of
+ * count trajectories of at most max_total_steps steps: the box grid (below)
+ * followed by the checkpoints.  kpx_refine_workspace_size(0, 0) is the box
+ * grid alone, enough for an objective without a gradient. */
 size_t kpx_refine_workspace_size(int32_t count, int32_t max_total_steps);
 
 /* J (cost_out[count]) and, when grad_u != NULL, dJ/du (grad_u[count]
@@ -405,17 +407,31 @@ size_t kpx_refine_workspace_size(int32_t count, int32_t max_total_steps);
  * [max_segments][4] (16-byte aligned, as is grad_u), steps[count]
  * [max_segments], n_segments[count].  The gradient is the adjoint
  * (reverse-mode) rollout with the state checkpointed every 32 steps in
- * workspace (>= kpx_refine_workspace_size(count, max_total_steps) bytes,
- * caller-owned).  A trajectory with more than max_total_steps steps or an
- * invalid segment count gets J = NaN and a zero gradient.  order (device,
- * may be NULL): a permutation of 0..count-1 giving the order in which the
- * trajectories are taken up; the results stay in index order.  Longest
- * first (by total steps) balances the launch. */
+ * workspace (256-byte aligned, caller-owned; >= kpx_refine_workspace_size
+ * (count, max_total_steps) bytes with a gradient; without one it may be NULL,
+ * or >= kpx_refine_workspace_size(0, 0) bytes for the box grid).
+ * The box grid: every call that has it builds, on the device, a uniform
+ * 16^3 grid over the boxes grown by the distance beyond which a box's term
+ * is dropped, each cell listing in index order the boxes that can reach it;
+ * a point then tests only its cell's boxes.  The terms kept are the same as
+ * with every box tested; the summation order differs, so results equal those
+ * of a call without the grid up to FP32 rounding, and calls with the grid
+ * equal one another exactly.  A trajectory with more than max_total_steps
+ * steps or an invalid segment count gets J = NaN and a zero gradient.  order
+ * (device, may be NULL): a permutation of 0..count-1 giving the order in
+ * which the trajectories are taken up; the results stay in index order.
+ * Longest first (by total steps) balances the launch. */
 kpx_status kpx_refine_eval(const kpx_dynamics* dyn, const kpx_refine_cost* cost, const float* obstacles,
                            int32_t n_obstacles, int32_t count, int32_t max_segments, const float* x0,
                            const float* u, const int32_t* steps, const int32_t* n_segments, const int32_t* order,
                            int32_t max_total_steps, float* cost_out, float* grad_u, void* workspace,
                            size_t workspace_bytes, void* cuda_stream);
+
+/* The box tests of the last kpx_refine_eval call that used the box grid in
+ * this workspace: counters[0] candidate boxes tested by the objective,
+ * [1] those within the far distance (terms evaluated), [2] and [3] the same
+ * for the gradient.  Synchronises cuda_stream. */
+kpx_status kpx_refine_counters(const void* workspace, uint64_t counters[4], void* cuda_stream);
 
 /* Re-validation of count trajectories with the planner's own FP32 RK4
  * stepper from x0: valid[i] = 1 when every state after a step satisfies the

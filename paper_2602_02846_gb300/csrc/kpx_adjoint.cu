@@ -239,16 +239,211 @@ __device__ __forceinline__ float sigmoid_t(float t) {
     return t >= 0.0f ? r : e * r;
 }
 
+// the squared distance beyond which beta (margin - d) < SOFTPLUS_CUT
+__device__ __forceinline__ float far_distance2(const RefineParams& R) {
+    const float d = R.margin - SOFTPLUS_CUT * R.inv_beta;
+    return d > 0.0f ? d * d : 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// broad phase of the box sum.  The grid covers the boxes grown by the far
+// distance (a little more, so that rounding never drops a box a point
+// reaches); cell c lists in index order every box whose grown box meets it,
+// so a point's cell holds every box whose term survives the cutoff.  The
+// exact squared-distance test still decides each candidate, and a cell's
+// list keeps index order, so the sum is the same on every call.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float grid_grow(const RefineParams& R) {
+    const float d = R.margin - SOFTPLUS_CUT * R.inv_beta;
+    return d > 0.0f ? d * 1.0001f + 1e-6f : 0.0f;
+}
+
+__device__ __forceinline__ int grid_axis_cell(float v, float lo, float inv) {
+    return (int)fminf(fmaxf((v - lo) * inv, 0.0f), (float)(REFINE_GRID_AXIS - 1));
+}
+
+// whether box b's grown box meets cell (cx, cy, cz)
+__device__ __forceinline__ bool grid_covers(const RefineParams& R, const RefineGridHeader& H, float grow, int b,
+                                            int cx, int cy, int cz) {
+    const int c[3] = {cx, cy, cz};
+    bool in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int c0 = grid_axis_cell(R.obs[6 * b + a] - grow, H.lo[a], H.inv_cs[a]);
+        const int c1 = grid_axis_cell(R.obs[6 * b + 3 + a] + grow, H.lo[a], H.inv_cs[a]);
+        in &= c[a] >= c0 && c[a] <= c1;
+    }
+    return in;
+}
+
+// one block: the grid's extent (zeroes the counters)
+__global__ void k_grid_bounds(RefineParams R) {
+    __shared__ float s_mn[3][32], s_mx[3][32];
+    const float INF = __int_as_float(0x7F800000);
+    float mn[3] = {INF, INF, INF}, mx[3] = {-INF, -INF, -INF};
+    for (int b = threadIdx.x; b < R.n_obs; b += blockDim.x) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = fminf(mn[a], R.obs[6 * b + a]);
+            mx[a] = fmaxf(mx[a], R.obs[6 * b + 3 + a]);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xFFFFFFFFu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xFFFFFFFFu, mx[a], o));
+        }
+        if (lane == 0) {
+            s_mn[a][warp] = mn[a];
+            s_mx[a][warp] = mx[a];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    RefineGridHeader* H = R.grid;
+    const float grow = grid_grow(R);
+    for (int a = 0; a < 3; ++a) {
+        float lo = INF, hi = -INF;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            lo = fminf(lo, s_mn[a][w]);
+            hi = fmaxf(hi, s_mx[a][w]);
+        }
+        if (!(lo <= hi)) lo = hi = 0.0f;  // no boxes
+        lo -= grow;
+        hi += grow;
+        H->lo[a] = lo;
+        H->inv_cs[a] = hi > lo ? (float)REFINE_GRID_AXIS / (hi - lo) : 0.0f;
+    }
+    H->ok = 0;
+    H->total = 0;
+    for (int k = 0; k < 4; ++k) H->tests[k] = 0ull;
+}
+
+// one thread per cell: the number of boxes the cell lists
+__global__ void k_grid_count(RefineParams R) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= REFINE_GRID_CELLS) return;
+    const RefineGridHeader H = *R.grid;
+    const float grow = grid_grow(R);
+    const int cx = c % REFINE_GRID_AXIS, cy = (c / REFINE_GRID_AXIS) % REFINE_GRID_AXIS,
+              cz = c / (REFINE_GRID_AXIS * REFINE_GRID_AXIS);
+    int n = 0;
+    for (int b = 0; b < R.n_obs; ++b) n += grid_covers(R, H, grow, b, cx, cy, cz) ? 1 : 0;
+    R.grid_off[c] = n;
+}
+
+// one block of 1024 threads: counts -> offsets; the grid is used only when
+// every entry fits
+__global__ void __launch_bounds__(1024) k_grid_scan(RefineParams R) {
+    constexpr int PER = REFINE_GRID_CELLS / 1024;
+    __shared__ int s_warp[32];
+    int v[PER], sum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        v[q] = R.grid_off[threadIdx.x * PER + q];
+        sum += v[q];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int run = x - sum + (warp > 0 ? s_warp[warp - 1] : 0);
+    __syncthreads();  // every count is read before any offset is written
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        R.grid_off[threadIdx.x * PER + q] = run;
+        run += v[q];
+    }
+    if (threadIdx.x == 1023) {
+        R.grid_off[REFINE_GRID_CELLS] = run;
+        R.grid->total = run;
+        R.grid->ok = run <= REFINE_GRID_ENTRIES ? 1 : 0;
+    }
+}
+
+// one thread per cell: the cell's boxes in index order
+__global__ void k_grid_fill(RefineParams R) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= REFINE_GRID_CELLS) return;
+    const RefineGridHeader H = *R.grid;
+    if (!H.ok) return;
+    const float grow = grid_grow(R);
+    const int cx = c % REFINE_GRID_AXIS, cy = (c / REFINE_GRID_AXIS) % REFINE_GRID_AXIS,
+              cz = c / (REFINE_GRID_AXIS * REFINE_GRID_AXIS);
+    int pos = R.grid_off[c];
+    for (int b = 0; b < R.n_obs; ++b)
+        if (grid_covers(R, H, grow, b, cx, cy, cz)) R.grid_ids[pos++] = (uint16_t)b;
+}
+
+// where a point's candidate boxes come from: its grid cell, or every box
+// (the grid's extent is read from the header, L1-resident, at each use)
+struct BoxSource {
+    const RefineGridHeader* H;
+    const int32_t* off;
+    const uint16_t* ids;
+    bool grid;
+};
+
+__device__ __forceinline__ BoxSource box_source(const RefineParams& R) {
+    BoxSource S;
+    S.grid = R.grid && R.grid->ok;
+    S.H = R.grid;
+    S.off = R.grid_off;
+    S.ids = R.grid_ids;
+    return S;
+}
+
+__device__ __forceinline__ void candidates(const BoxSource& S, int n_obs, float px, float py, float pz, int& e0,
+                                           int& e1) {
+    if (!S.grid) {
+        e0 = 0;
+        e1 = n_obs;
+        return;
+    }
+    const RefineGridHeader* H = S.H;
+    const int c = (grid_axis_cell(pz, H->lo[2], H->inv_cs[2]) * REFINE_GRID_AXIS +
+                   grid_axis_cell(py, H->lo[1], H->inv_cs[1])) *
+                      REFINE_GRID_AXIS +
+                  grid_axis_cell(px, H->lo[0], H->inv_cs[0]);
+    e0 = S.off[c];
+    e1 = S.off[c + 1];
+}
+
+__device__ __forceinline__ int box_of(const BoxSource& S, int e) { return S.grid ? (int)S.ids[e] : e; }
+
 // this lane's share of beta * sum_b sp(margin - d_b(p)); far2 = the squared
 // distance beyond which a box's term is dropped
-__device__ __forceinline__ float penalty_lane(const RefineParams& R, const ObsSmem& O, float px, float py, float pz,
-                                              float far2, int lane) {
+__device__ __forceinline__ float penalty_lane(const RefineParams& R, const ObsSmem& O, const BoxSource& S, float px,
+                                              float py, float pz, float far2, int lane, uint32_t& n_test,
+                                              uint32_t& n_near) {
     float acc = 0.0f;
+    int e0, e1;
+    candidates(S, R.n_obs, px, py, pz, e0, e1);
 #pragma unroll 4
-    for (int b = lane; b < R.n_obs; b += 32) {
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int b = box_of(S, e);
         float dx, dy, dz;
         const float o2 = box_offset(px, py, pz, O, b, dx, dy, dz);
+        ++n_test;
         if (o2 >= far2) continue;
+        ++n_near;
         float gx, gy, gz;
         const float d = o2 > 0.0f ? sqrtf(o2) : inside_distance(px, py, pz, O, b, gx, gy, gz);
         acc += softplus_t(R.beta * (R.margin - d));
@@ -257,14 +452,20 @@ __device__ __forceinline__ float penalty_lane(const RefineParams& R, const ObsSm
 }
 
 // this lane's share of d/dp sum_b sp(margin - d_b(p)) = -sum_b sigma(t) grad d_b
-__device__ __forceinline__ void penalty_grad_lane(const RefineParams& R, const ObsSmem& O, float px, float py,
-                                                  float pz, float far2, int lane, float& ox, float& oy, float& oz) {
+__device__ __forceinline__ void penalty_grad_lane(const RefineParams& R, const ObsSmem& O, const BoxSource& S,
+                                                  float px, float py, float pz, float far2, int lane, float& ox,
+                                                  float& oy, float& oz, uint32_t& n_test, uint32_t& n_near) {
     ox = oy = oz = 0.0f;
+    int e0, e1;
+    candidates(S, R.n_obs, px, py, pz, e0, e1);
 #pragma unroll 4
-    for (int b = lane; b < R.n_obs; b += 32) {
+    for (int e = e0 + lane; e < e1; e += 32) {
+        const int b = box_of(S, e);
         float dx, dy, dz;
         const float o2 = box_offset(px, py, pz, O, b, dx, dy, dz);
+        ++n_test;
         if (o2 >= far2) continue;
+        ++n_near;
         float gx, gy, gz, d;
         if (o2 > 0.0f) {
             d = sqrtf(o2);
@@ -288,6 +489,20 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
+// the warp's box tests into the grid header's counters k, k + 1
+__device__ __forceinline__ void count_tests(const RefineParams& R, int k, uint32_t n_test, uint32_t n_near) {
+    unsigned long long t = n_test, n = n_near;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+        n += __shfl_xor_sync(0xFFFFFFFFu, n, o);
+    }
+    if ((threadIdx.x & 31) == 0 && R.grid) {
+        atomicAdd(&R.grid->tests[k], t);
+        atomicAdd(&R.grid->tests[k + 1], n);
+    }
+}
+
 // stages the boxes (SoA) into shared memory; returns the views
 __device__ __forceinline__ ObsSmem stage_obstacles(const RefineParams& R, float* smem) {
     ObsSmem O;
@@ -302,12 +517,6 @@ __device__ __forceinline__ ObsSmem stage_obstacles(const RefineParams& R, float*
     }
     __syncthreads();
     return O;
-}
-
-// the squared distance beyond which beta (margin - d) < SOFTPLUS_CUT
-__device__ __forceinline__ float far_distance2(const RefineParams& R) {
-    const float d = R.margin - SOFTPLUS_CUT * R.inv_beta;
-    return d > 0.0f ? d * d : 0.0f;
 }
 
 __device__ __forceinline__ float effort_cost(const RefineParams& R, const float (&u)[4], int K, float (&g)[4]) {
@@ -349,6 +558,8 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_forward(RefineParams 
         return;
     }
     const float far2 = far_distance2(R);
+    const BoxSource BS = box_source(R);
+    uint32_t n_test = 0, n_near = 0;
     float x[12];
 #pragma unroll
     for (int i = 0; i < 12; ++i) x[i] = R.x0[tr * 12 + i];
@@ -369,9 +580,10 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_forward(RefineParams 
                 if (lane == 13) c[13] = __int_as_float(j);
             }
             rk4_step(R, x, u);
-            pen += penalty_lane(R, O, x[0], x[1], x[2], far2, lane);
+            pen += penalty_lane(R, O, BS, x[0], x[1], x[2], far2, lane, n_test, n_near);
         }
     }
+    count_tests(R, 0, n_test, n_near);
     pen = warp_sum(pen);
     if (lane == 0) {
         float goal = 0.0f;
@@ -405,6 +617,8 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
         return;
     }
     const float far2 = far_distance2(R);
+    const BoxSource BS = box_source(R);
+    uint32_t n_test = 0, n_near = 0;
     // the effort part of every segment's gradient (padding rows: 0)
     for (int s = lane; s < R.max_segments; s += 32) {
         float u[4], g[4] = {0.0f, 0.0f, 0.0f, 0.0f};
@@ -456,8 +670,8 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
         for (int t = len - 1; t >= 0; --t) {
             // the penalty at p_{k+1}: d/dp w_obs sp(margin - d) = -w_obs sigma grad d
             float ox, oy, oz;
-            penalty_grad_lane(R, O, xs[(t + 1) * 12 + 0], xs[(t + 1) * 12 + 1], xs[(t + 1) * 12 + 2], far2, lane, ox,
-                              oy, oz);
+            penalty_grad_lane(R, O, BS, xs[(t + 1) * 12 + 0], xs[(t + 1) * 12 + 1], xs[(t + 1) * 12 + 2], far2, lane,
+                              ox, oy, oz, n_test, n_near);
             lam[0] += R.w_obs * warp_sum(ox);
             lam[1] += R.w_obs * warp_sum(oy);
             lam[2] += R.w_obs * warp_sum(oz);
@@ -484,6 +698,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
         const float4 v = *q;
         *q = make_float4(v.x + gu[0], v.y + gu[1], v.z + gu[2], v.w + gu[3]);
     }
+    count_tests(R, 2, n_test, n_near);
 }
 
 // ---------------------------------------------------------------------------
@@ -537,7 +752,15 @@ cudaError_t launch_refine_eval(const RefineParams& R, cudaStream_t s) {
     if (R.count == 0) return cudaSuccess;
     const int blocks = (R.count + ADJ_WARPS - 1) / ADJ_WARPS;
     const size_t smem_obs = (size_t)6 * R.n_obs * sizeof(float);
-    cudaError_t e;
+    cudaError_t e = cudaSuccess;
+    if (R.grid) {  // the box grid of this call's boxes and cost
+        k_grid_bounds<<<1, 1024, 0, s>>>(R);
+        k_grid_count<<<REFINE_GRID_CELLS / 256, 256, 0, s>>>(R);
+        k_grid_scan<<<1, 1024, 0, s>>>(R);
+        k_grid_fill<<<REFINE_GRID_CELLS / 256, 256, 0, s>>>(R);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     if (!R.grad) {
         e = set_smem((const void*)k_refine_forward<false>, smem_obs);
         if (e == cudaSuccess) {

@@ -288,7 +288,27 @@ struct RefineParams {
     float* cost;            // [count]
     float* grad;            // [count][max_segments][4] (null: objective only)
     float* ckpt;            // [count][n_ckpt][REFINE_CKPT_WORDS]
+    // broad phase of the box sum (null: every box at every step)
+    struct RefineGridHeader* grid;
+    int32_t* grid_off;      // [REFINE_GRID_CELLS + 1]
+    uint16_t* grid_ids;     // [REFINE_GRID_ENTRIES]
 };
+
+// The box grid of the refinement objective: a uniform grid of
+// REFINE_GRID_AXIS^3 cells over the boxes grown by the distance beyond which
+// a box's term is dropped; cell c lists, in index order, every box whose
+// grown box meets it.  Built on the device at each kpx_refine_eval call; the
+// counters count the box tests of the call's kernels.
+constexpr int REFINE_GRID_AXIS = 16;
+constexpr int REFINE_GRID_CELLS = REFINE_GRID_AXIS * REFINE_GRID_AXIS * REFINE_GRID_AXIS;
+constexpr int REFINE_GRID_ENTRIES = 1 << 22;
+struct RefineGridHeader {
+    float lo[3], inv_cs[3];
+    int32_t ok, total;
+    unsigned long long tests[4];  // forward candidates, forward near, backward candidates, backward near
+};
+static_assert(sizeof(RefineGridHeader) <= 256, "the grid header's slot");
+constexpr size_t REFINE_GRID_BYTES = 256 + (size_t)(REFINE_GRID_CELLS + 1) * 4 + (size_t)REFINE_GRID_ENTRIES * 2;
 
 struct AdamParams {
     int32_t count, max_segments;

@@ -95,6 +95,9 @@ bool quad_rk4(const kpx_dynamics* dyn) { return dyn && dyn->kind == KPX_QUAD12 &
 
 bool aligned16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
+// workspace: the box grid first, then the checkpoints
+size_t grid_region() { return align256(REFINE_GRID_BYTES); }
+
 }  // namespace
 }  // namespace kpx
 
@@ -102,7 +105,8 @@ using namespace kpx;
 
 extern "C" size_t kpx_refine_workspace_size(int32_t count, int32_t max_total_steps) {
     if (count < 0 || max_total_steps < 0) return 0;
-    return align256((size_t)count * n_checkpoints(max_total_steps) * REFINE_CKPT_WORDS * sizeof(float));
+    return grid_region() +
+           align256((size_t)count * n_checkpoints(max_total_steps) * REFINE_CKPT_WORDS * sizeof(float));
 }
 
 extern "C" kpx_status kpx_refine_eval(const kpx_dynamics* dyn, const kpx_refine_cost* cost, const float* obstacles,
@@ -119,6 +123,7 @@ extern "C" kpx_status kpx_refine_eval(const kpx_dynamics* dyn, const kpx_refine_
     if (count == 0) return KPX_OK;
     if (grad_u && (!workspace || workspace_bytes < kpx_refine_workspace_size(count, max_total_steps)))
         return KPX_E_NOMEM;
+    if (workspace && reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return KPX_E_INVALID;
     RefineParams R;
     memset(&R, 0, sizeof(R));
     R.h = dyn->h;
@@ -150,7 +155,14 @@ extern "C" kpx_status kpx_refine_eval(const kpx_dynamics* dyn, const kpx_refine_
     R.order = order;
     R.cost = cost_out;
     R.grad = grad_u;
-    R.ckpt = reinterpret_cast<float*>(workspace);
+    // the box grid when the workspace holds it (with a gradient it always does)
+    if (workspace && workspace_bytes >= grid_region()) {
+        char* w = reinterpret_cast<char*>(workspace);
+        R.grid = reinterpret_cast<RefineGridHeader*>(w);
+        R.grid_off = reinterpret_cast<int32_t*>(w + 256);
+        R.grid_ids = reinterpret_cast<uint16_t*>(w + 256 + (size_t)(REFINE_GRID_CELLS + 1) * 4);
+    }
+    R.ckpt = workspace ? reinterpret_cast<float*>(reinterpret_cast<char*>(workspace) + grid_region()) : nullptr;
     return launch_refine_eval(R, reinterpret_cast<cudaStream_t>(cuda_stream)) == cudaSuccess ? KPX_OK : KPX_E_CUDA;
 }
 
@@ -234,4 +246,16 @@ extern "C" kpx_status kpx_refine_keep_best(int32_t count, int32_t max_segments, 
                                    reinterpret_cast<cudaStream_t>(cuda_stream)) == cudaSuccess
                ? KPX_OK
                : KPX_E_CUDA;
+}
+
+extern "C" kpx_status kpx_refine_counters(const void* workspace, uint64_t counters[4], void* cuda_stream) {
+    if (!workspace || !counters) return KPX_E_INVALID;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    const RefineGridHeader* H = reinterpret_cast<const RefineGridHeader*>(workspace);
+    unsigned long long t[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(t, H->tests, sizeof(t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return KPX_E_CUDA;
+    for (int k = 0; k < 4; ++k) counters[k] = t[k];
+    return KPX_OK;
 }

@@ -128,14 +128,14 @@ def evaluate(batch: Batch, spec, u=None, grad: bool = False, stream=None):
     u = batch.u if u is None else u
     J = torch.empty(batch.count, dtype=torch.float32, device=u.device)
     g = torch.empty_like(u) if grad else None
-    ws = None
-    size = 0
-    if grad:
-        size = int(L.kpx_refine_workspace_size(batch.count, batch.max_total_steps))
-        ws = torch.empty(size + 256, dtype=torch.uint8, device=u.device)
+    # the workspace: the box grid, plus the checkpoints for a gradient; the
+    # same grid either way, so J is the same with and without a gradient
+    size = int(L.kpx_refine_workspace_size(batch.count, batch.max_total_steps) if grad
+               else L.kpx_refine_workspace_size(0, 0))
+    ws = torch.empty(size + 256, dtype=torch.uint8, device=u.device)
     s = stream if stream is not None else torch.cuda.current_stream(u.device)
     cost = _cost_struct(spec)
-    wptr = None if ws is None else ws.data_ptr() + ((-ws.data_ptr()) % 256)
+    wptr = ws.data_ptr() + ((-ws.data_ptr()) % 256)
     _check(L.kpx_refine_eval(C.byref(batch.dyn), C.byref(cost), C.c_void_p(batch.obs.data_ptr()),
                              int(batch.obs.shape[0]), batch.count, batch.max_segments,
                              C.c_void_p(batch.x0.data_ptr()), C.c_void_p(u.data_ptr()),
@@ -143,7 +143,22 @@ def evaluate(batch: Batch, spec, u=None, grad: bool = False, stream=None):
                              C.c_void_p(batch.order.data_ptr()), batch.max_total_steps, C.c_void_p(J.data_ptr()),
                              C.c_void_p(g.data_ptr()) if grad else None, C.c_void_p(wptr), C.c_size_t(size),
                              C.c_void_p(s.cuda_stream)), "kpx_refine_eval")
+    batch.last_workspace = (ws, wptr)  # kept for box_tests()
     return (J, g) if grad else J
+
+
+def box_tests(batch: Batch, stream=None):
+    """The box tests of the batch's last evaluate (kpx_refine_counters):
+    (objective candidates, objective terms, gradient candidates, gradient
+    terms).  Synchronises the stream."""
+    import torch
+    if getattr(batch, "last_workspace", None) is None:
+        raise RuntimeError("box_tests: no evaluate() on this batch yet")
+    ws, wptr = batch.last_workspace
+    s = stream if stream is not None else torch.cuda.current_stream(ws.device)
+    out = (C.c_uint64 * 4)()
+    _check(_lib().kpx_refine_counters(C.c_void_p(wptr), out, C.c_void_p(s.cuda_stream)), "kpx_refine_counters")
+    return tuple(int(v) for v in out)
 
 
 def validate(batch: Batch, u=None, stream=None):

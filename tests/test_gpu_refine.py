@@ -192,3 +192,36 @@ def test_refine_planner_trajectories_revalidated_fp64(kpx, rf):
         print("refinement: J %.5f -> %.5f, effort+duration cost %.5f -> %.5f, accepted %s"
               % (J0, J, res["cost0"][0].item(), res["cost"][0].item(), bool(res["accepted"][0])))
     assert accepted >= 1
+
+
+def test_box_grid_equals_every_box(rf):
+    """The box grid keeps exactly the terms of the every-box sum: the
+    objective with the grid (evaluate) against the same call without a
+    workspace (every box at every step), up to FP32 summation order; its
+    candidates are a small part of the boxes, and every term found by
+    brute force is among them."""
+    import ctypes as C
+    prob, x0, u, steps, n_seg, obs = _case(8, (6, 30), (10, 50), 300, seed=7)
+    batch = rf.Batch(prob, x0, u, steps, n_seg, obstacles=obs)
+    J_grid = rf.evaluate(batch, SPEC).cpu().numpy()
+    f_cand, f_near, _, _ = rf.box_tests(batch)
+    L = rf._lib()
+    J_all = torch.empty(batch.count, dtype=torch.float32, device="cuda")
+    cost = rf._cost_struct(SPEC)
+    s = torch.cuda.current_stream()
+    rf._check(L.kpx_refine_eval(C.byref(batch.dyn), C.byref(cost), C.c_void_p(batch.obs.data_ptr()),
+                                int(batch.obs.shape[0]), batch.count, batch.max_segments,
+                                C.c_void_p(batch.x0.data_ptr()), C.c_void_p(batch.u.data_ptr()),
+                                C.c_void_p(batch.steps.data_ptr()), C.c_void_p(batch.n_seg.data_ptr()),
+                                C.c_void_p(batch.order.data_ptr()), batch.max_total_steps,
+                                C.c_void_p(J_all.data_ptr()), None, None, C.c_size_t(0), C.c_void_p(s.cuda_stream)),
+              "kpx_refine_eval")
+    J_all = J_all.cpu().numpy()
+    assert np.all(np.abs(J_grid - J_all) <= 1e-5 * np.abs(J_all)), (J_grid, J_all)
+    every = int(np.asarray(steps).sum()) * len(obs)
+    print("box grid: %d candidates, %d terms, of %d box tests without it" % (f_cand, f_near, every))
+    assert 0 < f_near <= f_cand < every // 4
+    # a gradient call counts its forward and backward box tests; the same grid and points
+    _, g = rf.evaluate(batch, SPEC, grad=True)
+    c = rf.box_tests(batch)
+    assert c[0] == f_cand and c[1] == f_near and c[2] == f_cand and c[3] == f_near
