@@ -563,6 +563,15 @@ typedef struct {
  * nullable; with records every slot is checked in full and recorded). */
 kpx_status kpx_debug_step(kpx_planner* p, int32_t phase, const kpx_debug_records* records);
 
+/* Runs one look-back wait (the bounded spin of the decoupled scans) that
+ * nothing will release: a scan tile waits on a predecessor word at an epoch
+ * no tile carries.  The wait gives up after its poll limit (2^20 polls, well
+ * under a second), records KPX_E_TIMEOUT in the planner's status with
+ * err_info[0] = 0x10000 | 1, and returns; the planner then stays stopped and
+ * the CUDA context usable.  Synchronises the stream.  For tests of the
+ * failure path: KPX_E_INVALID if the planner has fewer than two tiles. */
+kpx_status kpx_debug_wait_timeout(kpx_planner* p);
+
 /* Copies the whole workspace (every array and counter) to / from dst/src,
  * host or device memory of layout.workspace_bytes bytes.  Waits for the
  * planner's stream.  A restored planner continues bit-identically. */

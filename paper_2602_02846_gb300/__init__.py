@@ -40,7 +40,7 @@ EXPORTED = ("kpx_workspace_size", "kpx_create", "kpx_iterate", "kpx_best_traject
             "kpx_batch_assign", "kpx_batch_release", "kpx_batch_poll", "kpx_graph_info",
             "kpx_refine_workspace_size", "kpx_refine_eval", "kpx_refine_validate", "kpx_refine_adam",
             "kpx_refine_keep_best", "kpx_set_launch", "kpx_batch_set_launch", "kpx_set_regions",
-            "kpx_fp32_fma_rate", "kpx_refine_counters")
+            "kpx_fp32_fma_rate", "kpx_refine_counters", "kpx_debug_wait_timeout")
 
 
 class kpx_dynamics(C.Structure):
@@ -204,6 +204,8 @@ def load(path: Optional[str] = None):
         L.kpx_batch_poll.restype = C.c_int
         L.kpx_graph_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
         L.kpx_graph_info.restype = C.c_int
+        L.kpx_debug_wait_timeout.argtypes = [vp]
+        L.kpx_debug_wait_timeout.restype = C.c_int
         L.kpx_refine_counters.argtypes = [vp, C.POINTER(C.c_uint64), vp]
         L.kpx_refine_counters.restype = C.c_int
         L.kpx_fp32_fma_rate.argtypes = [C.c_int32, C.POINTER(C.c_double), vp]

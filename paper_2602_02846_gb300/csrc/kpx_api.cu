@@ -871,6 +871,15 @@ kpx_status kpx_get_layout(const kpx_planner* p, kpx_layout* out) {
     return KPX_OK;
 }
 
+kpx_status kpx_debug_wait_timeout(kpx_planner* p) {
+    if (!p) return KPX_E_INVALID;
+    cudaError_t e = launch_wait_timeout(p->P, p->stream);
+    if (e == cudaErrorInvalidValue) return fail(p, KPX_E_INVALID, "the planner has fewer than two scan tiles");
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "bounded wait test");
+    return KPX_OK;
+}
+
 kpx_status kpx_debug_step(kpx_planner* p, int32_t phase, const kpx_debug_records* records) {
     if (!p) return KPX_E_INVALID;
     if (records && records->valid && records->capacity < p->P.slot_cap)

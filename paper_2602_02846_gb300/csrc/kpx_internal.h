@@ -250,6 +250,8 @@ cudaError_t launch_end(const DevParams& P, cudaStream_t s);
 // again)
 cudaError_t launch_end_loop(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s);
 cudaError_t launch_path(const DevParams& P, cudaStream_t s);
+// one bounded look-back wait that nothing releases (tests): records KPX_E_TIMEOUT
+cudaError_t launch_wait_timeout(const DevParams& P, cudaStream_t s);
 // a new region decomposition (already in P): node regions, region keys and
 // owners, dominated bits (kpx_set_regions)
 cudaError_t launch_remap_regions(const DevParams& P, cudaStream_t s);

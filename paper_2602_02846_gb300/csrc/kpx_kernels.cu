@@ -471,6 +471,24 @@ cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// A look-back wait that nothing will release: tile 1 of `tiles` waits on
+// tile 0 at an epoch no tile word carries.  The wait gives up after its poll
+// limit and records KPX_E_TIMEOUT (err_info[0] = 0x10000 | 1): a test that the
+// bounded waits end and report without faulting.
+__global__ void k_wait_timeout(DevParams P, uint64_t* tiles) {
+    kpx_device_header* H = P.hdr;
+    uint32_t epoch = ((uint32_t)H->epoch + (1u << 29)) & 0x3FFFFFFFu;
+    if (epoch == 0) epoch = 1;
+    lookback(tiles, 1u, 0u, epoch, H);
+}
+
+cudaError_t launch_wait_timeout(const DevParams& P, cudaStream_t s) {
+    uint64_t* tiles = P.n_win_tiles >= 2 ? P.win_tiles : (P.n_prune_tiles >= 2 ? P.prune_tiles : nullptr);
+    if (!tiles) return cudaErrorInvalidValue;
+    k_wait_timeout<<<1, 1, 0, s>>>(P, tiles);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_end_loop(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s) {
     k_end_loop<<<1, 1, 0, s>>>(P, h, last ? 1 : 0);
     return cudaGetLastError();
