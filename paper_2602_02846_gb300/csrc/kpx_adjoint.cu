@@ -670,11 +670,16 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
         for (int t = len - 1; t >= 0; --t) {
             // the penalty at p_{k+1}: d/dp w_obs sp(margin - d) = -w_obs sigma grad d
             float ox, oy, oz;
+            const uint32_t near0 = n_near;
             penalty_grad_lane(R, O, BS, xs[(t + 1) * 12 + 0], xs[(t + 1) * 12 + 1], xs[(t + 1) * 12 + 2], far2, lane,
                               ox, oy, oz, n_test, n_near);
-            lam[0] += R.w_obs * warp_sum(ox);
-            lam[1] += R.w_obs * warp_sum(oy);
-            lam[2] += R.w_obs * warp_sum(oz);
+            // most steps have no box within the far distance: then every
+            // lane's share is 0 and the three reductions are skipped
+            if (__any_sync(0xFFFFFFFFu, n_near != near0)) {
+                lam[0] += R.w_obs * warp_sum(ox);
+                lam[1] += R.w_obs * warp_sum(oy);
+                lam[2] += R.w_obs * warp_sum(oz);
+            }
             const int sk = seg_of[t];
             if (sk != cur_seg) {  // entering an earlier segment: commit the later one
                 if (cur_seg >= 0 && lane == 0) {
