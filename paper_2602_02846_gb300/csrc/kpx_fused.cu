@@ -150,8 +150,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     if (n_iter < 0) n_iter = s_hdr.graph_pending;  // read by the leader (CTA 0) only
     if (leader) fused_begin(P, H, n_iter, gthreads);
     int done = 0;
+    bool merged = false;  // the last barrier already published this iteration's parameters
     for (;;) {
-        cluster_barrier();
+        if (!merged) cluster_barrier();
         const int ctl = ld_volatile_i32(&H->graph_ctl);
         if (!(ctl & 1)) break;
         // this iteration's parameters, written by the leader before the barrier
@@ -198,6 +199,10 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         const uint32_t word = __ballot_sync(FULL, won);
         if (lane == 0) dsmem_store(s_cnt + chunk, 0, (uint32_t)__popc(word));
         cluster_barrier();
+        // the tree's size before this iteration's appends and the winners
+        // kept: every thread derives them alike (prune uses them too, so it
+        // reads no header field the leader may rewrite at its end)
+        int n_old, kept;
         {
             uint32_t before = 0, total = 0;
             for (int k = lane; k < n_chunks; k += 32) {
@@ -208,9 +213,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
             before = warp_sum_u32(before);
             total = warp_sum_u32(total);
             const int W = (int)total;
-            const int n_old = H->n_nodes;
+            n_old = H->n_nodes;
             const int room = P.N - n_old;
-            const int kept = W < room ? W : room;
+            kept = W < room ? W : room;
             if (leader) {
                 H->n_win = W;
                 H->n_kept = kept;
@@ -224,19 +229,30 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         }
         cluster_barrier();
         // prune (Alg. 3) + compaction of the next V_A
+        const int total = n_old + kept;
+        const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
+        // one tile: CTA 0 prunes it alone, and its leader ends this iteration
+        // and begins the next before the barrier, which then also publishes
+        // the next iteration's parameters (no barrier at the top)
+        merged = n_tiles <= 1;
         {
-            const int n_old = H->n_nodes;
-            const int total = n_old + H->n_kept;
-            const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
             int cA = 0, cI = 0, cT = 0;
             for (int t = blockIdx.x; t < n_tiles; t += n_cta)
                 prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, s_parent, s_set, s_icount, s_anc, s_warp,
                            s_prefix, cA, cI, cT);
-            flush_prune_counters(H, cA, cI, cT);
+            flush_prune_counters(H, cA, cI, cT);  // CTAs without a tile touch nothing
+        }
+        ++done;
+        if (merged && blockIdx.x == 0) {
+            __syncthreads();  // the CTA's prune counts are in the header
+            if (leader) {
+                end_counters(P, H);
+                H->fused_iterations += 1;
+                fused_begin(P, H, n_iter - done, gthreads);
+            }
         }
         cluster_barrier();
-        ++done;
-        if (leader) {
+        if (!merged && leader) {
             end_counters(P, H);
             H->fused_iterations += 1;
             fused_begin(P, H, n_iter - done, gthreads);
