@@ -508,7 +508,7 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     if (!finite(cost->w_effort) || cost->w_effort < 0.0f) return reject(KPX_E_INVALID, "w_effort must be >= 0");
     if (cost->kind == KPX_COST_EFFORT_DURATION && dyn->kind != KPX_QUAD12)
         return reject(KPX_E_INVALID, "effort+duration cost needs the quadcopter");
-    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
+    const int n = kStateDim[dyn->kind];
     for (int i = 0; i < n; ++i)
         if (!finite(start[i])) return reject(KPX_E_INVALID, "start state must be finite");
 
