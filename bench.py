@@ -135,6 +135,7 @@ def parse_args(argv=None):
     ap.add_argument("--serve-memory-gb", type=float, default=32.0, help="device arena of the request loop")
     ap.add_argument("--serve-slots", type=int, default=64, help="request-loop slots per dynamics class")
     ap.add_argument("--serve-round", type=int, default=4, help="iterations per request-loop round")
+    ap.add_argument("--batch-count", type=int, default=0, help="problems of the batch workload (0 = its own)")
     ap.add_argument("--refine-count", type=int, default=0, help="trajectories of the refinement workload "
                                                                  "(0: the workload's 4,096)")
     return ap.parse_args(argv)
@@ -526,7 +527,9 @@ def run_batch(args):
     dev = torch.device("cuda", local)
     import paper_2602_02846_gb300 as kpx
     kpx.load()
-    spec = BATCH_WORKLOADS[args.workload]
+    spec = dict(BATCH_WORKLOADS[args.workload])
+    if args.batch_count > 0:  # a smaller batch of the same mix (profiling)
+        spec["count"] = args.batch_count
     iters = args.iters or 100
     probs = scenes.mixed_batch(spec["count"], seed=args.seed + 1000 * rank, iterations=iters)
     stream = torch.cuda.Stream(dev)
