@@ -130,6 +130,8 @@ def _declare(L):
     L.kpo_prune.argtypes = [C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int32]
     L.kpo_compact.argtypes = [C.c_int32, vp, vp, vp]
     L.kpo_compact.restype = C.c_int32
+    L.kpo_append.argtypes = [C.POINTER(Problem), C.c_int32, C.c_int32] + [vp] * 7 + [vp] * 11
+    L.kpo_append.restype = C.c_int32
     L.kpo_create.argtypes = [C.POINTER(Problem), vp]
     L.kpo_create.restype = vp
     L.kpo_iterate.argtypes = [vp, C.c_int32]
@@ -357,6 +359,35 @@ def prune(key, region_, parent, set_, icount, region_key, i_max):
     lib().kpo_prune(key.shape[0], key.ctypes.data, region_.ctypes.data, parent.ctypes.data, s.ctypes.data,
                     ic.ctypes.data, rk.ctypes.data, int(i_max))
     return s, ic
+
+
+def append(prob, n_nodes, cand, tree, region_key, goal_key):
+    """UpdateTree (Alg. 4) for one iteration's kept winners (kpo_append).
+    cand: arrays in slot order -- x [k][n], u [k][m], K, parent, cost (the
+    accumulated cost), region, goal (end state in the goal set).  tree: the
+    tree arrays x [N][n], u [N][m], K, parent, cost, key, region, set,
+    icount.  Returns (tree, region_key, goal_key, first_solution), the inputs
+    left unchanged."""
+    P = as_oracle(prob)
+    k = int(np.asarray(cand["K"]).shape[0])
+    cx = np.ascontiguousarray(cand["x"], dtype=np.float64).reshape(k, P.n)
+    cu = np.ascontiguousarray(cand["u"], dtype=np.float32).reshape(k, P.m)
+    cK = np.ascontiguousarray(cand["K"], dtype=np.int32)
+    cp = np.ascontiguousarray(cand["parent"], dtype=np.int32)
+    cc = np.ascontiguousarray(cand["cost"], dtype=np.float64)
+    cr = np.ascontiguousarray(cand["region"], dtype=np.int32)
+    cg = np.ascontiguousarray(cand["goal"], dtype=np.uint8)
+    types = dict(x=np.float64, u=np.float32, K=np.int32, parent=np.int32, cost=np.float64, key=np.uint64,
+                 region=np.int32, set=np.uint8, icount=np.uint8)
+    t = {name: np.ascontiguousarray(tree[name], dtype=dt).copy() for name, dt in types.items()}
+    rk = np.ascontiguousarray(region_key, dtype=np.uint64).copy()
+    gk = np.array([goal_key], dtype=np.uint64)
+    first = lib().kpo_append(P.ref, int(n_nodes), k, cx.ctypes.data, cu.ctypes.data, cK.ctypes.data,
+                             cp.ctypes.data, cc.ctypes.data, cr.ctypes.data, cg.ctypes.data, t["x"].ctypes.data,
+                             t["u"].ctypes.data, t["K"].ctypes.data, t["parent"].ctypes.data, t["cost"].ctypes.data,
+                             t["key"].ctypes.data, t["region"].ctypes.data, t["set"].ctypes.data,
+                             t["icount"].ctypes.data, rk.ctypes.data, gk.ctypes.data)
+    return t, rk, int(gk[0]), bool(first)
 
 
 def compact(mask):

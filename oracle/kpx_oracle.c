@@ -552,6 +552,38 @@ kpo_planner* kpo_create(const kpo_problem* P, const double* start) {
     return pl;
 }
 
+/* UpdateTree (Alg. 4): each kept winner, in slot order, becomes the next
+ * node; its key (cost, id) is written to its region (the winner holds the
+ * region's least key, so this is the region's new best node); appended goal
+ * nodes lower the solution key (Reading: the solution is the least key over
+ * appended goal nodes). */
+int32_t kpo_append(const kpo_problem* P, int32_t n_nodes, int32_t n_kept, const double* cx, const float* cu,
+                   const int32_t* cK, const int32_t* cparent, const double* ccost, const int32_t* cregion,
+                   const uint8_t* cgoal, double* x, float* u, int32_t* K, int32_t* parent, double* cost,
+                   uint64_t* key, int32_t* region, uint8_t* set, uint8_t* icount, uint64_t* region_key,
+                   uint64_t* goal_key) {
+    const int n = P->n, m = P->m;
+    int32_t first = 0;
+    for (int32_t k = 0; k < n_kept; ++k) {
+        const int32_t id = n_nodes + k;
+        for (int d = 0; d < n; ++d) x[(int64_t)id * n + d] = cx[(int64_t)k * n + d];
+        for (int d = 0; d < m; ++d) u[(int64_t)id * m + d] = cu[(int64_t)k * m + d];
+        K[id] = cK[k];
+        parent[id] = cparent[k];
+        cost[id] = ccost[k];
+        key[id] = kpo_pack_key((float)ccost[k], (uint32_t)id);
+        region[id] = cregion[k];
+        set[id] = KPO_SET_A;
+        icount[id] = 0;
+        region_key[cregion[k]] = key[id];
+        if (cgoal[k] && key[id] < *goal_key) {
+            if (*goal_key == KPO_KEY_INF) first = 1;
+            *goal_key = key[id];
+        }
+    }
+    return first;
+}
+
 static void vu_push(kpo_planner* pl, int64_t* n, const kpo_cand* c) {
     if (*n == pl->vu_cap) {
         pl->vu_cap = pl->vu_cap ? 2 * pl->vu_cap : 1024;
@@ -607,23 +639,31 @@ static int32_t iterate_once(kpo_planner* pl) {
     kpo_prune(v->n_nodes, v->key, v->region, v->parent, v->set, v->icount, v->region_key, P->i_max);
 
     /* ---- UpdateTree (Alg. 4): append in slot order, solution update ---- */
-    for (int64_t i = 0; i < kept; ++i) {
-        const kpo_cand* c = &pl->vu[i];
-        int32_t id = v->n_nodes + (int32_t)i;
-        for (int d = 0; d < n; ++d) v->x[(int64_t)id * n + d] = c->x[d];
-        for (int d = 0; d < m; ++d) v->u[(int64_t)id * m + d] = c->u[d];
-        v->K[id] = c->K;
-        v->parent[id] = c->parent;
-        v->cost[id] = c->cost;
-        v->key[id] = kpo_pack_key((float)c->cost, (uint32_t)id);
-        v->region[id] = c->region;
-        v->set[id] = KPO_SET_A;
-        v->icount[id] = 0;
-        v->region_key[c->region] = v->key[id];
-        if (c->goal && v->key[id] < v->goal_key) {
-            if (v->goal_key == KPO_KEY_INF) v->first_solution_iter = v->iter;
-            v->goal_key = v->key[id];
+    if (kept > 0) {
+        double* cx = (double*)malloc((size_t)kept * n * sizeof(double));
+        float* cu = (float*)malloc((size_t)kept * m * sizeof(float));
+        int32_t* ci = (int32_t*)malloc((size_t)kept * 3 * sizeof(int32_t));
+        double* cc = (double*)malloc((size_t)kept * sizeof(double));
+        uint8_t* cg = (uint8_t*)malloc((size_t)kept);
+        for (int64_t i = 0; i < kept; ++i) {
+            const kpo_cand* c = &pl->vu[i];
+            for (int d = 0; d < n; ++d) cx[i * n + d] = c->x[d];
+            for (int d = 0; d < m; ++d) cu[i * m + d] = c->u[d];
+            ci[i] = c->K;
+            ci[kept + i] = c->parent;
+            ci[2 * kept + i] = c->region;
+            cc[i] = c->cost;
+            cg[i] = (uint8_t)(c->goal != 0);
         }
+        if (kpo_append(P, v->n_nodes, (int32_t)kept, cx, cu, ci, ci + kept, cc, ci + 2 * kept, cg, v->x, v->u,
+                       v->K, v->parent, v->cost, v->key, v->region, v->set, v->icount, v->region_key,
+                       &v->goal_key))
+            v->first_solution_iter = v->iter;
+        free(cx);
+        free(cu);
+        free(ci);
+        free(cc);
+        free(cg);
     }
     v->n_nodes += (int32_t)kept;
     /* next V_A: ascending ids (Alg. 5 compaction of the V_A mask) */

@@ -111,6 +111,20 @@ int32_t kpo_select_winners(int32_t R, uint64_t* region_key, const uint64_t* regi
 void kpo_prune(int32_t n_nodes, const uint64_t* key, const int32_t* region, const int32_t* parent,
                uint8_t* set, uint8_t* icount, const uint64_t* region_key, int32_t i_max);
 
+/* UpdateTree (Alg. 4), one iteration's appends.  The first n_kept winners,
+ * given in slot order (cx[k][n] end state, cu[k][m] control, cK, cparent,
+ * ccost accumulated cost, cregion, cgoal = end state in the goal set), become
+ * nodes n_nodes + k: their rows are written, their key is pack(cost, id),
+ * that key becomes their region's key, their set is V_A with icount 0, and
+ * an appended goal node lowers *goal_key.  Tree arrays are row-major
+ * (x[N][n], u[N][m]).  Returns 1 when *goal_key went from infinity to a
+ * solution, else 0. */
+int32_t kpo_append(const kpo_problem* P, int32_t n_nodes, int32_t n_kept, const double* cx, const float* cu,
+                   const int32_t* cK, const int32_t* cparent, const double* ccost, const int32_t* cregion,
+                   const uint8_t* cgoal, double* x, float* u, int32_t* K, int32_t* parent, double* cost,
+                   uint64_t* key, int32_t* region, uint8_t* set, uint8_t* icount, uint64_t* region_key,
+                   uint64_t* goal_key);
+
 /* Exclusive scan + GraphSearch compaction (Alg. 5): I = [i : mask[i]] and
  * the count S[n-1] + mask[n-1] (the last element of an exclusive scan alone
  * misses the last mask entry).  S may be NULL. */

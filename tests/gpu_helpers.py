@@ -112,26 +112,35 @@ def step_phases(pl, prob, check_append=True):
         n0 = before["n_nodes"]
         ids = np.arange(n0, n0 + kept)
         ws = win[:kept]
-        assert np.array_equal(after["parent"][ids], before["VA"][ws // lam]), "parents differ"
-        assert np.array_equal(after["K"][ids], g["K"][ws]), "K differs"
-        assert np.array_equal(after["u"][ids].view(np.uint32), g["u"][ws].view(np.uint32)), "controls differ"
+        # UpdateTree (Alg. 4) by the oracle on the GPU's winning candidates:
+        # rows, keys, region keys and the solution key
+        goal, amb = np.zeros(kept, np.uint8), 0
+        for k, w in enumerate(ws):
+            inside, margin = oracle.in_goal(prob, g["x"][w].astype(np.float64))
+            goal[k] = 1 if inside else 0
+            amb += 1 if margin < NEAR else 0
+        cand = dict(x=g["x"][ws].astype(np.float64), u=g["u"][ws], K=g["K"][ws], parent=before["VA"][ws // lam],
+                    cost=oracle.key_cost(g["key"][ws]).astype(np.float64), region=g["region"][ws], goal=goal)
+
+        def rows(a):
+            a = np.asarray(a)[:n0]
+            return np.concatenate([a, np.zeros((kept,) + a.shape[1:], a.dtype)])
+        tree = {name: rows(before[name]) for name in ("x", "u", "K", "parent", "key", "region", "set", "icount")}
+        tree["cost"] = rows(oracle.key_cost(before["key"]).astype(np.float64))
+        t, rk_o, gk_o, _ = oracle.append(prob, n0, cand, tree, rk_ref, before["goal_key"])
+        assert np.array_equal(after["region_key"], rk_o), "region keys after append differ from the oracle's"
+        assert np.array_equal(after["parent"][ids], t["parent"][ids]), "parents differ"
+        assert np.array_equal(after["K"][ids], t["K"][ids]), "K differs"
+        assert np.array_equal(after["u"][ids].view(np.uint32), t["u"][ids].view(np.uint32)), "controls differ"
         # re-materialised winners are bit-identical to the propagate records
         assert np.array_equal(after["x"][ids].view(np.uint32), g["x"][ws].view(np.uint32)), "re-materialised state differs"
-        assert np.array_equal(after["key"][ids] >> np.uint64(32), g["key"][ws] >> np.uint64(32))
-        assert np.array_equal(after["key"][ids] & np.uint64(0xFFFFFFFF), ids.astype(np.uint64))
-        assert np.array_equal(after["region"][ids], g["region"][ws])
-        assert np.all(after["set"][ids] == A) and np.all(after["icount"][ids] == 0)
+        assert np.array_equal(after["key"][ids], t["key"][ids]), "keys differ"
+        assert np.array_equal(after["region"][ids], t["region"][ids])
+        assert np.array_equal(after["set"][ids], t["set"][ids]) and np.array_equal(after["icount"][ids],
+                                                                                   t["icount"][ids])
         # solution: least key among appended goal nodes (oracle goal test in FP64)
-        gk = before["goal_key"]
-        amb = 0
-        for i in ids:
-            inside, margin = oracle.in_goal(prob, after["x"][i].astype(np.float64))
-            if margin < NEAR:
-                amb += 1
-            if inside:
-                gk = min(gk, int(after["key"][i]))
         if amb == 0:
-            assert int(pl.header().goal_key) == gk, "solution key differs"
+            assert int(pl.header().goal_key) == gk_o, "solution key differs"
         rep["goal_exempt"] = amb
     # prune: oracle Alg. 3 on the same (pre-append) nodes and region keys
     s_ref, ic_ref = oracle.prune(before["key"], before["region"], before["parent"], before["set"],

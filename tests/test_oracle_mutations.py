@@ -70,6 +70,12 @@ MUTATIONS = [
     ("select_no_filter", "if (key[c] == region_key[region[c]]) winners[w++] = c;", "winners[w++] = c;",
      [stp.test_select_winners_min_ties_and_filter]),
     ("select_no_restore", "region_key[r] = region_snap[r];", "(void)r;", [stp.test_select_winners_capacity]),
+    ("append_no_region_key", "region_key[cregion[k]] = key[id];", "(void)id;",
+     [stp.test_append_rows_keys_and_solution]),
+    ("append_key_slot_id", "key[id] = kpo_pack_key((float)ccost[k], (uint32_t)id);",
+     "key[id] = kpo_pack_key((float)ccost[k], (uint32_t)k);", [stp.test_append_rows_keys_and_solution]),
+    ("append_goal_any", "if (cgoal[k] && key[id] < *goal_key) {", "if (key[id] < *goal_key) {",
+     [stp.test_append_rows_keys_and_solution]),
     ("prune_rule2_drops_best", "if (icount[i] > i_max && best) continue;", "if (icount[i] > i_max) continue;",
      [stp.test_prune_reactivation_after_imax]),
     ("prune_terminal_skip_dropped", "if (set[i] == KPO_SET_T) continue;", "(void)0;",

@@ -1,5 +1,6 @@
-"""Oracle pins: compaction (Alg. 5), region argmin + V_U filter (Alg. 2/4)
-and PruneNodes (Alg. 3) on hand-built inputs with hand-derived outcomes.
+"""Oracle pins: compaction (Alg. 5), region argmin + V_U filter (Alg. 2/4),
+PruneNodes (Alg. 3) and UpdateTree's append (Alg. 4) on hand-built inputs
+with hand-derived outcomes.
 
 Pins: the paper's own compaction example (tests/golden), and small trees
 whose expected node sets follow from reading Alg. 3 rule by rule.
@@ -164,3 +165,85 @@ def test_prune_ancestor_chain_is_strict_and_reaches_root(oracle_mod):
     rk[1] = key(o, 0.1, 99)
     s, _ = o.prune(keys, region, parent, sets, ic, rk, i_max=3)
     assert list(s) == [A, T, I, I, A]
+
+
+def _append_case(o):
+    """A 2-node tree (DI dimensions) and two kept winners: slot order gives
+    node ids 2 and 3; only the second, the dearer one, ends in the goal set."""
+    from paper_2602_02846_gb300 import scenes
+    prob = scenes.di_scene(0)
+    n, m, N, R = prob.n, prob.m, 8, 16
+    tree = dict(x=np.zeros((N, n)), u=np.zeros((N, m), np.float32), K=np.zeros(N, np.int32),
+                parent=np.full(N, -1, np.int32), cost=np.zeros(N), key=np.full(N, INF, np.uint64),
+                region=np.zeros(N, np.int32), set=np.zeros(N, np.uint8), icount=np.zeros(N, np.uint8))
+    tree["key"][0] = key(o, 0.0, 0)
+    tree["key"][1] = key(o, 0.75, 1)
+    tree["region"][:2] = [3, 5]
+    tree["set"][:2] = [A, I]
+    tree["icount"][1] = 4
+    rk = np.full(R, INF, np.uint64)
+    rk[3], rk[5] = tree["key"][0], tree["key"][1]
+    cand = dict(x=np.arange(2 * n, dtype=np.float64).reshape(2, n), u=np.array([[1, 2, 3], [4, 5, 6]], np.float32),
+                K=np.array([7, 9], np.int32), parent=np.array([0, 1], np.int32), cost=np.array([0.25, 0.5]),
+                region=np.array([5, 7], np.int32), goal=np.array([0, 1], np.uint8))
+    return prob, tree, rk, cand
+
+
+def test_append_rows_keys_and_solution(oracle_mod):
+    o = oracle_mod
+    prob, tree, rk, cand = _append_case(o)
+    t, rk2, gk, first = o.append(prob, 2, cand, tree, rk, INF)
+    for k, i in enumerate((2, 3)):
+        assert np.array_equal(t["x"][i], cand["x"][k]) and np.array_equal(t["u"][i], cand["u"][k])
+        assert t["K"][i] == cand["K"][k] and t["parent"][i] == cand["parent"][k]
+        assert t["cost"][i] == cand["cost"][k] and t["region"][i] == cand["region"][k]
+        assert t["key"][i] == key(o, float(cand["cost"][k]), i)  # (cost, id): the node's own id
+        assert t["set"][i] == A and t["icount"][i] == 0
+    # each winner's key becomes its region's key (region 5 changes hands)
+    assert rk2[5] == key(o, 0.25, 2) and rk2[7] == key(o, 0.5, 3)
+    assert rk2[3] == rk[3] and np.all(np.delete(rk2, [5, 7]) == np.delete(rk, [5, 7]))
+    # the untouched nodes keep their rows
+    assert t["key"][1] == tree["key"][1] and t["set"][1] == I and t["icount"][1] == 4
+    # the appended goal node is the solution (not the cheaper non-goal one), the first one
+    assert gk == key(o, 0.5, 3) and first
+    # a better solution already held is kept and is not a first
+    best = key(o, 0.1, 1)
+    _, _, gk, first = o.append(prob, 2, cand, tree, rk, best)
+    assert gk == best and not first
+
+
+def test_append_then_planner_iteration_agree(oracle_mod):
+    """One planner iteration equals its steps composed by hand: propagate,
+    select winners, prune, append."""
+    from paper_2602_02846_gb300 import scenes
+    o = oracle_mod
+    prob = scenes.di_scene(1, grid_pos=16, tree_cap=4096)
+    pl = o.Planner(prob)
+    pl.iterate(3)
+    s0 = pl.state()
+    n0 = s0["n_nodes"]
+    it, lam = s0["iter"], int(prob.lam)
+    pr = o.propagate(prob, it, lam, s0["x"][:n0], s0["cost"][:n0], s0["VA"], s0["count_A"])
+    rk, win, kept, full = o.select_winners(s0["region_key"], s0["region_key"], pr["valid"],
+                                           np.where(pr["valid"] == 1, pr["region"], 0), pr["key"], n0,
+                                           int(prob.tree_cap))
+    st, ic = o.prune(s0["key"][:n0], s0["region"][:n0], s0["parent"][:n0], s0["set"][:n0], s0["icount"][:n0], rk,
+                     prob.i_max)
+    ws = win[:kept]
+    cand = dict(x=pr["x_end"][ws], u=pr["u"][ws], K=pr["K"][ws], parent=np.asarray(s0["VA"])[ws // lam],
+                cost=pr["cost"][ws], region=pr["region"][ws], goal=pr["in_goal"][ws])
+    n1 = n0 + kept
+
+    def rows(a):  # the first n0 rows, room for the appended ones after them
+        a = np.asarray(a)
+        return np.concatenate([a, np.zeros((kept,) + a.shape[1:], a.dtype)])
+    tree = {name: rows(s0[name]) for name in ("x", "u", "K", "parent", "cost", "key", "region")}
+    tree["set"], tree["icount"] = rows(st), rows(ic)
+    t, rk2, gk, _ = o.append(prob, n0, cand, tree, rk, s0["goal_key"])
+    pl.iterate(1)
+    s1 = pl.state()
+    assert s1["n_nodes"] == n1 and not full and kept > 0
+    for name in ("x", "u", "K", "parent", "key", "region", "set", "icount"):
+        assert np.array_equal(np.asarray(s1[name])[:n1], t[name][:n1]), name
+    assert np.array_equal(s1["region_key"], rk2) and s1["goal_key"] == gk
+
