@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_b_prune(BatchParams BP) {
         const int n_old = H->n_nodes;
         const int n_tiles = (int)(BP.prune_prefix[p + 1] - BP.prune_prefix[p]);
         int cA = 0, cI = 0, cT = 0;
-        prune_tile(P, H, (uint32_t)(t - BP.prune_prefix[p]), n_tiles, n_old, n_old + H->n_kept, s_parent, s_set,
-                   s_icount, s_anc, s_warp, s_prefix, cA, cI, cT);
+        prune_tile(P, H, (uint32_t)(t - BP.prune_prefix[p]), n_tiles, n_old, n_old + H->n_kept, (uint32_t)H->epoch,
+                   va_following(P, H), s_parent, s_set, s_icount, s_anc, s_warp, s_prefix, cA, cI, cT);
         flush_prune_counters(H, cA, cI, cT);
     }
 }

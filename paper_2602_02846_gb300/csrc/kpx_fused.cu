@@ -51,8 +51,6 @@ __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
-__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) { return *(volatile const int32_t*)p; }
-
 // distributed shared memory: a generic pointer to CTA `cta`'s copy of a
 // shared variable (plain loads, stores and atomics reach it)
 template <typename T>
@@ -74,16 +72,56 @@ __device__ __forceinline__ void dsmem_store(const uint32_t* p, uint32_t cta, uin
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(dsmem_addr(p, cta)), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint32_t dsmem_load(const uint32_t* p, uint32_t cta) {
-    uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(dsmem_addr(p, cta)) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
+}
+
+// warp-wide, once per launch: add the launch's propagate counters to the
+// header (the totals, and the last iteration's valid candidates)
+__device__ __forceinline__ void flush_launch_counters(kpx_device_header* H, uint64_t steps, uint64_t tests,
+                                                      uint32_t valid, uint32_t last) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        steps += __shfl_down_sync(FULL, steps, o);
+        tests += __shfl_down_sync(FULL, tests, o);
+        valid += __shfl_down_sync(FULL, valid, o);
+        last += __shfl_down_sync(FULL, last, o);
+    }
+    if ((threadIdx.x & 31) == 0 && steps) {
+        atomicAdd((unsigned long long*)&H->total_steps, (unsigned long long)steps);
+        atomicAdd((unsigned long long*)&H->total_box_tests, (unsigned long long)tests);
+        if (valid) atomicAdd((unsigned long long*)&H->total_valid, (unsigned long long)valid);
+        if (last) atomicAdd((unsigned long long*)&H->last_valid, (unsigned long long)last);
+    }
+}
+
+// An iteration's parameters as the leader's begin leaves them in the header.
+// The leader's warp copies them into every CTA's shared memory before the
+// barrier that publishes them, so that after it each warp reads them from
+// its own SM instead of all warps of the cluster reading CTA 0's.
+struct IterParams {
+    int64_t n_slots;
+    int32_t ctl, lambda, iter, n_nodes, va_sel, epoch;
+};
+static_assert(sizeof(IterParams) == 32, "two 16-byte words");
+
+// warp 0 of CTA 0, after the leader's begin: lane c writes CTA c's copy
+__device__ __forceinline__ void publish_iteration(const kpx_device_header* H, IterParams* s_it, int n_cta) {
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    if (lane < n_cta) {
+        IterParams v;
+        v.n_slots = H->n_slots;
+        v.ctl = H->graph_ctl;
+        v.lambda = H->lambda;
+        v.iter = H->iter;
+        v.n_nodes = H->n_nodes;
+        v.va_sel = H->va_sel;
+        v.epoch = H->epoch;
+        *dsmem_generic(s_it, (uint32_t)lane) = v;
+    }
 }
 
 // Leader only: decide whether the next iteration runs here; if so, begin it.
@@ -115,13 +153,14 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint8_t s_icount[PRUNE_TILE];
     __shared__ uint8_t s_anc[PRUNE_TILE];
-    __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // CTA 0's: winners per chunk
+    __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // winners per chunk (every CTA's copy)
     // While the launch runs, the header lives in CTA 0's shared memory: the
     // leader's bookkeeping and every CTA's reads and counter atomics reach it
     // over distributed shared memory instead of L2 (each cluster barrier's
     // acquire would otherwise send every header read back to L2).  It is
     // copied in here and written back before the kernel exits.
     __shared__ __align__(16) kpx_device_header s_hdr;
+    __shared__ __align__(16) IterParams s_it;  // this CTA's copy of the iteration's parameters
     constexpr int HDR_WORDS = (int)(sizeof(kpx_device_header) / sizeof(uint32_t));
     static_assert(sizeof(kpx_device_header) % sizeof(uint32_t) == 0, "header size");
     if (blockIdx.x == 0) {
@@ -148,18 +187,34 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         G = GridView{sc, sb};
     }
     if (n_iter < 0) n_iter = s_hdr.graph_pending;  // read by the leader (CTA 0) only
-    if (leader) fused_begin(P, H, n_iter, gthreads);
+    const bool lead_warp = blockIdx.x == 0 && threadIdx.x < 32;
+    if (lead_warp) {
+        if (leader) fused_begin(P, H, n_iter, gthreads);
+        publish_iteration(H, &s_it, n_cta);
+    }
     int done = 0;
+    // the propagate counters (integration steps, box tests, valid candidates)
+    // stay in registers for the whole launch and reach the header once at its
+    // end: they are statistics, and no decision of the leader reads them
+    uint64_t acc_steps = 0, acc_tests = 0;
+    uint32_t acc_valid = 0, last_valid = 0;
+    int pA = 0, pI = 0, pT = 0;  // V_A, V_I, V_T sizes of this thread's nodes in the latest iteration
     bool merged = false;  // the last barrier already published this iteration's parameters
     for (;;) {
         if (!merged) cluster_barrier();
-        const int ctl = ld_volatile_i32(&H->graph_ctl);
+        // this iteration's parameters, published by the barrier (this CTA's
+        // copy): all of them are taken here, so the leader's warp may write
+        // the next iteration's while the cluster is still in this one
+        const IterParams it = s_it;
+        const int ctl = it.ctl;
         if (!(ctl & 1)) break;
-        // this iteration's parameters, written by the leader before the barrier
-        const int64_t n_slots = H->n_slots;
-        const int lam = H->lambda;
-        const uint32_t iter = (uint32_t)H->iter;
-        const int32_t* va = va_current(P, H);
+        const int64_t n_slots = it.n_slots;
+        const int lam = it.lambda;
+        const uint32_t iter = (uint32_t)it.iter;
+        const int n_old = it.n_nodes;  // the tree's size before this iteration's appends
+        const int32_t* va = it.va_sel ? P.va1 : P.va0;
+        int32_t* va_next = it.va_sel ? P.va0 : P.va1;
+        const uint32_t epoch = (uint32_t)it.epoch;
         if (ctl & 2) {  // region snapshot for the capacity rule
             for (int64_t r = gtid; r < P.R; r += gthreads) P.region_snap[r] = P.region_key[r];
             cluster_barrier();
@@ -188,32 +243,34 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
                     roll_candidate<DYN, INTEG, false>(P, G, lam, iter, va, early, slot, C, steps, tests);
             }
             n_valid = C.ok ? 1u : 0u;
-            flush_propagate_counters(H, steps, tests, n_valid);
+            acc_steps += steps;
+            acc_tests += tests;
+            acc_valid += n_valid;
+            last_valid = n_valid;
         }
         cluster_barrier();
         // the V_U filter and the winner ranks in slot order: a valid
         // candidate is its region's winner when the region holds its key;
-        // each warp publishes its winner count to CTA 0 (distributed shared
-        // memory), indexed by chunk
+        // each warp publishes its winner count to every CTA of the cluster
+        // (lane c stores it into CTA c's array, over distributed shared
+        // memory), indexed by chunk, so that the ranks read local words
         const bool won = C.ok && __ldcg(&P.region_key[C.r]) == C.key;
         const uint32_t word = __ballot_sync(FULL, won);
-        if (lane == 0) dsmem_store(s_cnt + chunk, 0, (uint32_t)__popc(word));
+        if (lane < n_cta) dsmem_store(s_cnt + chunk, (uint32_t)lane, (uint32_t)__popc(word));
         cluster_barrier();
-        // the tree's size before this iteration's appends and the winners
-        // kept: every thread derives them alike (prune uses them too, so it
-        // reads no header field the leader may rewrite at its end)
-        int n_old, kept;
+        // the winners kept: every thread derives them alike (prune uses them
+        // too, so it reads no header field the leader may rewrite at its end)
+        int kept;
         {
             uint32_t before = 0, total = 0;
             for (int k = lane; k < n_chunks; k += 32) {
-                const uint32_t v = dsmem_load(s_cnt + k, 0);
+                const uint32_t v = *(volatile const uint32_t*)&s_cnt[k];
                 total += v;
                 if (k < chunk) before += v;
             }
             before = warp_sum_u32(before);
             total = warp_sum_u32(total);
             const int W = (int)total;
-            n_old = H->n_nodes;
             const int room = P.N - n_old;
             kept = W < room ? W : room;
             if (leader) {
@@ -235,29 +292,36 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         // and begins the next before the barrier, which then also publishes
         // the next iteration's parameters (no barrier at the top)
         merged = n_tiles <= 1;
-        {
-            int cA = 0, cI = 0, cT = 0;
-            for (int t = blockIdx.x; t < n_tiles; t += n_cta)
-                prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, s_parent, s_set, s_icount, s_anc, s_warp,
-                           s_prefix, cA, cI, cT);
-            flush_prune_counters(H, cA, cI, cT);  // CTAs without a tile touch nothing
-        }
+        // the set sizes stay in registers: every begin resets the header's,
+        // so only the launch's last iteration reaches it, at the end
+        pA = pI = pT = 0;
+        for (int t = blockIdx.x; t < n_tiles; t += n_cta)
+            prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_anc,
+                       s_warp, s_prefix, pA, pI, pT);
         ++done;
-        if (merged && blockIdx.x == 0) {
-            __syncthreads();  // the CTA's prune counts are in the header
+        if (merged && lead_warp) {  // prune_tile ended with a CTA barrier
             if (leader) {
-                end_counters(P, H);
+                end_counters(P, H, false);
                 H->fused_iterations += 1;
                 fused_begin(P, H, n_iter - done, gthreads);
             }
+            publish_iteration(H, &s_it, n_cta);
         }
         cluster_barrier();
-        if (!merged && leader) {
-            end_counters(P, H);
-            H->fused_iterations += 1;
-            fused_begin(P, H, n_iter - done, gthreads);
+        if (!merged && lead_warp) {
+            if (leader) {
+                end_counters(P, H, false);
+                H->fused_iterations += 1;
+                fused_begin(P, H, n_iter - done, gthreads);
+            }
+            publish_iteration(H, &s_it, n_cta);
         }
     }
+    if (leader && done > 0) H->t_last_ns = globaltimer_ns();  // the last iteration's end
+    // every begin reset last_valid, so the header holds the sums over the
+    // launch's iterations (total_valid) and over its last one (last_valid)
+    flush_launch_counters(H, acc_steps, acc_tests, acc_valid, last_valid);
+    flush_prune_counters(H, pA, pI, pT);
     // every CTA has read the header for the last time; CTA 0 writes it back
     cluster_barrier();
     if (blockIdx.x == 0) {

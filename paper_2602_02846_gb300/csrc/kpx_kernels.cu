@@ -262,6 +262,8 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
     const int total = n_old + H->n_kept;
     const int n_tiles = (total + PRUNE_TILE - 1) / PRUNE_TILE;
     if ((int)blockIdx.x >= n_tiles) return;  // the other blocks take every tile
+    const uint32_t epoch = (uint32_t)H->epoch;
+    int32_t* va_next = va_following(P, H);
     int cA = 0, cI = 0, cT = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&H->prune_ticket, 1u);
@@ -269,7 +271,8 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
         const uint32_t tile = s_tile;
         __syncthreads();
         if ((int)tile >= n_tiles) break;
-        prune_tile(P, H, tile, n_tiles, n_old, total, s_parent, s_set, s_icount, s_anc, s_warp, s_prefix, cA, cI, cT);
+        prune_tile(P, H, tile, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_anc, s_warp,
+                   s_prefix, cA, cI, cT);
     }
     flush_prune_counters(H, cA, cI, cT);
 }

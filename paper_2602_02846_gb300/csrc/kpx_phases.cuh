@@ -105,6 +105,11 @@ __device__ __forceinline__ const int32_t* va_current(const DevParams& P, const k
     return H->va_sel ? P.va1 : P.va0;
 }
 
+// the buffer that receives the next V_A (the compaction's output)
+__device__ __forceinline__ int32_t* va_following(const DevParams& P, const kpx_device_header* H) {
+    return H->va_sel ? P.va0 : P.va1;
+}
+
 // ---------------------------------------------------------------------------
 // begin: branching factor (fixed, or floor(t_e/|V_A|)), slot count, tickets.
 // ---------------------------------------------------------------------------
@@ -474,9 +479,12 @@ __device__ __forceinline__ bool prune_rules_123(uint8_t sb, int i_max, int& ic, 
 // prune (block-wide): PruneNodes (Alg. 3) over the tile's nodes below n_old,
 // literal rule order, then the tile's part of the compaction of V_A (Alg. 5)
 // over [0, total): nodes appended this iteration are active by Alg. 4.
+// epoch and va_next are the iteration's (the header's epoch, and the V_A
+// buffer that va_sel does not select), read by the caller.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
-                                           int n_old, int total, int32_t* s_parent, uint8_t* s_set,
+                                           int n_old, int total, uint32_t epoch, int32_t* va_next,
+                                           int32_t* s_parent, uint8_t* s_set,
                                            uint8_t* s_icount, uint8_t* s_anc, uint32_t* s_warp,
                                            uint32_t& s_prefix, int& cA, int& cI, int& cT) {
     const int i_max = P.i_max;
@@ -561,11 +569,10 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
     uint32_t agg;
     const uint32_t excl = block_exclusive_scan<PRUNE_THREADS>((uint32_t)__popc(amask), agg, s_warp);
     if (threadIdx.x == 0) {
-        s_prefix = lookback(P.prune_tiles, tile, agg, (uint32_t)H->epoch, H);
+        s_prefix = lookback(P.prune_tiles, tile, agg, epoch, H);
         if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
     }
     __syncthreads();
-    int32_t* va_next = H->va_sel ? P.va0 : P.va1;
     uint32_t pos = s_prefix + excl;
 #pragma unroll
     for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
@@ -599,8 +606,11 @@ __device__ __forceinline__ void flush_prune_counters(kpx_device_header* H, int& 
 
 // ---------------------------------------------------------------------------
 // end (one thread per problem): commit the counters of the iteration.
+// stamp_last: take the end-of-iteration time now; the fused kernel passes
+// false and stamps it once when its launch ends (its header is private to the
+// launch until then), keeping the global timer off the iteration's chain.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void end_counters(const DevParams& P, kpx_device_header* H) {
+__device__ __forceinline__ void end_counters(const DevParams& P, kpx_device_header* H, bool stamp_last = true) {
     if (!H->active) return;
     H->n_nodes += H->n_kept;
     H->count_A = H->count_A_next;
@@ -610,13 +620,14 @@ __device__ __forceinline__ void end_counters(const DevParams& P, kpx_device_head
     H->total_candidates += (uint64_t)H->n_slots;
     H->total_valid += H->last_valid;
     H->total_winners += (uint64_t)H->n_kept;
-    const uint64_t now = globaltimer_ns();
+    uint64_t now = 0ull;
     if (H->goal_key != KEY_INF && H->first_solution_iter < 0) {
+        now = globaltimer_ns();
         H->first_solution_iter = H->iter;
         H->t_first_solution_ns = now;
     }
     H->iter += 1;
-    H->t_last_ns = now;
+    if (stamp_last) H->t_last_ns = now ? now : globaltimer_ns();
 }
 
 }  // namespace kpx

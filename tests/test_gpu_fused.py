@@ -30,7 +30,8 @@ def _state(pl):
     a["counters"] = np.array([h.status, h.iter, h.n_nodes, h.count_A, h.first_solution_iter, h.n_active,
                               h.n_inactive, h.n_terminal, h.lam], np.int64)
     a["totals"] = np.array([h.total_candidates, h.total_valid, h.total_winners, h.total_steps,
-                            h.total_box_tests, h.goal_key], np.uint64)
+                            h.total_box_tests, h.goal_key, h.last_candidates, h.last_valid, h.last_winners],
+                           np.uint64)
     a.pop("region_snap")  # scratch of the capacity rule: unwritten until a snapshot is due
     return a
 
@@ -101,12 +102,18 @@ def test_one_launch_per_call_and_count_updates(kpx):
     mx, fused = pl.graph_info()
     assert fused and mx > 1000
     assert kpx.Planner.launch_plan(200, mx) == [200]
-    done = 0
+    done, t_prev = 0, 0
     for n in (5, 5, 1, 37, 37, 2, 16):
         pl.iterate(n)
         done += n
         h = pl.header()
         assert h.iter == done and h.fused_iterations == done and h.graph_pending == 0
+        # device clock: the launch's first iteration began after the
+        # planner's start, and its last one ended after it began
+        assert 0 < h.t_start_ns < h.t_last_ns
+        assert h.first_solution_iter < 0 or h.t_start_ns <= h.t_first_solution_ns <= h.t_last_ns
+        assert h.t_last_ns > t_prev
+        t_prev = h.t_last_ns
     pl.close()
 
 
