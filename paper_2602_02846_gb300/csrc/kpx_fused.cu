@@ -188,9 +188,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     }
     if (n_iter < 0) n_iter = s_hdr.graph_pending;  // read by the leader (CTA 0) only
     const bool lead_warp = blockIdx.x == 0 && threadIdx.x < 32;
+    // the leader's warp keeps the books through CTA 0's own window
+    kpx_device_header* HL = &s_hdr;
     if (lead_warp) {
-        if (leader) fused_begin(P, H, n_iter, gthreads);
-        publish_iteration(H, &s_it, n_cta);
+        if (leader) fused_begin(P, HL, n_iter, gthreads);
+        publish_iteration(HL, &s_it, n_cta);
     }
     int done = 0;
     // the propagate counters (integration steps, box tests, valid candidates)
@@ -237,10 +239,21 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
                 else
                     roll_candidate_coop<DYN, INTEG, false>(P, G, lam, iter, va, live, slot, g, C, steps, tests);
             } else if (live) {
-                if (grid_smem)
-                    roll_candidate<DYN, INTEG, true>(P, G, lam, iter, va, early, slot, C, steps, tests);
-                else
-                    roll_candidate<DYN, INTEG, false>(P, G, lam, iter, va, early, slot, C, steps, tests);
+                if (early) {
+                    if (grid_smem)
+                        roll_candidate<DYN, INTEG, true>(P, G, lam, iter, va, true, slot, C, steps, tests);
+                    else
+                        roll_candidate<DYN, INTEG, false>(P, G, lam, iter, va, true, slot, C, steps, tests);
+                } else if (DYN == KPX_DI6) {  // a short step: nothing to overlap
+                    if (grid_smem)
+                        roll_candidate<DYN, INTEG, true>(P, G, lam, iter, va, false, slot, C, steps, tests);
+                    else
+                        roll_candidate<DYN, INTEG, false>(P, G, lam, iter, va, false, slot, C, steps, tests);
+                } else if (grid_smem) {
+                    roll_candidate_ahead<DYN, INTEG, true>(P, G, lam, iter, va, slot, C, steps, tests);
+                } else {
+                    roll_candidate_ahead<DYN, INTEG, false>(P, G, lam, iter, va, slot, C, steps, tests);
+                }
             }
             n_valid = C.ok ? 1u : 0u;
             acc_steps += steps;
@@ -254,7 +267,20 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         // each warp publishes its winner count to every CTA of the cluster
         // (lane c stores it into CTA c's array, over distributed shared
         // memory), indexed by chunk, so that the ranks read local words
-        const bool won = C.ok && __ldcg(&P.region_key[C.r]) == C.key;
+        // (a valid candidate also reads its region's key node, which only
+        // the region's winner rewrites, in the append phase: one L2 round
+        // trip fewer there)
+        bool won = false;
+        int owner = -1;
+        if (C.ok) {
+            const uint64_t rk = __ldcg(&P.region_key[C.r]);
+            owner = __ldcg(&P.region_owner[C.r]);
+            won = rk == C.key;
+        }
+        // CTA 0 prunes tile 0: it stages the tile now, in the same round
+        // trip, and the winners that take a region from one of its nodes
+        // write that node's new set byte into the staged copy as well
+        if (blockIdx.x == 0) stage_tile(P, 0, n_old, s_parent, s_set, s_icount);
         const uint32_t word = __ballot_sync(FULL, won);
         if (lane < n_cta) dsmem_store(s_cnt + chunk, (uint32_t)lane, (uint32_t)__popc(word));
         cluster_barrier();
@@ -281,7 +307,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
             // UpdateTree (Alg. 4): each winner appends itself at its rank
             if (won) {
                 const int rank = (int)(before + __popc(word & ((1u << lane) - 1u)));
-                append_row<DYN, INTEG>(P, H, rank, kept, n_old, C.R, C.c, C.r);
+                append_row<DYN, INTEG>(P, H, rank, kept, n_old, C.R, C.c, C.r, owner, dsmem_generic(s_set, 0));
             }
         }
         cluster_barrier();
@@ -297,24 +323,24 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         pA = pI = pT = 0;
         for (int t = blockIdx.x; t < n_tiles; t += n_cta)
             prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_anc,
-                       s_warp, s_prefix, pA, pI, pT);
+                       s_warp, s_prefix, pA, pI, pT, t == 0);
         ++done;
         if (merged && lead_warp) {  // prune_tile ended with a CTA barrier
             if (leader) {
-                end_counters(P, H, false);
-                H->fused_iterations += 1;
-                fused_begin(P, H, n_iter - done, gthreads);
+                end_counters(P, HL, false);
+                HL->fused_iterations += 1;
+                fused_begin(P, HL, n_iter - done, gthreads);
             }
-            publish_iteration(H, &s_it, n_cta);
+            publish_iteration(HL, &s_it, n_cta);
         }
         cluster_barrier();
         if (!merged && lead_warp) {
             if (leader) {
-                end_counters(P, H, false);
-                H->fused_iterations += 1;
-                fused_begin(P, H, n_iter - done, gthreads);
+                end_counters(P, HL, false);
+                HL->fused_iterations += 1;
+                fused_begin(P, HL, n_iter - done, gthreads);
             }
-            publish_iteration(H, &s_it, n_cta);
+            publish_iteration(HL, &s_it, n_cta);
         }
     }
     if (leader && done > 0) H->t_last_ns = globaltimer_ns();  // the last iteration's end

@@ -210,6 +210,59 @@ __device__ __forceinline__ void roll_candidate(const DevParams& P, const GridVie
     C.ok = ok;
 }
 
+// roll_candidate() with early reject off, for one lane whose warp waits on
+// its longest rollout (the fused kernel): step k+1 is integrated before step
+// k's point is checked, so that the integration and the check, which both
+// depend only on step k's state, overlap instead of the check's verdict
+// gating the next integration.  The bounds test does not short-circuit the
+// obstacle walk (whose box count is then dropped for an out-of-bounds point).
+// One integration beyond the last step is thus discarded; the end state,
+// path length, verdict and the step and box-test counts equal
+// roll_candidate()'s (K >= 1).
+template <int DYN, int INTEG, bool SMEM>
+__device__ __forceinline__ void roll_candidate_ahead(const DevParams& P, const GridView& G, int lam, uint32_t iter,
+                                                     const int32_t* va, int64_t slot, Candidate<DYN, INTEG>& C,
+                                                     uint32_t& steps, uint32_t& tests) {
+    constexpr int n = Dims<DYN>::n;
+    C.R.start(P, va, lam, iter, slot);
+    C.R.integrate(P);  // step 1
+    bool ok = true;
+    for (int k = 1;; ++k) {
+        float xc[n];  // step k's point
+#pragma unroll
+        for (int d = 0; d < n; ++d) xc[d] = C.R.x[d];
+        const float len_c = C.R.len;
+        C.R.integrate(P);  // step k+1 (discarded after the last step)
+        ++steps;
+        const bool inb = bounds_ok(P, xc);
+        uint32_t t = 0;
+        const bool hit = hits_obstacle_in<SMEM>(P, G, xc[0], xc[1], xc[2], t);
+        tests += inb ? t : 0u;
+        if (!inb || hit) {
+            ok = false;
+            break;
+        }
+        if (k == C.R.K) {
+#pragma unroll
+            for (int d = 0; d < n; ++d) C.R.x[d] = xc[d];
+            C.R.len = len_c;
+            C.R.k = k;
+            break;
+        }
+    }
+    C.r = -1;
+    C.c = 0.0f;
+    C.key = KEY_INF;
+    if (ok) {
+        C.r = region_of<n>(P, C.R.x);
+        C.c = C.R.cost(P);
+        C.key = pack_key(C.c, (uint32_t)P.N + (uint32_t)slot);
+        if (C.key < __ldcg(&P.region_key[C.r]))
+            atomicMin((unsigned long long*)&P.region_key[C.r], (unsigned long long)C.key);
+    }
+    C.ok = ok;
+}
+
 // Lanes per rollout for n_slots rollouts on `threads` threads: the largest
 // power of two up to 32 with n_slots * g <= threads (1 when the slots fill
 // more than half of the threads).
@@ -401,11 +454,16 @@ __device__ __forceinline__ void scan_tile(const DevParams& P, kpx_device_header*
 // solution key.
 // ---------------------------------------------------------------------------
 // The row writes of winner w (rank in slot order) with rollout Rw, cost c,
-// region r: appended at n_old + w when w < kept, else the capacity rule
+// region r, whose key node is `old` (region_owner[r], read by the caller;
+// -1 for none): appended at n_old + w when w < kept, else the capacity rule
 // restores the region's key.
+// set_mirror: where the fused kernel keeps tile 0's staged set bytes (CTA
+// 0's shared memory), which receive the previous owner's new byte too; null
+// elsewhere.
 template <int DYN, int INTEG>
 __device__ __forceinline__ void append_row(const DevParams& P, kpx_device_header* H, int w, int kept, int n_old,
-                                           const LaneRollout<DYN, INTEG>& Rw, float c, int r) {
+                                           const LaneRollout<DYN, INTEG>& Rw, float c, int r, int old,
+                                           uint8_t* set_mirror = nullptr) {
     constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
     if (w < kept) {
         const int id = n_old + w;
@@ -423,8 +481,11 @@ __device__ __forceinline__ void append_row(const DevParams& P, kpx_device_header
         P.region_key[r] = k;
         // the previous owner of r loses its region (one winner per region,
         // so this thread is the only writer of that node's set byte)
-        const int old = P.region_owner[r];
-        if (old >= 0) P.set[old] = (uint8_t)(P.set[old] | SET_DOM);
+        if (old >= 0) {
+            const uint8_t nb = (uint8_t)(P.set[old] | SET_DOM);
+            P.set[old] = nb;
+            if (set_mirror && old < PRUNE_TILE) set_mirror[old] = nb;
+        }
         P.region_owner[r] = id;
         if (in_goal(P, Rw.x[0], Rw.x[1], Rw.x[2])) goal_key_min(H, k);
     } else {
@@ -449,7 +510,7 @@ __device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_hea
         H->err_info[1] = (uint32_t)slot;
         return;
     }
-    append_row<DYN, INTEG>(P, H, w, kept, n_old, Rw, c, r);
+    append_row<DYN, INTEG>(P, H, w, kept, n_old, Rw, c, r, P.region_owner[r]);
 }
 
 // Rules 1-3 of Alg. 3 (literal order, first match wins) for a node that is
@@ -482,16 +543,11 @@ __device__ __forceinline__ bool prune_rules_123(uint8_t sb, int i_max, int& ic, 
 // epoch and va_next are the iteration's (the header's epoch, and the V_A
 // buffer that va_sel does not select), read by the caller.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
-                                           int n_old, int total, uint32_t epoch, int32_t* va_next,
-                                           int32_t* s_parent, uint8_t* s_set,
-                                           uint8_t* s_icount, uint8_t* s_anc, uint32_t* s_warp,
-                                           uint32_t& s_prefix, int& cA, int& cI, int& cT) {
-    const int i_max = P.i_max;
-    const int tile0 = (int)tile * PRUNE_TILE;
-    // the tile's parent ids, set bytes and inactivity counts, read in one
-    // pass: ancestor walks that stay inside the tile read shared memory
-    // (parents precede children), and a node's own bytes come from here
+// The tile's parent ids, set bytes and inactivity counts below n_old, read in
+// one pass: ancestor walks that stay inside the tile read shared memory
+// (parents precede children), and a node's own bytes come from here.
+__device__ __forceinline__ void stage_tile(const DevParams& P, int tile0, int n_old, int32_t* s_parent,
+                                           uint8_t* s_set, uint8_t* s_icount) {
     for (int k = threadIdx.x; k < PRUNE_TILE; k += PRUNE_THREADS) {
         const int i = tile0 + k;
         const bool in = i < n_old;
@@ -499,6 +555,18 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
         s_set[k] = in ? P.set[i] : 0;
         s_icount[k] = in ? P.icount[i] : 0;
     }
+}
+
+// staged: the caller staged the tile already (the fused kernel stages tile 0
+// before the append phase, whose dominated marks it then receives directly)
+__device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
+                                           int n_old, int total, uint32_t epoch, int32_t* va_next,
+                                           int32_t* s_parent, uint8_t* s_set,
+                                           uint8_t* s_icount, uint8_t* s_anc, uint32_t* s_warp,
+                                           uint32_t& s_prefix, int& cA, int& cI, int& cT, bool staged = false) {
+    const int i_max = P.i_max;
+    const int tile0 = (int)tile * PRUNE_TILE;
+    if (!staged) stage_tile(P, tile0, n_old, s_parent, s_set, s_icount);
     __syncthreads();
     // rule 4 first, one node per thread at a stride: whether a strict
     // ancestor is dominated, for the nodes that rules 1-3 leave undecided.
