@@ -15,29 +15,29 @@ constexpr uint32_t LOOKBACK_POLL_LIMIT = 1u << 20;
 // ---------------------------------------------------------------------------
 // Block-wide exclusive scan of one value per thread.
 // ---------------------------------------------------------------------------
-template <int THREADS>
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t& total, uint32_t* s_warp) {
+template <int THREADS, typename T>
+__device__ __forceinline__ T block_exclusive_scan(T v, T& total, T* s_warp) {
     constexpr int NW = THREADS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t x = v;
+    T x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        const T y = __shfl_up_sync(FULL, x, o);
         if (lane >= o) x += y;
     }
     if (lane == 31) s_warp[warp] = x;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < NW ? s_warp[lane] : 0u;
+        T w = lane < NW ? s_warp[lane] : (T)0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, w, o);
+            const T y = __shfl_up_sync(FULL, w, o);
             if (lane >= o) w += y;
         }
         if (lane < NW) s_warp[lane] = w;
     }
     __syncthreads();
-    const uint32_t excl = x - v + (warp > 0 ? s_warp[warp - 1] : 0u);
+    const T excl = x - v + (warp > 0 ? s_warp[warp - 1] : (T)0);
     total = s_warp[NW - 1];
     __syncthreads();
     return excl;
@@ -558,30 +558,47 @@ __device__ __forceinline__ void stage_tile(const DevParams& P, int tile0, int n_
 }
 
 // staged: the caller staged the tile already (the fused kernel stages tile 0
-// before the append phase, whose dominated marks it then receives directly)
+// before the append phase, whose dominated marks it then receives directly).
+// One pass, one node per thread in each of PRUNE_PER_THREAD rounds (node
+// tile0 + round * PRUNE_THREADS + thread): rules 1-3, then rule 4's walk
+// for the nodes they leave undecided, so that a small tree's nodes spread
+// over the block's warps.  The compaction keeps id order: one block scan of
+// the rounds' active flags, packed as 16-bit fields (a round holds at most
+// PRUNE_THREADS nodes), gives each node its place after the earlier rounds.
 __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
                                            int n_old, int total, uint32_t epoch, int32_t* va_next,
-                                           int32_t* s_parent, uint8_t* s_set,
-                                           uint8_t* s_icount, uint8_t* s_anc, uint32_t* s_warp,
-                                           uint32_t& s_prefix, int& cA, int& cI, int& cT, bool staged = false) {
+                                           int32_t* s_parent, uint8_t* s_set, uint8_t* s_icount,
+                                           uint64_t* s_warp64, uint32_t& s_prefix, int& cA, int& cI, int& cT,
+                                           bool staged = false) {
+    static_assert(PRUNE_PER_THREAD <= 4 && PRUNE_THREADS < (1 << 16), "16-bit fields of a 64-bit scan");
     const int i_max = P.i_max;
     const int tile0 = (int)tile * PRUNE_TILE;
     if (!staged) stage_tile(P, tile0, n_old, s_parent, s_set, s_icount);
     __syncthreads();
-    // rule 4 first, one node per thread at a stride: whether a strict
-    // ancestor is dominated, for the nodes that rules 1-3 leave undecided.
-    // A small tree's nodes thus walk in parallel across the warps instead of
-    // one after another within the warp that owns them below.
+    uint64_t fields = 0;  // bit 16 q: this thread's node of round q stays in V_A
 #pragma unroll
     for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
         const int k = threadIdx.x + q * PRUNE_THREADS;
         const int i = tile0 + k;
-        bool anc = false;
-        if (i < n_old) {
-            const uint8_t sb = s_set[k];
-            int ic = s_icount[k], nst = sb & SET_MASK;
-            anc = (sb & SET_ANC) != 0;
-            if (nst != SET_T && !prune_rules_123(sb, i_max, ic, nst) && !anc) {
+        if (i >= total) continue;
+        if (i >= n_old) {  // appended this iteration: in V_A
+            fields |= 1ull << (16 * q);
+            ++cA;
+            continue;
+        }
+        const uint8_t sb = s_set[k];
+        if ((sb & SET_MASK) == SET_T) {  // V_T is permanent
+            ++cT;
+            continue;
+        }
+        int ic = s_icount[k];
+        const int ic0 = ic;
+        int nst = sb & SET_MASK;
+        bool anc = (sb & SET_ANC) != 0;
+        if (!prune_rules_123(sb, i_max, ic, nst)) {
+            // rule 4: whether a strict ancestor is dominated (the ANC flag
+            // memoises a positive answer; it is monotone)
+            if (!anc) {
                 int p = s_parent[k];
                 while (p >= tile0) {  // inside the tile: shared memory (a stale set byte
                     // only lacks a monotone flag, which the walk re-derives)
@@ -597,36 +614,13 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
                     if (sp & (SET_DOM | SET_ANC)) anc = true;
                 }
             }
+            if (anc) nst = SET_I;
         }
-        s_anc[k] = anc ? 1 : 0;
-    }
-    __syncthreads();
-    const int base = tile0 + threadIdx.x * PRUNE_PER_THREAD;
-    uint32_t amask = 0;
-#pragma unroll
-    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
-        const int i = base + q;
-        if (i >= total) break;
-        if (i >= n_old) {  // appended this iteration: in V_A
-            amask |= 1u << q;
-            ++cA;
-            continue;
-        }
-        const uint8_t sb = s_set[i - tile0];
-        if ((sb & SET_MASK) == SET_T) {  // V_T is permanent
-            ++cT;
-            continue;
-        }
-        int ic = s_icount[i - tile0];
-        const int ic0 = ic;
-        int nst = sb & SET_MASK;
-        const bool anc = s_anc[i - tile0] != 0;
-        if (!prune_rules_123(sb, i_max, ic, nst) && anc) nst = SET_I;  // rule 4
         const uint8_t nb = (uint8_t)(nst | (anc ? SET_ANC : 0) | (sb & SET_DOM));
         if (nb != sb) P.set[i] = nb;
         if (ic != ic0) P.icount[i] = (uint8_t)ic;
         if (nst == SET_A) {
-            amask |= 1u << q;
+            fields |= 1ull << (16 * q);
             ++cA;
         } else if (nst == SET_I) {
             ++cI;
@@ -634,24 +628,28 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
             ++cT;
         }
     }
-    uint32_t agg;
-    const uint32_t excl = block_exclusive_scan<PRUNE_THREADS>((uint32_t)__popc(amask), agg, s_warp);
+    uint64_t tot;
+    const uint64_t excl = block_exclusive_scan<PRUNE_THREADS>(fields, tot, s_warp64);
+    uint32_t agg = 0;
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) agg += (uint32_t)(tot >> (16 * q)) & 0xFFFFu;
     if (threadIdx.x == 0) {
         s_prefix = lookback(P.prune_tiles, tile, agg, epoch, H);
         if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
     }
     __syncthreads();
-    uint32_t pos = s_prefix + excl;
+    uint32_t before = s_prefix;  // V_A entries of the earlier tiles, then of the earlier rounds
 #pragma unroll
     for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
-        if (amask & (1u << q)) {
+        if (fields & (1ull << (16 * q))) {
             // at most one active node per region, so pos < min(N, R) = va_cap
+            const uint32_t pos = before + ((uint32_t)(excl >> (16 * q)) & 0xFFFFu);
             if (pos < (uint32_t)P.va_cap)
-                va_next[pos] = base + q;
+                va_next[pos] = tile0 + (int)threadIdx.x + q * PRUNE_THREADS;
             else
                 set_status(H, KPX_E_INTERNAL);
-            ++pos;
         }
+        before += (uint32_t)(tot >> (16 * q)) & 0xFFFFu;
     }
     __syncthreads();
 }
