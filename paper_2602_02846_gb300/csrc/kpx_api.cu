@@ -34,6 +34,7 @@ struct kpx_planner {
     int32_t count_value = 1;               // the count node's current value
     float grid_scale = 1.0f;     // obstacle-grid cell edge / mean box extent
     std::vector<float> host_obs; // the boxes (lo xyz, hi xyz), to rebuild the grid
+    std::vector<float4> upload;  // source of kpx_create's obstacle copy, alive until destroy
 };
 
 // Many problems iterated together (one launch per phase for all of them).
@@ -315,8 +316,12 @@ cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s) {
 
 // Iterations of the phase kernels per trip of the graph's loop: a trip
 // costs a few microseconds on top of its kernels, so it carries several
-// iterations (those past graph_pending are no-ops).
+// iterations (those past graph_pending are no-ops).  Behind the fused
+// kernel the loop runs only once a problem has outgrown it, where an
+// iteration costs tens of microseconds or more; there a shorter body keeps
+// the graph, which every new planner builds, small.
 constexpr int kLoopIterations = 8;
+constexpr int kLoopIterationsFused = 2;
 
 // One iteration of the phase kernels in the body of the graph's loop: it
 // runs only while iterations are owed, and its last kernel counts it off
@@ -348,8 +353,9 @@ cudaMemsetParams count_params(const kpx_planner* p, int n) {
 //   count node (memset: graph_pending = n)
 //   -> the fused kernel (kpx_fused.cu), when the device can run its cluster:
 //      iterations while the problem is small; the rest stay in graph_pending
-//   -> WHILE node: up to kLoopIterations iterations of the phase kernels
-//      per trip, until graph_pending is 0 (each iteration's last kernel
+//   -> WHILE node: up to kLoopIterations (kLoopIterationsFused behind the
+//      fused kernel) iterations of the phase kernels per trip, until
+//      graph_pending is 0 (each iteration's last kernel
 //      counts it off).
 // With the fused kernel the loop's handle starts at 0 and the fused kernel
 // sets it; without it the handle starts at 1 (n >= 1).  Only the count
@@ -400,8 +406,9 @@ cudaError_t build_loop_graph(kpx_planner* p, bool fused) {
         e = cudaStreamBeginCaptureToGraph(p->capture_stream, body, nullptr, nullptr, 0,
                                           cudaStreamCaptureModeRelaxed);
         if (e == cudaSuccess) {
-            for (int u = 0; u < kLoopIterations && le == cudaSuccess; ++u)
-                le = enqueue_loop_iteration(p->P, h, u == kLoopIterations - 1, p->capture_stream);
+            const int unroll = fused ? kLoopIterationsFused : kLoopIterations;
+            for (int u = 0; u < unroll && le == cudaSuccess; ++u)
+                le = enqueue_loop_iteration(p->P, h, u == unroll - 1, p->capture_stream);
             cudaGraph_t out = nullptr;
             e = cudaStreamEndCapture(p->capture_stream, &out);
             if (le != cudaSuccess) e = le;
@@ -427,6 +434,32 @@ void drop_graphs(kpx_planner* p) {
     p->count_node = nullptr;
 }
 
+// The stream that planners' graphs are captured on: one per host thread and
+// device, made on first use and kept (a capture leaves it idle), so that a
+// planner neither creates nor destroys one.  nullptr when none can be made.
+struct CaptureStreams {
+    static constexpr int kDevices = 64;
+    cudaStream_t s[kDevices] = {};
+    ~CaptureStreams() {
+        for (cudaStream_t x : s)
+            if (x) cudaStreamDestroy(x);  // fails harmlessly once the context is gone
+    }
+};
+
+cudaStream_t capture_stream_here() {
+    thread_local CaptureStreams streams;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= CaptureStreams::kDevices) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (!streams.s[dev] && cudaStreamCreateWithFlags(&streams.s[dev], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        streams.s[dev] = nullptr;
+    }
+    return streams.s[dev];
+}
+
 // Decides once how kpx_iterate launches: a graph that starts with the fused
 // kernel when the device can run its cluster (and KPX_FLAG_NO_FUSED is
 // clear), else a graph of the phase kernels alone; plain launches (same
@@ -437,11 +470,8 @@ void ensure_graphs(kpx_planner* p) {
     prepare_launches(p->P);
     p->graph_fused = !(p->P.flags & KPX_FLAG_NO_FUSED) && fused_cluster_size(p->P) > 0;
     cudaGetLastError();
-    if (!p->capture_stream && cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        p->capture_stream = nullptr;
-        return;
-    }
+    p->capture_stream = capture_stream_here();
+    if (!p->capture_stream) return;
     p->graph_state = 1;
 }
 
@@ -635,9 +665,9 @@ kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kp
         delete p;
         return st;
     }
-    std::vector<float4> ob;
-    cudaError_t e = upload_and_init(p, obs, ob);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);  // the host copy buffer is local
+    // enqueued only: the copy's source lives as long as the planner, and
+    // every later call runs on the same stream
+    cudaError_t e = upload_and_init(p, obs, p->upload);
     if (e != cudaSuccess) {
         g_create_error = std::string("kpx_create: ") + cudaGetErrorString(e);
         delete p;
@@ -818,7 +848,6 @@ kpx_status kpx_destroy(kpx_planner* p) {
     if (!p) return KPX_OK;
     cudaError_t e = cudaStreamSynchronize(p->stream);
     drop_graphs(p);
-    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     delete p;
     return e == cudaSuccess ? KPX_OK : KPX_E_CUDA;
 }
