@@ -154,10 +154,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     __shared__ uint64_t s_warp64[PRUNE_THREADS / 32];
     __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // winners per chunk (every CTA's copy)
     // While the launch runs, the header lives in CTA 0's shared memory: the
-    // leader's bookkeeping and every CTA's reads and counter atomics reach it
-    // over distributed shared memory instead of L2 (each cluster barrier's
-    // acquire would otherwise send every header read back to L2).  It is
-    // copied in here and written back before the kernel exits.
+    // leader's bookkeeping stays on the SM, and the few header updates of
+    // other CTAs (a status, the goal key) reach it over distributed shared
+    // memory instead of L2 (each cluster barrier's acquire would otherwise
+    // send header reads back to L2).  What every warp needs in each iteration
+    // comes from its own CTA's copy of the parameters (s_it), and the
+    // counters stay in registers until the launch ends.  The header is copied
+    // in here and written back before the kernel exits.
     __shared__ __align__(16) kpx_device_header s_hdr;
     __shared__ __align__(16) IterParams s_it;  // this CTA's copy of the iteration's parameters
     constexpr int HDR_WORDS = (int)(sizeof(kpx_device_header) / sizeof(uint32_t));
