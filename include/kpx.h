@@ -175,9 +175,13 @@ size_t kpx_workspace_size(const kpx_dynamics* dyn, const kpx_config* cfg, int32_
  * must lie in X_valid.  device_workspace: caller-owned device memory of at
  * least kpx_workspace_size() bytes, 256-byte aligned.  cuda_stream: the
  * stream all work of this planner is enqueued on.  On success *out receives
- * the planner.  Errors: KPX_E_INVALID (inconsistent or non-finite inputs,
- * start not valid, sizes out of range), KPX_E_NOMEM (workspace too small),
- * KPX_E_CUDA. */
+ * the planner; the device work that sets it up (obstacle upload, reset,
+ * obstacle grid) is enqueued on the stream, not waited for, and a fault in
+ * it is reported by the next call that waits for the stream.  The host
+ * arrays may be reused as soon as the call returns.  Errors: KPX_E_INVALID
+ * (inconsistent or non-finite inputs, start not valid, sizes out of range),
+ * KPX_E_NOMEM (workspace too small), KPX_E_CUDA (a launch or copy that
+ * could not be enqueued). */
 kpx_status kpx_create(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
                       const float* start, const kpx_goal* goal, const kpx_cost* cost,
                       const kpx_config* cfg, void* device_workspace, size_t workspace_bytes,
