@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_b_prune(BatchParams BP) {
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint8_t s_icount[PRUNE_TILE];
-    __shared__ uint64_t s_warp64[PRUNE_THREADS / 32];
+    __shared__ uint32_t s_counts[PRUNE_ROUND_WARPS];
     const int64_t total_tiles = BP.prune_prefix[BP.B];
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&BP.bh->prune_ticket, 1u);
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_b_prune(BatchParams BP) {
         const int n_tiles = (int)(BP.prune_prefix[p + 1] - BP.prune_prefix[p]);
         int cA = 0, cI = 0, cT = 0;
         prune_tile(P, H, (uint32_t)(t - BP.prune_prefix[p]), n_tiles, n_old, n_old + H->n_kept, (uint32_t)H->epoch,
-                   va_following(P, H), s_parent, s_set, s_icount, s_warp64, s_prefix, cA, cI, cT);
+                   va_following(P, H), s_parent, s_set, s_icount, s_counts, s_prefix, cA, cI, cT);
         flush_prune_counters(H, cA, cI, cT);
     }
 }

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint8_t s_icount[PRUNE_TILE];
-    __shared__ uint64_t s_warp64[PRUNE_THREADS / 32];
+    __shared__ uint32_t s_counts[PRUNE_ROUND_WARPS];
     __shared__ uint32_t s_cnt[FUSED_MAX_CLUSTER * (FUSED_THREADS / 32)];  // winners per chunk (every CTA's copy)
     // While the launch runs, the header lives in CTA 0's shared memory: the
     // leader's bookkeeping stays on the SM, and the few header updates of
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 1)
         // so only the launch's last iteration reaches it, at the end
         pA = pI = pT = 0;
         for (int t = blockIdx.x; t < n_tiles; t += n_cta)
-            prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_warp64,
+            prune_tile(P, H, (uint32_t)t, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_counts,
                        s_prefix, pA, pI, pT, t == 0);
         ++done;
         if (merged && lead_warp) {  // prune_tile ended with a CTA barrier

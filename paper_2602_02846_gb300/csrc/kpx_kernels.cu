@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
     __shared__ uint8_t s_icount[PRUNE_TILE];
-    __shared__ uint64_t s_warp64[PRUNE_THREADS / 32];
+    __shared__ uint32_t s_counts[PRUNE_ROUND_WARPS];
     kpx_device_header* H = P.hdr;
     if (!H->active) return;
     const int n_old = H->n_nodes;
@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
         const uint32_t tile = s_tile;
         __syncthreads();
         if ((int)tile >= n_tiles) break;
-        prune_tile(P, H, tile, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_warp64, s_prefix, cA,
-                   cI, cT);
+        prune_tile(P, H, tile, n_tiles, n_old, total, epoch, va_next, s_parent, s_set, s_icount, s_counts, s_prefix,
+                   cA, cI, cT);
     }
     flush_prune_counters(H, cA, cI, cT);
 }

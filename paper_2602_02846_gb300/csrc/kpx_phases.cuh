@@ -562,27 +562,31 @@ __device__ __forceinline__ void stage_tile(const DevParams& P, int tile0, int n_
 // One pass, one node per thread in each of PRUNE_PER_THREAD rounds (node
 // tile0 + round * PRUNE_THREADS + thread): rules 1-3, then rule 4's walk
 // for the nodes they leave undecided, so that a small tree's nodes spread
-// over the block's warps.  The compaction keeps id order: one block scan of
-// the rounds' active flags, packed as 16-bit fields (a round holds at most
-// PRUNE_THREADS nodes), gives each node its place after the earlier rounds.
+// over the block's warps.  The compaction keeps id order, which runs round
+// by round, then warp by warp, then lane by lane: each warp ballots its
+// active nodes of each round, and one warp scans the (round, warp) counts,
+// PRUNE_ROUND_WARPS of them, in that order (s_counts) and takes the tile's
+// look-back.
+constexpr int PRUNE_ROUND_WARPS = PRUNE_PER_THREAD * (PRUNE_THREADS / 32);
+static_assert(PRUNE_ROUND_WARPS <= 32, "one warp scans the (round, warp) counts");
+
 __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int n_tiles,
                                            int n_old, int total, uint32_t epoch, int32_t* va_next,
                                            int32_t* s_parent, uint8_t* s_set, uint8_t* s_icount,
-                                           uint64_t* s_warp64, uint32_t& s_prefix, int& cA, int& cI, int& cT,
+                                           uint32_t* s_counts, uint32_t& s_prefix, int& cA, int& cI, int& cT,
                                            bool staged = false) {
-    static_assert(PRUNE_PER_THREAD <= 4 && PRUNE_THREADS < (1 << 16), "16-bit fields of a 64-bit scan");
     const int i_max = P.i_max;
     const int tile0 = (int)tile * PRUNE_TILE;
     if (!staged) stage_tile(P, tile0, n_old, s_parent, s_set, s_icount);
     __syncthreads();
-    uint64_t fields = 0;  // bit 16 q: this thread's node of round q stays in V_A
+    uint32_t fields = 0;  // bit q: this thread's node of round q stays in V_A
 #pragma unroll
     for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
         const int k = threadIdx.x + q * PRUNE_THREADS;
         const int i = tile0 + k;
         if (i >= total) continue;
         if (i >= n_old) {  // appended this iteration: in V_A
-            fields |= 1ull << (16 * q);
+            fields |= 1u << q;
             ++cA;
             continue;
         }
@@ -620,7 +624,7 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
         if (nb != sb) P.set[i] = nb;
         if (ic != ic0) P.icount[i] = (uint8_t)ic;
         if (nst == SET_A) {
-            fields |= 1ull << (16 * q);
+            fields |= 1u << q;
             ++cA;
         } else if (nst == SET_I) {
             ++cI;
@@ -628,28 +632,45 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
             ++cT;
         }
     }
-    uint64_t tot;
-    const uint64_t excl = block_exclusive_scan<PRUNE_THREADS>(fields, tot, s_warp64);
-    uint32_t agg = 0;
-#pragma unroll
-    for (int q = 0; q < PRUNE_PER_THREAD; ++q) agg += (uint32_t)(tot >> (16 * q)) & 0xFFFFu;
-    if (threadIdx.x == 0) {
-        s_prefix = lookback(P.prune_tiles, tile, agg, epoch, H);
-        if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
-    }
-    __syncthreads();
-    uint32_t before = s_prefix;  // V_A entries of the earlier tiles, then of the earlier rounds
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t ball[PRUNE_PER_THREAD];
 #pragma unroll
     for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
-        if (fields & (1ull << (16 * q))) {
+        ball[q] = __ballot_sync(FULL, (fields >> q) & 1u);
+        if (lane == 0) s_counts[q * (PRUNE_THREADS / 32) + warp] = (uint32_t)__popc(ball[q]);
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // exclusive prefix of the (round, warp) counts, then the tile's
+        // place among the tiles (look-back)
+        const uint32_t v = lane < PRUNE_ROUND_WARPS ? s_counts[lane] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, x, o);
+            if (lane >= o) x += y;
+        }
+        const uint32_t agg = __shfl_sync(FULL, x, 31);
+        __syncwarp();
+        if (lane < PRUNE_ROUND_WARPS) s_counts[lane] = x - v;
+        if (lane == 0) {
+            s_prefix = lookback(P.prune_tiles, tile, agg, epoch, H);
+            if ((int)tile == n_tiles - 1) H->count_A_next = (int32_t)(s_prefix + agg);
+        }
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;  // lanes below this one
+#pragma unroll
+    for (int q = 0; q < PRUNE_PER_THREAD; ++q) {
+        if ((fields >> q) & 1u) {
             // at most one active node per region, so pos < min(N, R) = va_cap
-            const uint32_t pos = before + ((uint32_t)(excl >> (16 * q)) & 0xFFFFu);
+            const uint32_t pos =
+                s_prefix + s_counts[q * (PRUNE_THREADS / 32) + warp] + (uint32_t)__popc(ball[q] & lt);
             if (pos < (uint32_t)P.va_cap)
                 va_next[pos] = tile0 + (int)threadIdx.x + q * PRUNE_THREADS;
             else
                 set_status(H, KPX_E_INTERNAL);
         }
-        before += (uint32_t)(tot >> (16 * q)) & 0xFFFFu;
     }
     __syncthreads();
 }
