@@ -55,7 +55,7 @@ SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
 FUSED_DRAM_BYTES = {
-    "dubins6_forest300": 178176,     # profiles/k_fused_dubins6_forest300.md (one 200-iteration launch)
+    "dubins6_forest300": 178432,     # profiles/k_fused_dubins6_forest300.md (one 200-iteration launch)
 }
 PROPAGATE_DRAM_BYTES = {
     "dubins6_forest300": 34816,      # profiles/k_propagate_dubins6_forest300.md (phase-kernel path)
