@@ -731,8 +731,14 @@ void kpo_destroy(kpo_planner* pl) {
  * re-rolled in FP64 from its stored start state with its stored control and
  * step count (state mismatch, clearance and cost are accumulated), and the
  * whole control sequence is re-rolled open loop from the start state.
- * Returns 1 when every re-rolled point has clearance >= -1e-4 and the final
- * stored state is within goal_r + 1e-4 of the goal centre.
+ * A solution of Sec. III follows the dynamics, stays in X_valid and ends in
+ * X_goal, so the verdict is 1 exactly when
+ *   - every re-rolled point (and the start) has clearance >= -1e-4,
+ *   - the final stored state is within goal_r + 1e-4 of the goal centre, and
+ *   - every segment's re-rolled end state matches the next stored state to
+ *     1e-4 relative (|a - b| / max(1, |b|) per component).
+ * The open-loop error is reported only: FP32 and FP64 rollouts of an
+ * unstable system drift apart over many segments without either being wrong.
  * ---------------------------------------------------------------------- */
 int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, const float* controls,
                        const int32_t* steps, double* max_seg_err, double* min_clearance,
@@ -800,7 +806,7 @@ int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, 
     *goal_slack = P->goal_r - sqrt(d2);
     *cost = total;
     *openloop_err = olerr;
-    return (clear >= -1e-4 && *goal_slack >= -1e-4) ? 1 : 0;
+    return (clear >= -1e-4 && *goal_slack >= -1e-4 && worst <= 1e-4) ? 1 : 0;
 }
 
 /* ------------------------------------------------------------------------

@@ -160,7 +160,11 @@ int32_t kpo_best_trajectory(const kpo_planner* pl, int32_t cap, double* states, 
                             int32_t* steps, int32_t* out_len, double* out_cost);
 void kpo_destroy(kpo_planner* pl);
 
-/* FP64 re-validation of a returned trajectory (states[len+1][n], controls[len][m]). */
+/* FP64 re-validation of a returned trajectory (states[len+1][n], controls[len][m]):
+ * 1 when the start and every re-rolled point have clearance >= -1e-4, the
+ * last stored state lies within goal_r + 1e-4 of the goal centre, and each
+ * segment re-rolled from its stored start reaches the next stored state to
+ * 1e-4 relative (Sec. III: dynamics, X_valid, X_goal). */
 int32_t kpo_revalidate(const kpo_problem* P, int32_t len, const double* states, const float* controls,
                        const int32_t* steps, double* max_seg_err, double* min_clearance,
                        double* goal_slack, double* cost, double* openloop_err);

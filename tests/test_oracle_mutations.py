@@ -16,6 +16,7 @@ from tests import test_oracle_dynamics as dyn
 from tests import test_oracle_geometry as geo
 from tests import test_oracle_refine as ref
 from tests import test_oracle_remap as rmp
+from tests import test_oracle_revalidate as rv
 from tests import test_oracle_sampling as smp
 from tests import test_oracle_steps as stp
 
@@ -107,6 +108,36 @@ MUTATIONS = [
     ("softplus_scale", "return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t))) / beta;",
      "return (t > 0.0 ? t + log1p(exp(-t)) : log1p(exp(t)));", [ref.test_penalty_value_by_hand]),
     ("validate_no_check", "if (!kpo_point_valid(P, x)) ok = 0;", "(void)0;", [ref.test_validate_controls]),
+    # FP64 re-validation of a returned trajectory and the returned trajectory itself
+    ("revalidate_always_ok", "return (clear >= -1e-4 && *goal_slack >= -1e-4 && worst <= 1e-4) ? 1 : 0;",
+     "return 1;", [rv.test_revalidate_rejects_one_point_in_thin_box, rv.test_revalidate_rejects_missing_the_goal]),
+    ("revalidate_no_step_clearance",
+     "for (int k = 1; k <= kdone; ++k) clear = fmin(clear, kpo_point_clearance(P, traj + (int64_t)k * n));",
+     "(void)kdone;", [rv.test_revalidate_rejects_one_point_in_thin_box]),
+    ("revalidate_no_goal_test", "clear >= -1e-4 && *goal_slack >= -1e-4 && worst <= 1e-4",
+     "clear >= -1e-4 && worst <= 1e-4", [rv.test_revalidate_rejects_missing_the_goal]),
+    ("revalidate_goal_slack_sign", "*goal_slack = P->goal_r - sqrt(d2);", "*goal_slack = sqrt(d2) - P->goal_r;",
+     [rv.test_revalidate_accepts_valid_flight, rv.test_revalidate_rejects_missing_the_goal]),
+    ("revalidate_no_consistency", "clear >= -1e-4 && *goal_slack >= -1e-4 && worst <= 1e-4",
+     "clear >= -1e-4 && *goal_slack >= -1e-4", [rv.test_revalidate_rejects_inconsistent_stored_state]),
+    ("revalidate_start_unchecked", "clear = fmin(clear, kpo_point_clearance(P, states));", "(void)0;",
+     [rv.test_revalidate_rejects_start_in_box]),
+    ("revalidate_cost_last_only", "total += ec;", "total = ec;", [rv.test_revalidate_accepts_valid_flight]),
+    ("revalidate_goal_on_previous_state", "const double* xl = states + (int64_t)len * n;",
+     "const double* xl = states + (int64_t)(len - 1) * n;", [rv.test_revalidate_rejects_missing_the_goal]),
+    ("revalidate_tolerance_loose", "return (clear >= -1e-4 && *goal_slack >= -1e-4 && worst <= 1e-4)",
+     "return (clear >= -1e-2 && *goal_slack >= -1e-2 && worst <= 1e-2)",
+     [rv.test_revalidate_rejects_one_point_in_thin_box, rv.test_revalidate_rejects_missing_the_goal,
+      rv.test_revalidate_rejects_inconsistent_stored_state]),
+    ("best_traj_steps_of_parent", "steps[k - 1] = v->K[p];", "steps[k - 1] = v->K[v->parent[p]];",
+     [rv.test_best_trajectory_is_the_parent_walk]),
+    ("best_traj_cost_of_parent", "*out_cost = v->cost[id];", "*out_cost = v->cost[v->parent[id]];",
+     [rv.test_best_trajectory_is_the_parent_walk]),
+    ("best_traj_skips_goal_node", "int32_t id = (int32_t)(v->goal_key & 0xFFFFFFFFu);",
+     "int32_t id = v->parent[(int32_t)(v->goal_key & 0xFFFFFFFFu)];", [rv.test_best_trajectory_is_the_parent_walk]),
+    ("best_traj_controls_shift", "controls[(int64_t)(k - 1) * v->m + d] = v->u[(int64_t)p * v->m + d];",
+     "controls[(int64_t)(k - 1) * v->m + d] = v->u[(int64_t)v->parent[p] * v->m + d];",
+     [rv.test_best_trajectory_is_the_parent_walk]),
     # region remap (adaptive delta)
     ("remap_terminal_holds_region", "if (set[i] != KPO_SET_T && key[i] < region_key[region[i]])",
      "if (key[i] < region_key[region[i]])", [rmp.test_remap_hand_example]),
