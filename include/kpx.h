@@ -343,31 +343,36 @@ const char* kpx_batch_last_error(const kpx_batch* b);
 /* One complete planning run that allocates nothing (the paper has no
  * counterpart: this is a deployment convenience of this library).
  *
- * Some callers cannot call cudaMalloc: code that runs while its stream is
- * being captured into a CUDA graph (allocation is not allowed during
- * capture), real-time control loops that must never block on an allocator or
- * meet an out-of-memory error mid-plan, and plugins whose host application
- * already owns the device's memory pool.  This entry point plans with device
+ * Some callers cannot call cudaMalloc: real-time control loops that must
+ * never block on an allocator or meet an out-of-memory error mid-plan, and
+ * plugins whose host application already owns the device's memory pool and
+ * hands out no device memory of its own.  This entry point plans with device
  * memory reserved inside the library instead: a static device array of
  * KPX_STATIC_SCRATCH_BYTES that every GPU loading the library holds until the
  * process exits.  It runs kpx_create + kpx_iterate(n_iters) +
- * kpx_best_trajectory in one call, synchronously on cuda_stream, with the
- * same arguments and outputs as those calls (host inputs; host outputs of
- * capacity segments).  It calls no cudaMalloc, cudaFree or other allocating
- * routine.
+ * kpx_best_trajectory in one call, with the same arguments and outputs as
+ * those calls (host inputs; host outputs of capacity segments), and the same
+ * validation as kpx_create.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * The call enqueues its work on cuda_stream, copies the result to the host
+ * and synchronises cuda_stream before it returns.  So it must not be called
+ * while cuda_stream is being captured into a CUDA graph (nor, in global
+ * capture mode, while any stream is): it then returns KPX_E_INVALID without
+ * enqueuing anything.
  *
  * Limits and caveats:
  *   - problems whose kpx_workspace_size() exceeds KPX_STATIC_SCRATCH_BYTES
  *     are rejected with KPX_E_NOMEM (message in kpx_last_error(NULL));
  *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture;
+ *     (cudaGetSymbolAddress) with that device current;
  *   - every call, from any thread or stream, uses the same array, and the
  *     array keeps the last call's contents (each call re-initialises what it
  *     reads); calls that overlap on the GPU race and corrupt each other.
  * Returns KPX_OK, KPX_NO_SOLUTION (*out_len = 0), KPX_E_INVALID (bad input,
- * or capacity too small with *out_len = required segments), KPX_E_NOMEM,
- * KPX_E_CUDA, or a device status (KPX_E_TIMEOUT / KPX_E_INTERNAL). */
+ * a capturing stream, or capacity too small with *out_len = required
+ * segments), KPX_E_NOMEM, KPX_E_CUDA, or a device status (KPX_E_TIMEOUT /
+ * KPX_E_INTERNAL). */
 #define KPX_STATIC_SCRATCH_BYTES (16u << 20)
 kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
                            const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <string>
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -506,11 +507,12 @@ kpx_status run_phase(kpx_planner* p, int phase, const kpx_debug_records* rec) {
     return KPX_OK;
 }
 
-// Validates one problem and lays it out in `device_workspace` (no device
-// work): fills p->P, p->L, p->ws.  On failure returns the status and a message.
-kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
-                        const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
-                        void* device_workspace, size_t workspace_bytes, kpx_planner* p, std::string& err) {
+// Checks one problem's arguments and computes its workspace layout (no device
+// work; nothing is allocated unless a message is returned).  kpx_create, the
+// batch calls and kpx_plan_static all go through it.
+kpx_status validate_problem(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                            const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                            Layout& L, std::string& err) {
     auto reject = [&](kpx_status st, const std::string& msg) {
         err = msg;
         return st;
@@ -520,9 +522,6 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     std::string msg = check_config(dyn, cfg, n_obs);
     if (!msg.empty()) return reject(KPX_E_INVALID, msg);
     if (n_obs > 0 && !obs->aabb) return reject(KPX_E_INVALID, "obstacle array is null");
-    if (!device_workspace) return reject(KPX_E_INVALID, "device workspace is null");
-    if (reinterpret_cast<uintptr_t>(device_workspace) % 256 != 0)
-        return reject(KPX_E_INVALID, "device workspace must be 256-byte aligned");
     for (int a = 0; a < 3; ++a)
         if (!finite(ws->lo[a]) || !finite(ws->hi[a]) || !(ws->hi[a] >= ws->lo[a]))
             return reject(KPX_E_INVALID, "workspace box needs finite lo <= hi");
@@ -541,14 +540,22 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     const int n = kStateDim[dyn->kind];
     for (int i = 0; i < n; ++i)
         if (!finite(start[i])) return reject(KPX_E_INVALID, "start state must be finite");
-
-    Layout L = make_layout(dyn, cfg, n_obs);
-    if (workspace_bytes < L.total) return reject(KPX_E_NOMEM, "device workspace smaller than kpx_workspace_size()");
+    L = make_layout(dyn, cfg, n_obs);
     if ((uint64_t)cfg->tree_cap + (uint64_t)L.slot_cap >= 0xFFFFFFFFull)
         return reject(KPX_E_INVALID, "tree_cap + candidate slots must stay below 2^32");
+    return KPX_OK;
+}
+
+// Fills the parameter block of a validated problem laid out by L in the
+// device memory at p->ws: problem fields, planner fields, device pointers and
+// the obstacle grid (cell edge = grid_scale x the mean box extent), then
+// checks that the start lies in X_valid.
+kpx_status fill_problem(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                        const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                        const Layout& L, float grid_scale, kpx_planner* p, std::string& err) {
+    const int32_t n_obs = obs->count;
+    const int n = kStateDim[dyn->kind];
     p->L = L;
-    p->ws = reinterpret_cast<char*>(device_workspace);
-    p->ws_bytes = workspace_bytes;
     DevParams& P = p->P;
     memset(&P, 0, sizeof(P));
     fill_dynamics(P, dyn);
@@ -576,9 +583,39 @@ kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const 
     P.n_win_tiles = L.n_win_tiles;
     P.n_prune_tiles = L.n_prune_tiles;
     bind_pointers(p);
-    choose_grid(P, obs->aabb, n_obs, p->grid_scale);
-    p->host_obs.assign(obs->aabb, obs->aabb + 6 * (size_t)n_obs);
-    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) return reject(KPX_E_INVALID, "start state is not in X_valid");
+    choose_grid(P, obs->aabb, n_obs, grid_scale);
+    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) {
+        err = "start state is not in X_valid";
+        return KPX_E_INVALID;
+    }
+    return KPX_OK;
+}
+
+// Validates one problem and lays it out in `device_workspace` (no device
+// work): fills p->P, p->L, p->ws.  On failure returns the status and a message.
+kpx_status setup_member(const kpx_dynamics* dyn, const kpx_workspace* ws, const kpx_obstacles* obs,
+                        const float* start, const kpx_goal* goal, const kpx_cost* cost, const kpx_config* cfg,
+                        void* device_workspace, size_t workspace_bytes, kpx_planner* p, std::string& err) {
+    Layout L;
+    kpx_status st = validate_problem(dyn, ws, obs, start, goal, cost, cfg, L, err);
+    if (st != KPX_OK) return st;
+    if (!device_workspace) {
+        err = "device workspace is null";
+        return KPX_E_INVALID;
+    }
+    if (reinterpret_cast<uintptr_t>(device_workspace) % 256 != 0) {
+        err = "device workspace must be 256-byte aligned";
+        return KPX_E_INVALID;
+    }
+    if (workspace_bytes < L.total) {
+        err = "device workspace smaller than kpx_workspace_size()";
+        return KPX_E_NOMEM;
+    }
+    p->ws = reinterpret_cast<char*>(device_workspace);
+    p->ws_bytes = workspace_bytes;
+    st = fill_problem(dyn, ws, obs, start, goal, cost, cfg, L, p->grid_scale, p, err);
+    if (st != KPX_OK) return st;
+    p->host_obs.assign(obs->aabb, obs->aabb + 6 * (size_t)obs->count);
     return KPX_OK;
 }
 
@@ -1233,15 +1270,15 @@ kpx_status kpx_restore(kpx_planner* p, const void* src) {
 // ===========================================================================
 // kpx_plan_static: one planning run without any allocation.
 //
-// For callers that may not allocate device memory: code running while a
-// stream is being captured into a CUDA graph (allocation calls are not
-// allowed during capture), real-time control loops that must never wait on
-// an allocator or see an out-of-memory error mid-flight, and plugins whose
-// host application owns the whole device memory pool.  Their device memory
-// is this file-scope array, reserved when the library is loaded and held by
-// every GPU that loads it until the process exits.  This path deliberately
-// duplicates the parameter set-up of kpx_create instead of sharing it, so
-// that the allocating path above stays exactly as it is.
+// For callers that may not allocate device memory: real-time control loops
+// that must never wait on an allocator or see an out-of-memory error
+// mid-flight, and plugins whose host application owns the whole device
+// memory pool.  Their device memory is this file-scope array, reserved when
+// the library is loaded and held by every GPU that loads it until the
+// process exits.  The call synchronises its stream, so it refuses to run
+// while that stream is being captured into a CUDA graph.  Validation and the
+// parameter block are kpx_create's (validate_problem, fill_problem), and the
+// iterations are the phase kernels of enqueue_iteration.
 // ===========================================================================
 namespace {
 
@@ -1251,22 +1288,23 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 
 // Device address of g_static_scratch, looked up once per device with that
 // device current (the host-side symbol is only a stand-in, never a device
-// address).
+// address).  Threads that race on a device's first call both look it up and
+// store the same address.
 constexpr int kMaxDevices = 64;
-void* g_static_addr[kMaxDevices] = {};
+std::atomic<void*> g_static_addr[kMaxDevices];
 
 cudaError_t static_scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_static_addr[dev]) {
-        void* ptr = nullptr;
+    void* ptr = g_static_addr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         e = cudaGetSymbolAddress(&ptr, g_static_scratch);
         if (e != cudaSuccess) return e;
-        g_static_addr[dev] = ptr;
+        g_static_addr[dev].store(ptr, std::memory_order_release);
     }
-    *out = g_static_addr[dev];
+    *out = ptr;
     return cudaSuccess;
 }
 
@@ -1284,45 +1322,38 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     };
     if (!out_len) return reject(KPX_E_INVALID, "out_len is null");
     *out_len = 0;
-    if (!ws || !obs || !start || !goal || !cost) return reject(KPX_E_INVALID, "null argument");
-    if (n_iters < 0) return reject(KPX_E_INVALID, "n_iters must be >= 0");
-    const int32_t n_obs = obs->count;
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
     {
-        std::string msg = check_config(dyn, cfg, n_obs);
-        if (!msg.empty()) {
-            g_create_error = msg;
-            return KPX_E_INVALID;
+        // the call copies to the host and synchronises the stream, neither of
+        // which a capturing stream allows: refuse before any stream work
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        const cudaError_t ce = cudaStreamIsCapturing(stream, &cs);
+        if (ce == cudaErrorStreamCaptureImplicit || (ce == cudaSuccess && cs != cudaStreamCaptureStatusNone))
+            return reject(KPX_E_INVALID, "kpx_plan_static synchronises its stream and cannot run while the stream "
+                                         "is being captured into a CUDA graph");
+        if (ce != cudaSuccess) {
+            g_create_error = std::string("kpx_plan_static: cudaStreamIsCapturing: ") + cudaGetErrorString(ce);
+            return KPX_E_CUDA;
         }
     }
-    if (n_obs > 0 && !obs->aabb) return reject(KPX_E_INVALID, "obstacle array is null");
-    for (int a = 0; a < 3; ++a)
-        if (!finite(ws->lo[a]) || !finite(ws->hi[a]) || !(ws->hi[a] >= ws->lo[a]))
-            return reject(KPX_E_INVALID, "workspace box needs finite lo <= hi");
-    for (int i = 0; i < 6 * n_obs; ++i)
-        if (!finite(obs->aabb[i])) return reject(KPX_E_INVALID, "obstacle coordinates must be finite");
-    for (int b = 0; b < n_obs; ++b)
-        for (int a = 0; a < 3; ++a)
-            if (obs->aabb[6 * b + a] > obs->aabb[6 * b + 3 + a]) return reject(KPX_E_INVALID, "obstacle box with lo > hi");
-    for (int a = 0; a < 3; ++a)
-        if (!finite(goal->center[a])) return reject(KPX_E_INVALID, "goal centre must be finite");
-    if (!finite(goal->radius) || goal->radius < 0.0f) return reject(KPX_E_INVALID, "goal radius must be >= 0");
-    if (cost->kind < 0 || cost->kind > 2) return reject(KPX_E_INVALID, "unknown cost kind");
-    if (!finite(cost->w_effort) || cost->w_effort < 0.0f) return reject(KPX_E_INVALID, "w_effort must be >= 0");
-    if (cost->kind == KPX_COST_EFFORT_DURATION && dyn->kind != KPX_QUAD12)
-        return reject(KPX_E_INVALID, "effort+duration cost needs the quadcopter");
-    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
-    for (int i = 0; i < n; ++i)
-        if (!finite(start[i])) return reject(KPX_E_INVALID, "start state must be finite");
-    const Layout L = make_layout(dyn, cfg, n_obs);
+    if (n_iters < 0) return reject(KPX_E_INVALID, "n_iters must be >= 0");
+    Layout L;
+    {
+        std::string msg;
+        const kpx_status st = validate_problem(dyn, ws, obs, start, goal, cost, cfg, L, msg);
+        if (st != KPX_OK) {
+            g_create_error = msg;
+            return st;
+        }
+    }
     if (L.total > kStaticScratchBytes)
         return reject(KPX_E_NOMEM, "problem needs more device memory than the static scratch of "
                                    "kpx_plan_static (KPX_STATIC_SCRATCH_BYTES); use kpx_create with a workspace");
-    if ((uint64_t)cfg->tree_cap + (uint64_t)L.slot_cap >= 0xFFFFFFFFull)
-        return reject(KPX_E_INVALID, "tree_cap + candidate slots must stay below 2^32");
+    const int n = kStateDim[dyn->kind], m = kControlDim[dyn->kind];
+    const int32_t n_obs = obs->count;
 
     kpx_planner pl;  // host handle on the stack: nothing is allocated
-    pl.L = L;
-    pl.stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+    pl.stream = stream;
     void* scratch = nullptr;
     cudaError_t e = static_scratch_address(&scratch);
     if (e != cudaSuccess) {
@@ -1331,35 +1362,15 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     }
     pl.ws = reinterpret_cast<char*>(scratch);
     pl.ws_bytes = kStaticScratchBytes;
-    DevParams& P = pl.P;
-    memset(&P, 0, sizeof(P));
-    fill_dynamics(P, dyn);
-    for (int i = 0; i < 16; ++i) P.start[i] = i < n ? start[i] : 0.0f;
-    for (int a = 0; a < 3; ++a) {
-        P.ws_lo[a] = ws->lo[a];
-        P.ws_hi[a] = ws->hi[a];
-        P.goal_c[a] = goal->center[a];
+    {
+        std::string msg;
+        const kpx_status st = fill_problem(dyn, ws, obs, start, goal, cost, cfg, L, pl.grid_scale, &pl, msg);
+        if (st != KPX_OK) {
+            g_create_error = msg;
+            return st;
+        }
     }
-    set_position_box(P);
-    P.goal_r2 = goal->radius * goal->radius;
-    P.cost_kind = cost->kind;
-    P.w_effort = cost->w_effort;
-    fill_axes(P, cfg->n_axes, cfg->axis);
-    P.N = cfg->tree_cap;
-    P.lambda_fixed = cfg->samples_per_node;
-    P.i_max = cfg->i_max;
-    P.seed_lo = (uint32_t)(cfg->seed & 0xFFFFFFFFull);
-    P.seed_hi = (uint32_t)(cfg->seed >> 32);
-    P.flags = cfg->flags;
-    P.n_obs = n_obs;
-    P.va_cap = L.va_cap;
-    P.slot_cap = L.slot_cap;
-    P.mask_words = L.mask_words;
-    P.n_win_tiles = L.n_win_tiles;
-    P.n_prune_tiles = L.n_prune_tiles;
-    bind_pointers(&pl);
-    choose_grid(P, obs->aabb, n_obs);
-    if (!host_point_valid(P, P.start, obs->aabb, n_obs)) return reject(KPX_E_INVALID, "start state is not in X_valid");
+    const DevParams& P = pl.P;
 
     // obstacles: lo and hi corners copied straight from the caller's
     // float[M][6] into the float4 pairs the kernels read (no staging buffer)
@@ -1373,15 +1384,7 @@ extern "C" kpx_status kpx_plan_static(const kpx_dynamics* dyn, const kpx_workspa
     // every array that must start at zero is cleared by the first-time init
     if (e == cudaSuccess) e = launch_init(P, true, pl.stream);
     if (e == cudaSuccess) e = launch_grid_build(P, pl.stream);
-    for (int32_t it = 0; e == cudaSuccess && it < n_iters; ++it) {
-        e = launch_begin(P, pl.stream);
-        if (e == cudaSuccess) e = launch_propagate(P, nullptr, pl.stream);
-        if (e == cudaSuccess) e = launch_mark(P, pl.stream);
-        if (e == cudaSuccess) e = launch_scan(P, pl.stream);
-        if (e == cudaSuccess) e = launch_append(P, pl.stream);
-        if (e == cudaSuccess) e = launch_prune(P, pl.stream);
-        if (e == cudaSuccess) e = launch_end(P, pl.stream);
-    }
+    for (int32_t it = 0; e == cudaSuccess && it < n_iters; ++it) e = enqueue_iteration(P, pl.stream);
     if (e == cudaSuccess) e = launch_path(P, pl.stream);
     kpx_device_header h;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, P.hdr, sizeof(h), cudaMemcpyDeviceToHost, pl.stream);
