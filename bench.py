@@ -7,16 +7,17 @@ I passes of Propagate -> winner select -> UpdateTree append -> PruneNodes with
 the active-set compaction.  Every step of a run is the same deterministic
 problem, so each step does identical work.
 
-Default workload: 6D Dubins airplane, forest of 300 seeded columns
-(half-width U[0.01, 0.03]), RK4 h = 0.02, 16^3 x 4 regions, tree cap 2^20,
-lambda = 64, 200 iterations.
+Default workload: 12D quadcopter in a 1,000-box building (9 zig-zag walls
+with 0.04 x 0.04 openings plus 964 clutter boxes), RK4 h = 0.005,
+16^3 x 4^3 regions, tree cap 2^22, lambda = 128, 200 iterations.
 
 Printed (rank 0, one JSON line): value = valid expansions/s over the timed
 device region (inputs resident in HBM, L2 flushed between steps), e2e = the
 same metric through the C ABI with host buffers (kpx_create from host arrays,
 iterate, kpx_best_trajectory to host, destroy), the roofline of the dominant
-kernel (propagate, bound by FP32/ALU issue), the FP64 oracle timed on the
-host cores, and SM clocks sampled during the timed region.
+kernel (propagate, bound by FP32/ALU issue), the roofline of the tree update
+(mark + scan + append + prune, against HBM bandwidth), the FP64 oracle timed
+on the host cores, and SM clocks sampled during the timed region.
 
 --impl reference times the FP64 oracle (the CPU reference of this project) on
 the same workload and prints the same line with "impl": "reference".
@@ -62,6 +63,64 @@ PROPAGATE_DRAM_BYTES = {
     "quad12_building1000": 928768,   # profiles/k_propagate_quad12_building1000.md (iteration 20)
 }
 FP32_LANES_PER_SM = 128
+HBM_FALLBACK_GBS = 6800.0
+# Algorithmic bytes of the tree update of one iteration (PruneNodes over the
+# pre-append tree, UpdateTree's rows, the V_U filter's candidate flags):
+# per pre-append node 8 key + 4 region + 1 set + 1 inactivity count read, an
+# 8-byte gather of its region's key and 1 set byte written; per appended row
+# the state and control (4 n + 4 m), K 2, parent 4, key 8, region 4, set 1,
+# inactivity count 1 and its region's key 8; one bit per candidate slot.
+UPDATE_BYTES_PER_NODE = 23
+UPDATE_PHASES = ("mark", "scan", "append", "prune")
+
+
+def update_row_bytes(n, m):
+    return 4 * n + 4 * m + 28
+
+
+# DRAM bytes (read + write) of the update kernels of one iteration, from the
+# ncu captures in profiles/; None for a workload not captured
+UPDATE_DRAM_BYTES = {}
+
+
+def hbm_peak():
+    """(GB/s, basis): the copy bandwidth measured on this GPU pool
+    (MEASURED_PEAKS.json beside this file), else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return HBM_FALLBACK_GBS, "of fallback (6.8 TB/s, one earlier GB300 measurement)"
+
+
+def host_cpu():
+    """Model, maximum clock and logical CPU count of the host."""
+    model, mhz = None, None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            k, _, v = line.partition(":")
+            if k.strip() == "Model name" and not model:
+                model = v.strip()
+            elif k.strip() == "CPU max MHz":
+                mhz = float(v.strip())
+    except (OSError, ValueError, subprocess.SubprocessError):
+        pass
+    if mhz is None:
+        try:
+            with open("/sys/devices/system/cpu/cpu0/cpufreq/cpuinfo_max_freq") as f:
+                mhz = int(f.read().strip()) / 1000.0
+        except (OSError, ValueError):
+            pass
+    return {"model": model, "max_mhz": mhz, "logical_cpus": os.cpu_count()}
 
 
 def fma_fields(achieved):
@@ -84,7 +143,14 @@ WORKLOADS = {
                         desc="6D double integrator, 20 boxes, Euler h=0.01, 8^3x2^3 regions, cap 32768, lambda 16"),
     "quad12_building1000": dict(make=lambda seed: scenes.quad_scene(seed),
                                 desc="12D quadcopter, 1,000-box building, RK4 h=0.005, 16^3x4^3 regions, "
-                                     "cap 2^22, lambda 128"),
+                                     "cap 2^22, lambda 128", ref_iters=3),
+    # the same system and configuration among 1,000 boxes without the walls:
+    # the tree grows past 2.5 M nodes in 400 iterations, where PruneNodes and
+    # the append cover millions of nodes per iteration
+    "quad12_clutter1000": dict(make=lambda seed: scenes.quad_scene(seed, clutter=1000, certify=False, walls=False,
+                                                                   iterations=400),
+                               desc="12D quadcopter, 1,000 boxes without walls, RK4 h=0.005, 16^3x4^3 regions, "
+                                    "cap 2^22, lambda 128, 400 iterations", ref_iters=2),
 }
 BATCH_WORKLOADS = {
     "mixed_batch512": dict(count=512, desc="512 independent problems (DI / Dubins / quadcopter in turn), 10-1,000 "
@@ -109,7 +175,7 @@ REFINE_OPS_RK4_ADJOINT = 794.0     # 3 derivative + 4 vector-Jacobian evaluation
 REFINE_OPS_BOX_PENALTY = 22.0      # signed distance + softplus
 REFINE_OPS_BOX_GRADIENT = 29.0     # signed distance + its gradient + sigmoid
 REFINE_OPS_BOX_TEST = 13.0         # the squared outside distance and its comparison (every candidate box)
-DEFAULT_WORKLOAD = "dubins6_forest300"
+DEFAULT_WORKLOAD = "quad12_building1000"
 
 
 def parse_args(argv=None):
@@ -128,6 +194,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-autotune", action="store_true", help="batch workloads: keep the default launch choices")
     ap.add_argument("--no-fused", action="store_true",
                     help="run every iteration as the seven phase kernels (KPX_FLAG_NO_FUSED; same results)")
+    ap.add_argument("--no-slot-order", action="store_true",
+                    help="propagate slots in index order, not sorted by step count (KPX_FLAG_NO_SLOT_ORDER; "
+                         "same results)")
     ap.add_argument("--ttfs-seeds", type=int, default=8, help="problems (scene seeds) for time-to-first-solution")
     ap.add_argument("--ttfs-variant-seeds", type=int, default=100,
                     help="problems (scene seeds) per solvable variant for time-to-first-solution (default bench)")
@@ -274,9 +343,11 @@ def run_reference(args):
     spec = WORKLOADS[args.workload]
     prob = spec["make"](args.seed)
     iters = args.iters or prob.iterations
-    per_step_iters = min(iters, 40)
+    # a bounded sample: the oracle's first iterations of the same problem
+    # (the quadcopter's first 3 take about 4 s on one core)
+    per_step_iters = min(iters, spec.get("ref_iters", 40))
     for _ in range(args.warmup):
-        oracle_sample(prob, min(per_step_iters, 5), 1e9)
+        oracle_sample(prob, min(per_step_iters, 2), 1e9)
     vals, secs = 0, 0.0
     for _ in range(args.steps):
         r = oracle_sample(prob, per_step_iters, 1e9)
@@ -288,10 +359,14 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "desc": spec["desc"], "iterations_per_step": per_step_iters,
+                   "gpu_arm_iterations_per_step": iters, "same_iterations": per_step_iters == iters,
+                   "note": "each step times the oracle's first %d of the %d iterations the GPU arm runs on the same "
+                           "deterministic problem; both arms report valid expansions per second" % (per_step_iters,
+                                                                                                   iters),
                    "seed": args.seed},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "first %d iterations of the workload per step, single-threaded FP64 C oracle"
-                                   % per_step_iters},
+                                   % per_step_iters, "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -349,7 +424,8 @@ def run_kpx(args):
     prob = spec["make"](args.seed + rank)
     iters = args.iters or prob.iterations
     stream = torch.cuda.current_stream(dev)
-    flags = kpx.KPX_FLAG_NO_FUSED if args.no_fused else 0
+    flags = (kpx.KPX_FLAG_NO_FUSED if args.no_fused else 0) | (kpx.KPX_FLAG_NO_SLOT_ORDER if args.no_slot_order
+                                                                else 0)
     pl = kpx.Planner(prob, device=dev, stream=stream, flags=flags)
 
     # one step to learn the (deterministic) work of a step
@@ -402,11 +478,15 @@ def run_kpx(args):
     else:
         launches_per_step = 1 + 7 * iters
 
-    # per-phase device time over one step (same launches, CUDA events on the planner's stream)
+    # per-phase device time over one step (same launches, CUDA events on the
+    # planner's stream), with each iteration's tree size, winners kept and
+    # slots read from the header between iterations (outside the events)
     phase_ms = [0.0] * 7
     pl.reset()
     flush.zero_()
     evs = []
+    upd_bytes = 0
+    row = update_row_bytes(prob.n, prob.m)
     for _ in range(iters):
         for ph in range(7):
             a = torch.cuda.Event(enable_timing=True)
@@ -415,9 +495,30 @@ def run_kpx(args):
             pl.debug_step(ph)
             b.record(stream)
             evs.append((ph, a, b))
+        h = pl.header()
+        n_old = int(h.n_nodes) - int(h.n_kept)
+        upd_bytes += UPDATE_BYTES_PER_NODE * n_old + row * int(h.n_kept) + (int(h.n_slots) + 7) // 8
     torch.cuda.synchronize(dev)
     for ph, a, b in evs:
         phase_ms[ph] += a.elapsed_time(b)
+    upd_ms = sum(phase_ms[kpx.PHASES.index(n)] for n in UPDATE_PHASES)
+    hbm, hbm_basis = hbm_peak()
+    upd_gbs = upd_bytes / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else 0.0
+    l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 0)
+    work_set = UPDATE_BYTES_PER_NODE * int(st["n_nodes"]) + 8 * int(prob.n_regions)
+    roofline_update = {
+        "bound": "hbm", "kernel": "tree update: k_mark + k_scan + k_append + k_prune (phase kernels)",
+        "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": upd_gbs / hbm if hbm else 0.0,
+        "peak_basis": hbm_basis, "traffic": UPDATE_DRAM_BYTES.get(args.workload),
+        "algorithmic_bytes_per_step": upd_bytes, "update_ms_per_step": upd_ms,
+        "bytes_basis": "per iteration: %d B per pre-append node + %d B per appended row + 1 bit per candidate slot"
+                      % (UPDATE_BYTES_PER_NODE, row),
+        "working_set_bytes_end": work_set, "l2_bytes": l2,
+        "l2_resident": bool(l2 and work_set < l2),
+        "note": ("the update's working set (tree arrays and region keys) stays in L2 within a step, so this is an "
+                 "L2/latency-bound figure reported against HBM bandwidth" if l2 and work_set < l2 else
+                 "the tree outgrows L2: the update streams from HBM"),
+    }
     prop_ms = phase_ms[1]
     prop_launch_ms = prop_ms / max(1, iters_done)
     ops_step = OPS_PER_STEP[prob.dyn] * steps_per_step + OPS_PER_BOX_TEST * tests_per_step
@@ -476,7 +577,8 @@ def run_kpx(args):
         r = oracle_sample(prob, iters, args.cpu_seconds)
         cpu = {"value": r["valid"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "first %d of %d iterations of the same problem (%d valid rollouts, %.1f s), "
-                         "single-threaded FP64 C oracle" % (r["iters"], iters, r["valid"], r["seconds"])}
+                         "single-threaded FP64 C oracle" % (r["iters"], iters, r["valid"], r["seconds"]),
+               "host": host_cpu()}
 
     if rank == 0:
         line = {
@@ -505,8 +607,9 @@ def run_kpx(args):
                                            "phase_share": {n: round(t / sum(phase_ms), 4)
                                                            for n, t in zip(kpx.PHASES, phase_ms)},
                                            "note": "phase-by-phase pass over one step (kpx_debug_step)"}},
+            "roofline_update": roofline_update,
             "launch_path": {"fused": bool(fused), "fused_iterations": fused_iters, "graph_launches": graph_launches,
-                            "max_iterations_per_graph": max_g},
+                            "max_iterations_per_graph": max_g, "slot_order": not args.no_slot_order},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clk,

@@ -120,12 +120,20 @@ typedef struct {
 enum {
     /* Reject a candidate whose key cannot win its region before checking
      * obstacles (the collision-after-cost remark of the appendix).  Results
-     * are identical; only the "valid" statistic then counts fewer rollouts. */
+     * are identical; only the "valid" statistic then counts fewer rollouts.
+     * That count and the step and box-test counts then depend on the order
+     * in which candidates reach the check, so they can differ between runs
+     * and launch paths. */
     KPX_FLAG_EARLY_REJECT = 1,
     /* Never run whole iterations in the single-launch cluster kernel (used
      * while an iteration has at most a few thousand slots); every iteration
      * then launches the seven phase kernels.  Results are identical. */
-    KPX_FLAG_NO_FUSED = 2
+    KPX_FLAG_NO_FUSED = 2,
+    /* Roll the propagate kernel's slots out in index order instead of in
+     * ascending step count K within each aligned chunk of 128 slots.
+     * Results are identical (every slot's outcome is independent of the
+     * lane that computes it); only the time changes. */
+    KPX_FLAG_NO_SLOT_ORDER = 4
 };
 
 /* Planner hyperparameters (appendix "Hyperparameters"): tree capacity t_e,
@@ -540,6 +548,11 @@ typedef struct {
     int64_t slot_cap;
     int64_t mask_words;
     size_t workspace_bytes;
+    /* propagate order of the current iteration (written by the begin phase):
+     * uint8[slot_cap rounded up to 128]; entry c * 128 + p is the offset in
+     * chunk c of the slot with the p-th smallest (K, offset); null when
+     * KPX_FLAG_NO_SLOT_ORDER is set */
+    uint8_t* slot_order;
 } kpx_layout;
 
 kpx_status kpx_get_layout(const kpx_planner* p, kpx_layout* out);

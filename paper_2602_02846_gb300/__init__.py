@@ -30,6 +30,7 @@ KPX_OK, KPX_E_INVALID, KPX_E_NOMEM, KPX_E_CUDA = 0, 1, 2, 3
 KPX_TREE_FULL, KPX_NO_SOLUTION, KPX_E_TIMEOUT, KPX_E_INTERNAL = 4, 5, 6, 7
 KPX_FLAG_EARLY_REJECT = 1
 KPX_FLAG_NO_FUSED = 2
+KPX_FLAG_NO_SLOT_ORDER = 4
 PHASES = ("begin", "propagate", "mark", "scan", "append", "prune", "end")
 KEY_INF = 0xFFFFFFFFFFFFFFFF
 
@@ -110,7 +111,7 @@ class kpx_layout(C.Structure):
                 ("va", C.c_void_p * 2), ("win_slot", C.c_void_p), ("win_mask", C.c_void_p),
                 ("obstacles", C.c_void_p), ("n", C.c_int32), ("m", C.c_int32), ("N", C.c_int32),
                 ("R", C.c_int32), ("va_cap", C.c_int32), ("n_obstacles", C.c_int32), ("slot_cap", C.c_int64),
-                ("mask_words", C.c_int64), ("workspace_bytes", C.c_size_t)]
+                ("mask_words", C.c_int64), ("workspace_bytes", C.c_size_t), ("slot_order", C.c_void_p)]
 
 
 class kpx_problem(C.Structure):
@@ -475,6 +476,17 @@ class Planner:
         return dict(header=h, x=x, u=u, K=K, parent=parent, key=key, region=region, set=setb & 3,
                     set_raw=setb, icount=icount, region_key=rk, region_snap=snap, VA=va,
                     n_nodes=h.n_nodes, count_A=h.count_A, iter=h.iter, goal_key=int(h.goal_key))
+
+    def slot_order(self, n_slots: int) -> np.ndarray:
+        """The propagate order of the current iteration (begin phase), as
+        offsets within each 128-slot chunk; None when disabled."""
+        import torch
+        lay = self.layout()
+        if not lay.slot_order:
+            return None
+        self.stream.synchronize()
+        total = (int(n_slots) + 127) // 128 * 128
+        return self._view(lay.slot_order, total, torch.uint8).cpu().numpy()
 
     def win_slots(self, count: int) -> np.ndarray:
         import torch

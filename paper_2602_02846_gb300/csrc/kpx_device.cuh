@@ -33,6 +33,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
 // "Randomly sample u and dt" (Alg. 2): counter (iteration, node, sample,
 // block), key = seed words.  u_i = lo + (hi - lo) * f, f = (w >> 8) 2^-24,
 // one FP32 rounding per operation; K from word m (block 1 word 0 when m = 4).
+__device__ __forceinline__ int steps_from_word(const DevParams& P, uint32_t wk) {
+    const uint64_t range = (uint64_t)(P.k_max - P.k_min + 1);
+    return P.k_min + (int)(((uint64_t)wk * range) >> 32);
+}
+
 template <int M>
 __device__ __forceinline__ void sample_control(const DevParams& P, uint32_t iter, uint32_t node, uint32_t s,
                                                float (&u)[M], int& K) {
@@ -51,8 +56,15 @@ __device__ __forceinline__ void sample_control(const DevParams& P, uint32_t iter
         const float f = __fmul_rn(__uint2float_rn(w[i] >> 8), 0x1p-24f);
         u[i] = __fadd_rn(P.u_lo[i], __fmul_rn(__fsub_rn(P.u_hi[i], P.u_lo[i]), f));
     }
-    const uint64_t range = (uint64_t)(P.k_max - P.k_min + 1);
-    K = P.k_min + (int)(((uint64_t)wk * range) >> 32);
+    K = steps_from_word(P, wk);
+}
+
+// The step count K of sample_control() alone (the same Philox word).
+template <int M>
+__device__ __forceinline__ int sample_steps(const DevParams& P, uint32_t iter, uint32_t node, uint32_t s) {
+    const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
+    const uint4 w = philox4x32_10(make_uint4(iter, node, s, M == 4 ? 1u : 0u), key);
+    return steps_from_word(P, M == 4 ? w.x : (M == 3 ? w.w : w.z));
 }
 
 // --------------------------------------------------------------------------
@@ -115,7 +127,9 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
         fast_sincos(x[3], sph, cph);
         fast_sincos(x[4], sth, cth);
         fast_sincos(x[5], sps, cps);
-        const float inv_cth = __frcp_rn(cth);  // correctly rounded, as 1.0f / cth
+        // the hardware's approximate reciprocal (about 1 ulp): cos(theta) >= cos(pi/4)
+        // within the state bounds, and propagate, append and re-validation share it
+        const float inv_cth = __fdividef(1.0f, cth);
         const float tth = sth * inv_cth;
         const float p = x[9], q = x[10], r = x[11];
         const float a = u[0] * P.inv_mass;

@@ -160,14 +160,35 @@ __global__ void __launch_bounds__(1024) k_grid_scan(DevParams P) {
 // In the loop body of a planner's graph (loop = 1) an iteration runs only
 // while iterations are owed (graph_pending > 0); otherwise every kernel of
 // the iteration is a no-op.
+// Every warp also sorts chunks of the iteration's slots by K for the
+// propagate kernel (slot_order); the slot count and lambda it uses are read
+// from counters begin_counters leaves alone (|V_A|, the iteration, the V_A
+// buffer), exactly as begin_counters derives them.
 __global__ void k_begin(DevParams P, int loop) {
-    const bool allowed = !loop || P.hdr->graph_pending > 0;
-    const bool snap = begin_needs_snapshot(P, P.hdr, allowed);  // reads counters begin_counters leaves alone
-    if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P, P.hdr, allowed);
-    if (!snap) return;
+    kpx_device_header* H = P.hdr;
+    const bool allowed = !loop || H->graph_pending > 0;
+    const bool snap = begin_needs_snapshot(P, H, allowed);  // reads counters begin_counters leaves alone
+    const bool runs = allowed && problem_runs(P, H);
+    const int count_A = H->count_A;
+    const uint32_t iter = (uint32_t)H->iter;
+    const int32_t* va = va_current(P, H);
+    if (blockIdx.x == 0 && threadIdx.x == 0) begin_counters(P, H, allowed);
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r = tid; r < P.R; r += stride) P.region_snap[r] = P.region_key[r];
+    if (snap)
+        for (int64_t r = tid; r < P.R; r += stride) P.region_snap[r] = P.region_key[r];
+    if (runs && P.slot_order) {
+        const int lam = begin_lambda(P, count_A);
+        const int64_t n_slots = (int64_t)count_A * lam;
+        const int64_t n_chunks = (n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK;
+        const int64_t warps = stride >> 5;
+        for (int64_t c = tid >> 5; c < n_chunks; c += warps) {
+            if (P.m == 4)
+                order_chunk<4>(P, va, lam, iter, n_slots, c);
+            else
+                order_chunk<3>(P, va, lam, iter, n_slots, c);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -199,7 +220,8 @@ __global__ void __launch_bounds__(PROP_THREADS, PropOccupancy<DYN>::blocks)
     int64_t chunk = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     uint32_t steps = 0, tests = 0, n_valid = 0;
     while (chunk * 32 < n_slots) {
-        propagate_chunk<DYN, INTEG>(P, n_slots, lam, iter, va, early, chunk, rec, rec_on, steps, tests, n_valid);
+        propagate_chunk<DYN, INTEG>(P, n_slots, lam, iter, va, early, chunk, rec, rec_on, steps, tests, n_valid,
+                                    P.slot_order);
         unsigned long long t = 0ull;
         if ((threadIdx.x & 31) == 0) t = atomicAdd((unsigned long long*)&H->prop_ticket, 1ull);
         chunk = n_warps + (int64_t)__shfl_sync(FULL, t, 0);
@@ -448,7 +470,16 @@ cudaError_t launch_grid_build(const DevParams& P, cudaStream_t s) {
 }
 
 cudaError_t launch_begin(const DevParams& P, cudaStream_t s, bool loop) {
-    k_begin<<<persistent_blocks((P.R + 255) / 256, 2), 256, 0, s>>>(P, loop ? 1 : 0);
+    // the snapshot wants a few blocks per SM; the propagate order one warp
+    // per 128-slot chunk (up to 6 blocks of 8 warps per SM at 40 registers)
+    int64_t work = (P.R + 255) / 256;
+    int per_sm = 2;
+    if (P.slot_order) {
+        const int64_t order_blocks = (P.slot_cap + ORDER_CHUNK * 8 - 1) / (ORDER_CHUNK * 8);
+        if (order_blocks > work) work = order_blocks;
+        per_sm = 6;
+    }
+    k_begin<<<persistent_blocks(work, per_sm), 256, 0, s>>>(P, loop ? 1 : 0);
     return cudaGetLastError();
 }
 

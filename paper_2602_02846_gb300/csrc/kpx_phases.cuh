@@ -159,6 +159,70 @@ __device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P, const k
 }
 
 // ---------------------------------------------------------------------------
+// propagate order: the slots of each aligned ORDER_CHUNK-slot chunk sorted by
+// their step count K (one warp per chunk, a bitonic network over the warp's
+// registers and shuffles).  Only the lane that computes a slot changes, not
+// the slot's result.
+// ---------------------------------------------------------------------------
+// Ascending sort of the 128 values v[e] of all lanes, element i = lane + 32 e.
+__device__ __forceinline__ void warp_sort128(uint32_t (&v)[4]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 128; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {  // partner in this lane's registers: e ^ (j / 32)
+                const int je = j >> 5;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if ((e & je) == 0) {
+                        const int f = e | je;
+                        const bool asc = ((lane + 32 * e) & k) == 0;
+                        const uint32_t lo = min(v[e], v[f]), hi = max(v[e], v[f]);
+                        v[e] = asc ? lo : hi;
+                        v[f] = asc ? hi : lo;
+                    }
+                }
+            } else {  // partner in lane ^ j, same register
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const uint32_t o = __shfl_xor_sync(FULL, v[e], j);
+                    const bool lower = (lane & j) == 0;
+                    const bool asc = ((lane + 32 * e) & k) == 0;  // bit k is the pair's common bit
+                    v[e] = (lower == asc) ? min(v[e], o) : max(v[e], o);
+                }
+            }
+        }
+    }
+}
+
+// Chunk c of this iteration's slots: order[c * 128 + p] = offset in the
+// chunk of the slot with the p-th smallest (K, offset).  Slots past n_slots
+// take keys above every live slot's, so they sort to the chunk's end.
+template <int M>
+__device__ __forceinline__ void order_chunk(const DevParams& P, const int32_t* va, int lam, uint32_t iter,
+                                            int64_t n_slots, int64_t c) {
+    static_assert(ORDER_CHUNK == 128, "one warp sorts 4 slots per lane");
+    const int lane = threadIdx.x & 31;
+    uint32_t v[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const uint32_t off = (uint32_t)(lane + 32 * e);
+        const int64_t slot = c * ORDER_CHUNK + off;
+        if (slot < n_slots) {
+            const int j = (int)(slot / lam);
+            const int s = (int)(slot - (int64_t)j * lam);
+            v[e] = ((uint32_t)sample_steps<M>(P, iter, (uint32_t)va[j], (uint32_t)s) << 7) | off;  // K < 2^16
+        } else {
+            v[e] = 0xFFFFFF80u | off;
+        }
+    }
+    warp_sort128(v);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) P.slot_order[c * ORDER_CHUNK + lane + 32 * e] = (uint8_t)(v[e] & 127u);
+}
+
+// ---------------------------------------------------------------------------
 // propagate (Alg. 2): 32 consecutive slots, one per lane.  Slot = rank j of
 // the parent in V_A times lambda plus sample s.
 // ---------------------------------------------------------------------------
@@ -347,14 +411,20 @@ __device__ __forceinline__ void roll_candidate_coop(const DevParams& P, const Gr
     C.ok = ok;
 }
 
+// Lane l of a warp takes position chunk * 32 + l of the slot sequence: the
+// slot itself, or with `order` (written by the begin kernel) the slot at that
+// position of its ORDER_CHUNK-slot chunk sorted by K, so that a warp's lanes
+// run similar step counts.  The slots past n_slots sort last in the final
+// chunk, so a position below n_slots always names a live slot.
 template <int DYN, int INTEG>
 __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_slots, int lam, uint32_t iter,
                                                 const int32_t* va, bool early, int64_t chunk,
                                                 const kpx_debug_records& rec, int rec_on, uint32_t& steps,
-                                                uint32_t& tests, uint32_t& n_valid) {
+                                                uint32_t& tests, uint32_t& n_valid, const uint8_t* order = nullptr) {
     constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
-    const int64_t slot = chunk * 32 + (threadIdx.x & 31);
-    if (slot >= n_slots) return;
+    const int64_t pos = chunk * 32 + (threadIdx.x & 31);
+    if (pos >= n_slots) return;
+    const int64_t slot = order ? (pos & ~(int64_t)(ORDER_CHUNK - 1)) + order[pos] : pos;
     Candidate<DYN, INTEG> C;
     roll_candidate<DYN, INTEG>(P, GridView{P.cell_start, P.cell_box}, lam, iter, va, early, slot, C, steps, tests);
     n_valid += C.ok ? 1u : 0u;

@@ -69,9 +69,11 @@ def compare_propagate(prob, g, o, slots=None):
                 max_state_err=max_err, max_cost_err=float(cerr.max()) if cerr.size else 0.0)
 
 
-def step_phases(pl, prob, check_append=True):
+def step_phases(pl, prob, check_append=True, sample_slots=None, seed=0):
     """Runs one iteration phase by phase on the GPU and checks every phase
-    against the oracle.  Returns the report dict."""
+    against the oracle.  With ``sample_slots`` the oracle re-rolls that many
+    sampled slots (plus the first and last) instead of every slot; every other
+    phase is still checked in full.  Returns the report dict."""
     import torch
     n, m = prob.n, prob.m
     before = pl.arrays()
@@ -83,8 +85,14 @@ def step_phases(pl, prob, check_append=True):
     N = pl.layout().N
     g = records_host(rec, n, m, ns)
     tx, tc = oracle_inputs(before)
-    o = oracle.propagate(prob, it, lam, tx, tc, before["VA"], h.count_A)
-    rep = compare_propagate(prob, g, o)
+    if sample_slots is not None and sample_slots < ns:
+        rng = np.random.default_rng(seed)
+        sl = np.unique(np.concatenate([rng.integers(0, ns, size=sample_slots), [0, ns - 1]]))
+        o = oracle.propagate(prob, it, lam, tx, tc, before["VA"], h.count_A, slots=sl)
+        rep = compare_propagate(prob, g, o, slots=sl)
+    else:
+        o = oracle.propagate(prob, it, lam, tx, tc, before["VA"], h.count_A)
+        rep = compare_propagate(prob, g, o)
     # region argmin: the GPU's region keys after propagate equal the min over
     # its own candidate keys (atomicMin) -- bit-exact
     mid = pl.arrays()
@@ -172,3 +180,96 @@ def rk_ref_with_ids(rk_ref, g, win, kept, n0, N):
         r = g["region"][s]
         rk[r] = (g["key"][s] & np.uint64(0xFFFFFFFF00000000)) | np.uint64(n0 + rank)
     return rk
+
+
+def check_tree_fp64(prob, a, created=None, lam_at=None, max_nodes=None):
+    """Oracle-anchored invariants of a GPU tree (``a`` from Planner.arrays()).
+
+    Every edge is re-rolled by the oracle in FP64 from the parent's stored
+    state with the stored control and step count (Alg. 2): the segment is
+    valid, reaches the stored state within REL_TOL, and the node's cost is
+    the parent's plus the edge cost (Assumption 1).  The stored region is the
+    oracle's region of the stored state (the FP32 region map of both sides,
+    bit-exact), the key packs (FP32 cost, id), each visited region's key is
+    held by exactly one node of that region, V_A nodes are region-best and
+    V_T nodes are dominated, and the solution key is the least key among the
+    goal nodes.  With ``created`` (iteration that appended each node) and
+    ``lam_at`` (lambda of each iteration), every node's control and step
+    count must be the Philox draw (iteration, parent, s) for some sample
+    s < lambda, and each iteration's nodes must come in ascending (parent,
+    s) order (Alg. 4's append order).  Segments whose oracle re-roll passes
+    within NEAR of a face or bound are exempt from the validity check and
+    counted.  Returns a report."""
+    n = int(a["n_nodes"])
+    m = max_nodes if max_nodes is not None else n
+    ids = np.arange(n, dtype=np.int64)
+    par = a["parent"][:n].astype(np.int64)
+    assert par[0] == -1
+    assert np.all(par[1:] >= 0) and np.all(par[1:] < ids[1:]), "parents must precede children"
+    key = a["key"][:n]
+    assert np.array_equal(key & np.uint64(0xFFFFFFFF), ids.astype(np.uint64)), "key ids"
+    cost = oracle.key_cost(key).astype(np.float64)
+    x = a["x"][:n].astype(np.float64)
+    r0, _ = oracle.region(prob, x[0])
+    assert r0 == a["region"][0]
+    worst, exempt, draws_checked = 0.0, 0, 0
+    last_order, draws = {}, {}
+    for i in range(1, min(n, m)):
+        p = int(par[i])
+        ro = oracle.rollout(prob, x[p], a["u"][i], int(a["K"][i]))
+        if not ro["valid"]:
+            assert ro["margin"] < NEAR, "edge %d invalid away from any boundary" % i
+            exempt += 1
+        worst = max(worst, float(rel_err(a["x"][i], ro["x_end"]).max()))
+        assert abs(cost[i] - (cost[p] + ro["edge_cost"])) <= REL_TOL * max(1.0, cost[i]), "cost of node %d" % i
+        reg, _ = oracle.region(prob, x[i])
+        assert reg == a["region"][i], "region of node %d" % i
+        if created is not None:
+            t = int(created[i])
+            if (t, p) not in draws:
+                # every sample of parent p at iteration t (the oracle's Alg. 2 with V_A = [p])
+                o = oracle.propagate(prob, t, int(lam_at[t]), x, cost, np.array([p], np.int32), 1)
+                draws[(t, p)] = (o["u"].view(np.uint32), o["K"])
+            du, dk = draws[(t, p)]
+            hits = np.nonzero((dk == int(a["K"][i])) &
+                              np.all(du == np.asarray(a["u"][i], np.float32).view(np.uint32), axis=1))[0]
+            assert hits.size, "node %d: (u, K) is no Philox draw of its parent at iteration %d" % (i, t)
+            prev = last_order.get(t, (-1, -1))
+            later = hits[[(p, int(h)) > prev for h in hits]]
+            assert later.size, "iteration %d appends out of slot order at node %d" % (t, i)
+            last_order[t] = (p, int(later[0]))
+            draws_checked += 1
+    assert worst <= REL_TOL, "end state error %.3g" % worst
+    rk = a["region_key"]
+    reg = a["region"][:n].astype(np.int64)
+    assert np.all(key >= rk[reg]), "a node's key below its region's key"
+    visited = np.nonzero(rk != np.uint64(oracle.KEY_INF))[0]
+    owner = (rk[visited] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    assert np.all(owner < n) and np.array_equal(reg[owner], visited), "region key owners"
+    assert np.array_equal(key[owner], rk[visited])
+    setb = a["set"][:n]
+    assert np.all(key[setb == A] == rk[reg[setb == A]]), "V_A node not its region's best"
+    assert np.all(key[setb == T] > rk[reg[setb == T]]), "V_T node holds its region"
+    goal_key = int(a["goal_key"])
+    goal_exempt = 0
+    if goal_key != oracle.KEY_INF:
+        gid = goal_key & 0xFFFFFFFF
+        inside, margin = oracle.in_goal(prob, x[gid])
+        assert inside or margin < NEAR, "solution node outside the goal ball"
+        assert int(key[gid]) == goal_key
+    for i in range(min(n, m)):
+        inside, margin = oracle.in_goal(prob, x[i])
+        if margin < NEAR:
+            goal_exempt += 1
+        elif inside:
+            assert goal_key != oracle.KEY_INF and int(key[i]) >= goal_key, "goal node %d beats the solution" % i
+    return dict(nodes=n, checked=min(n, m), max_state_err=worst, validity_exempt=exempt, goal_exempt=goal_exempt,
+                draws_checked=draws_checked)
+
+
+def revalidate_trajectory(prob, tr):
+    """The oracle's FP64 re-validation of a returned trajectory (Sec. III)."""
+    rv = oracle.revalidate(prob, tr["states"].astype(np.float64), tr["controls"], tr["steps"])
+    assert rv["ok"], rv
+    assert abs(rv["cost"] - tr["cost"]) <= REL_TOL * max(1.0, tr["cost"]), (rv["cost"], tr["cost"])
+    return rv

@@ -1,6 +1,7 @@
 """Batched planning (kpx_batch_*): every problem of a mixed batch ends
 bit-identical to the same problem planned alone with kpx_create, whatever
-else is in the batch (the problems share launches, not state)."""
+else is in the batch (the problems share launches, not state), and every
+member's tree and solution are checked against the FP64 oracle directly."""
 import numpy as np
 import pytest
 
@@ -8,6 +9,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from paper_2602_02846_gb300 import scenes  # noqa: E402
+
+from tests import gpu_helpers as gh  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -145,3 +148,41 @@ def test_autotune_keeps_results(kpx):
         _same(_results(ref.member(i)), _results(tuned.member(i)), "problem %d" % i)
     ref.close()
     tuned.close()
+
+
+def test_batch_members_match_the_oracle(kpx):
+    """Every member of a mixed batch (the three systems, adaptive lambda and a
+    problem that overflows its tree among them) against the FP64 oracle, with
+    no single-problem planner in between: each tree edge re-rolled in FP64,
+    regions, keys, region ownership, node sets and the solution key, and each
+    node's control and step count as the Philox draw of its parent at the
+    iteration that appended it, in slot order (Alg. 2-4 per problem); every
+    returned trajectory re-validated by the oracle."""
+    probs = _mixed_problems()
+    iters = 10
+    batch = kpx.BatchPlanner(probs)
+    B = len(probs)
+    sizes = [[1] for _ in range(B)]
+    lams = [[] for _ in range(B)]
+    for _ in range(iters):
+        batch.iterate(1)
+        for i in range(B):
+            h = batch.member(i).header()
+            sizes[i].append(int(h.n_nodes))
+            lams[i].append(int(h.lam))
+    solved = 0
+    for i, prob in enumerate(probs):
+        a = batch.member(i).arrays()
+        n = int(a["n_nodes"])
+        created = np.searchsorted(np.asarray(sizes[i]), np.arange(n), side="right") - 1
+        rep = gh.check_tree_fp64(prob, a, created=created, lam_at=lams[i], max_nodes=3000)
+        print("member", i, prob.name, rep)
+        assert rep["validity_exempt"] <= max(2, 0.002 * rep["checked"])
+        tr = batch.member(i).best_trajectory()
+        if tr is not None:
+            gh.revalidate_trajectory(prob, tr)
+            solved += 1
+    full = batch.member(6).iterate(0, stats=True)
+    assert full["status"] == kpx.KPX_TREE_FULL and full["n_nodes"] == 700
+    assert solved >= 2
+    batch.close()

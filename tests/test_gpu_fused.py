@@ -24,14 +24,22 @@ def kpx():
     return k
 
 
-def _state(pl):
+def _state(pl, work_counts=True):
+    """Arrays and counters.  work_counts=False leaves out the valid, step and
+    box-test counts: with the early cost rejection they depend on the order in
+    which slots reach the region-key check (a slot checked after a better
+    valid key landed skips its obstacle pass), while every result does not."""
     a = pl.arrays()
     h = a.pop("header")
     a["counters"] = np.array([h.status, h.iter, h.n_nodes, h.count_A, h.first_solution_iter, h.n_active,
                               h.n_inactive, h.n_terminal, h.lam], np.int64)
-    a["totals"] = np.array([h.total_candidates, h.total_valid, h.total_winners, h.total_steps,
-                            h.total_box_tests, h.goal_key, h.last_candidates, h.last_valid, h.last_winners],
-                           np.uint64)
+    if work_counts:
+        a["totals"] = np.array([h.total_candidates, h.total_valid, h.total_winners, h.total_steps,
+                                h.total_box_tests, h.goal_key, h.last_candidates, h.last_valid, h.last_winners],
+                               np.uint64)
+    else:
+        a["totals"] = np.array([h.total_candidates, h.total_winners, h.goal_key, h.last_candidates,
+                                h.last_winners], np.uint64)
     a.pop("region_snap")  # scratch of the capacity rule: unwritten until a snapshot is due
     return a
 
@@ -79,7 +87,7 @@ def test_fused_equals_phase_kernels(kpx, case):
         fused.iterate(n)
         plain.iterate(n)
         done += n
-        _same(_state(plain), _state(fused), "%s after %d iterations" % (case, done))
+        _same(_state(plain, not early), _state(fused, not early), "%s after %d iterations" % (case, done))
     if case in ("di_capacity", "quad_fills_in_loop"):
         assert fused.header().status == kpx.KPX_TREE_FULL
     if case == "quad_fills_in_loop":

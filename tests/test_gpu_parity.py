@@ -117,6 +117,25 @@ def test_quad_full_config_sampled(kpx):
     assert rep["validity_exempt"] + rep["region_exempt"] <= max(2, 0.002 * rep["slots"])
 
 
+def test_quad_large_tree_lockstep(kpx):
+    """The quadcopter at its full configuration (16^3 x 4^3 regions, lambda
+    128, 2^22 capacity) among 1,000 boxes without the walls, grown past 10^6
+    nodes; then one iteration phase by phase: sampled propagate slots, and in
+    full the region argmin, the winners, the capacity rule, the appended rows,
+    PruneNodes over every node (Alg. 3; the prune's look-back spans over a
+    thousand tiles) and the next V_A."""
+    prob = scenes.quad_scene(0, clutter=1000, certify=False, walls=False)
+    pl = kpx.Planner(prob)
+    pl.iterate(45)
+    h = pl.header()
+    assert h.n_nodes >= 1_000_000, h.n_nodes
+    rep = gh.step_phases(pl, prob, sample_slots=4000)
+    print("quad large tree", rep)
+    assert rep["validity_exempt"] + rep["region_exempt"] <= max(2, 0.002 * rep["slots"])
+    assert rep["n_nodes"] >= 1_000_000 and rep["winners"] > 1000
+    pl.close()
+
+
 def test_dubins_full_config_sampled(kpx):
     prob = scenes.dubins_scene(0)
     rep = _sampled_propagate(kpx, prob, warm_iters=10, n_samples=3000)
@@ -125,8 +144,10 @@ def test_dubins_full_config_sampled(kpx):
 
 
 def _all_arrays(pl):
+    """Every tree array and region key; not the header, nor region_snap (the
+    capacity rule's scratch, unwritten until a snapshot is due)."""
     a = pl.arrays()
-    return {k: v for k, v in a.items() if k != "header"}
+    return {k: v for k, v in a.items() if k not in ("header", "region_snap")}
 
 
 def _same(a, b):
@@ -157,6 +178,51 @@ def test_production_iteration_equals_phases_and_early_reject(kpx):
     pe.iterate(9)
     _same(ref, _all_arrays(pe))
     pe.close()
+
+
+@pytest.mark.parametrize("case", ["quad_full", "quad_small", "di_adaptive", "dubins_forest"])
+def test_slot_order_sorts_by_steps_and_leaves_results_unchanged(kpx, case):
+    """The begin phase orders each 128-slot chunk by (K, offset): a
+    permutation of the chunk whose live slots come first in non-decreasing K.
+    Rolling the slots out in that order changes no result: workspaces and the
+    step, box-test and valid counters equal those of index order."""
+    prob = scenes.quad_scene(0) if case == "quad_full" else CASES[case]()
+    iters = {"quad_full": 4, "quad_small": 4, "di_adaptive": 3, "dubins_forest": 8}[case]
+    flags = kpx.KPX_FLAG_NO_FUSED
+    pa = kpx.Planner(prob, flags=flags)
+    pb = kpx.Planner(prob, flags=flags | kpx.KPX_FLAG_NO_SLOT_ORDER)
+    pa.iterate(iters)
+    pb.iterate(iters)
+    # the order of the next iteration against the K the propagate records carry
+    rec = pa.make_records()
+    pa.debug_step("begin")
+    h = pa.header()
+    ns = int(h.n_slots)
+    order = pa.slot_order(ns)
+    pa.debug_step("propagate", rec)
+    pb.debug_step("begin")
+    pb.debug_step("propagate")
+    assert ns > 0 and order is not None and pb.slot_order(ns) is None
+    K = rec["K"][:ns].cpu().numpy()
+    chunks = order.reshape(-1, 128).astype(np.int64)
+    for c, perm in enumerate(chunks):
+        assert np.array_equal(np.sort(perm), np.arange(128)), "chunk %d is not a permutation" % c
+        live = min(128, ns - 128 * c)
+        slots = 128 * c + perm[:live]
+        assert np.all(slots < ns), "a dead slot sorted before a live one"
+        key = K[slots].astype(np.int64) * 128 + perm[:live]
+        assert np.all(np.diff(key) > 0), "chunk %d not in ascending (K, offset)" % c
+    for ph in kpx.PHASES[2:]:
+        pa.debug_step(ph)
+        pb.debug_step(ph)
+    pa.iterate(2)
+    pb.iterate(2)
+    _same(_all_arrays(pb), _all_arrays(pa))
+    sa, sb = pa.iterate(0, stats=True), pb.iterate(0, stats=True)
+    for k in ("total_valid", "total_steps", "total_box_tests", "total_candidates", "n_nodes"):
+        assert sa[k] == sb[k], k
+    pa.close()
+    pb.close()
 
 
 def test_determinism_and_reset(kpx):

@@ -1,7 +1,8 @@
 """The request loop on the GPU: every served query ends bit-identical to the
 same problem planned alone (kpx_create + kpx_iterate for its budget), though
 it was admitted into a recycled slot, in arena memory another query used
-before, and iterated beside whatever else was resident."""
+before, and iterated beside whatever else was resident.  Each served tree and
+solution is also checked against the FP64 oracle directly."""
 import numpy as np
 import pytest
 
@@ -10,6 +11,8 @@ pytestmark = pytest.mark.gpu
 
 from paper_2602_02846_gb300 import scenes  # noqa: E402
 from paper_2602_02846_gb300.serve import Request, Server, summarize  # noqa: E402
+
+from tests import gpu_helpers as gh  # noqa: E402
 
 
 @pytest.fixture(scope="module")
@@ -76,6 +79,7 @@ def test_served_results_equal_planning_alone(kpx):
     assert srv.arena.in_use == 0
     reused = len({o.slot for o in out}) < len(out)
     assert reused
+    n_solved = 0
     for r, o in zip(reqs, out):
         assert o.status in ("done", "tree_full"), (r.rid, o.status)
         single = kpx.Planner(r.problem)
@@ -90,6 +94,13 @@ def test_served_results_equal_planning_alone(kpx):
             assert o.cost == ts["cost"]
         assert o.iterations == int(ref["counters"][1])
         single.close()
+        # the served tree and solution against the FP64 oracle (no CUDA planner in between)
+        rep = gh.check_tree_fp64(r.problem, got, max_nodes=1500)
+        assert rep["validity_exempt"] <= max(2, 0.002 * rep["checked"]), (r.rid, rep)
+        if traj is not None:
+            gh.revalidate_trajectory(r.problem, traj)
+            n_solved += 1
+    assert n_solved >= 1
     assert out[5].status == "tree_full" and out[5].n_nodes == 700
     srv.batch.close()
 

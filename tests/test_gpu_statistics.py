@@ -9,6 +9,11 @@ near-tie, so results are compared as distributions, with the bounds:
 * every GPU trajectory re-validated by the oracle in FP64 (segment error
   <= 1e-4, clearance >= -1e-4, goal reached within 1e-4, cost within 1e-4).
 
+Seeds 0-99 of three families, one per system.  The quadcopter family is a
+reduced configuration on both sides (120 boxes without walls, 2^15 nodes,
+lambda 8, 20 iterations; the tree fills after about 14), so that 100 oracle
+runs take a minute on the host cores.
+
 The oracle runs in a process pool started (spawn) before the first GPU call.
 """
 import concurrent.futures as cf
@@ -23,13 +28,17 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from tests import gpu_helpers as gh  # noqa: E402
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-SEEDS = list(range(24))
+SEEDS = list(range(100))
 
 FAMILIES = {
     # the paper's large-delta DI setting scaled to a 32,768-node tree (16^3 x 2^3 regions)
     "di16": dict(kind="di", kw=dict(grid_pos=16, tree_cap=32768), iters=40),
     "dubins_open": dict(kind="dubins", kw=dict(n_obstacles=0, tree_cap=1 << 14, lam=16), iters=40),
+    "quad_room": dict(kind="quad", kw=dict(clutter=120, certify=False, walls=False, tree_cap=1 << 15, lam=8),
+                      iters=20),
 }
 
 
@@ -70,7 +79,6 @@ def oracle_results():
 def test_success_and_cost_distributions_match_oracle(family, oracle_results):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    import oracle
     import paper_2602_02846_gb300 as kpx
     from scipy import stats
     f = FAMILIES[family]
@@ -84,12 +92,8 @@ def test_success_and_cost_distributions_match_oracle(family, oracle_results):
         pl.close()
         gpu[seed] = tr["cost"] if tr else None
         if tr is not None:
-            rv = oracle.revalidate(prob, tr["states"].astype(np.float64), tr["controls"], tr["steps"])
+            rv = gh.revalidate_trajectory(prob, tr)
             worst_seg = max(worst_seg, rv["max_seg_err"])
-            assert rv["max_seg_err"] <= 1e-4
-            assert rv["min_clearance"] >= -1e-4
-            assert rv["goal_slack"] >= -1e-4
-            assert abs(rv["cost"] - tr["cost"]) <= 1e-4 * max(1.0, tr["cost"])
     orc = oracle_results[family]
     g_ok = [c for c in gpu.values() if c is not None]
     o_ok = [c for c in orc.values() if c is not None]
