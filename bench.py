@@ -58,10 +58,7 @@ SM_COUNT_FALLBACK = 152
 FUSED_DRAM_BYTES = {
     "dubins6_forest300": 178432,     # profiles/k_fused_dubins6_forest300.md (one 200-iteration launch)
 }
-PROPAGATE_DRAM_BYTES = {
-    "dubins6_forest300": 34816,      # profiles/k_propagate_dubins6_forest300.md (phase-kernel path)
-    "quad12_building1000": 928768,   # profiles/k_propagate_quad12_building1000.md (iteration 20)
-}
+PROPAGATE_DRAM_BYTES = {}
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
 # Algorithmic bytes of the tree update of one iteration (PruneNodes over the
@@ -78,8 +75,9 @@ def update_row_bytes(n, m):
     return 4 * n + 4 * m + 28
 
 
-# DRAM bytes (read + write) of the update kernels of one iteration, from the
-# ncu captures in profiles/; None for a workload not captured
+# DRAM bytes (read + write) of the four update kernels of one iteration, from
+# the ncu captures in profiles/ (each kernel from a cold L2, as ncu flushes
+# caches between captured kernels): workload -> (iteration, bytes)
 UPDATE_DRAM_BYTES = {}
 
 
@@ -479,14 +477,12 @@ def run_kpx(args):
         launches_per_step = 1 + 7 * iters
 
     # per-phase device time over one step (same launches, CUDA events on the
-    # planner's stream), with each iteration's tree size, winners kept and
-    # slots read from the header between iterations (outside the events)
+    # planner's stream; nothing synchronises inside the pass, so the host
+    # stays ahead of the device and the events time the kernels alone)
     phase_ms = [0.0] * 7
     pl.reset()
     flush.zero_()
     evs = []
-    upd_bytes = 0
-    row = update_row_bytes(prob.n, prob.m)
     for _ in range(iters):
         for ph in range(7):
             a = torch.cuda.Event(enable_timing=True)
@@ -495,12 +491,22 @@ def run_kpx(args):
             pl.debug_step(ph)
             b.record(stream)
             evs.append((ph, a, b))
-        h = pl.header()
-        n_old = int(h.n_nodes) - int(h.n_kept)
-        upd_bytes += UPDATE_BYTES_PER_NODE * n_old + row * int(h.n_kept) + (int(h.n_slots) + 7) // 8
     torch.cuda.synchronize(dev)
     for ph, a, b in evs:
         phase_ms[ph] += a.elapsed_time(b)
+    # the same iterations again, untimed, reading each one's tree size,
+    # winners kept and slots (the update's algorithmic bytes)
+    upd_bytes, upd_bytes_at = 0, {}
+    row = update_row_bytes(prob.n, prob.m)
+    pl.reset()
+    for it in range(iters):
+        for ph in range(7):
+            pl.debug_step(ph)
+        h = pl.header()
+        n_old = int(h.n_nodes) - int(h.n_kept)
+        b_it = UPDATE_BYTES_PER_NODE * n_old + row * int(h.n_kept) + (int(h.n_slots) + 7) // 8
+        upd_bytes += b_it
+        upd_bytes_at[it] = b_it
     upd_ms = sum(phase_ms[kpx.PHASES.index(n)] for n in UPDATE_PHASES)
     hbm, hbm_basis = hbm_peak()
     upd_gbs = upd_bytes / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else 0.0
@@ -509,7 +515,13 @@ def run_kpx(args):
     roofline_update = {
         "bound": "hbm", "kernel": "tree update: k_mark + k_scan + k_append + k_prune (phase kernels)",
         "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": upd_gbs / hbm if hbm else 0.0,
-        "peak_basis": hbm_basis, "traffic": UPDATE_DRAM_BYTES.get(args.workload),
+        "peak_basis": hbm_basis,
+        "traffic": UPDATE_DRAM_BYTES[args.workload][1] if args.workload in UPDATE_DRAM_BYTES else None,
+        "traffic_iteration": UPDATE_DRAM_BYTES[args.workload][0] if args.workload in UPDATE_DRAM_BYTES else None,
+        "algorithmic_bytes_at_traffic_iteration": (upd_bytes_at.get(UPDATE_DRAM_BYTES[args.workload][0])
+                                                   if args.workload in UPDATE_DRAM_BYTES else None),
+        "traffic_note": "DRAM bytes of the four update kernels of one iteration (ncu capture, each kernel from a "
+                        "cold L2; profiles/), beside the algorithmic bytes of the same iteration",
         "algorithmic_bytes_per_step": upd_bytes, "update_ms_per_step": upd_ms,
         "bytes_basis": "per iteration: %d B per pre-append node + %d B per appended row + 1 bit per candidate slot"
                       % (UPDATE_BYTES_PER_NODE, row),

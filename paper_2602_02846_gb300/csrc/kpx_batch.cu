@@ -4,7 +4,7 @@
 // with the number of problems.
 //
 // Each problem keeps its own workspace laid out exactly as a single planner's,
-// its own counters, Philox keys and tile words; work units (32-slot chunks,
+// its own counters, Philox keys, tile words and propagate order; work units (32-slot chunks,
 // regions, scan tiles, winners, prune tiles) are numbered across problems by
 // prefix sums recomputed every iteration, and a unit finds its problem by a
 // binary search.  Nothing couples two problems, so each result is the one the
@@ -69,9 +69,24 @@ __global__ void __launch_bounds__(1024) k_b_begin(BatchParams BP) {
     }
 }
 
-// region snapshot where the capacity rule could trigger (grid.y = problem)
+// region snapshot where the capacity rule could trigger, and the propagate
+// order of the problem's slots (each 128-slot chunk sorted by K; grid.y =
+// problem)
 __global__ void k_b_snapshot(BatchParams BP) {
     const DevParams& P = BP.Ps[blockIdx.y];
+    const kpx_device_header* H = P.hdr;
+    if (H->active && P.slot_order) {
+        const int64_t n_slots = H->n_slots;
+        const int64_t n_chunks = (n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK;
+        const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+        const int32_t* va = va_current(P, H);
+        for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
+            if (P.m == 4)
+                order_chunk<4>(P, va, H->lambda, (uint32_t)H->iter, n_slots, c);
+            else
+                order_chunk<3>(P, va, H->lambda, (uint32_t)H->iter, n_slots, c);
+        }
+    }
     if (!begin_needs_snapshot(P, P.hdr)) return;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
         P.region_snap[r] = P.region_key[r];
@@ -101,7 +116,7 @@ __global__ void __launch_bounds__(PROP_THREADS, BatchPropOccupancy<DYN>::blocks)
         const kpx_device_header* H = P.hdr;
         const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) != 0;
         propagate_chunk<DYN, INTEG>(P, H->n_slots, H->lambda, (uint32_t)H->iter, va_current(P, H), early,
-                                    chunk - BP.chunk_prefix[p], no_rec, 0, steps, tests, n_valid);
+                                    chunk - BP.chunk_prefix[p], no_rec, 0, steps, tests, n_valid, P.slot_order);
         unsigned long long t = 0ull;
         if ((threadIdx.x & 31) == 0) t = atomicAdd(&BP.bh->prop_ticket[BP.cls], 1ull);
         chunk = c_lo + n_warps + (int64_t)__shfl_sync(FULL, t, 0);

@@ -98,7 +98,10 @@ __device__ __forceinline__ void fast_sincos(float a, float& s, float& c) {
     __sincosf(r, &s, &c);
 }
 
-template <int DYN>
+// ISO (quadcopter only): the inertia is isotropic (J_x = J_y = J_z), so the
+// gyroscopic term omega x J omega is zero and omega' = tau / J.  With J
+// isotropic both forms give the same FP32 values for finite states.
+template <int DYN, bool ISO = false>
 __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<DYN>::n],
                                       const float (&u)[Dims<DYN>::m], float (&dx)[Dims<DYN>::n]) {
     if constexpr (DYN == KPX_DI6) {
@@ -123,9 +126,12 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
     } else {
         // p' = v; v' = (T/m) R(phi,theta,psi) e3 - g e3 (R = Rz Ry Rx);
         // (phi,theta,psi)' = W(phi,theta) omega; omega' = J^-1 (tau - omega x J omega)
+        // roll and pitch stay near the state bounds' range (|phi|, |theta| <= pi/4 at
+        // every checked point; a stage point passes it by at most h |rate|), where the
+        // hardware sine and cosine need no range reduction; yaw is unbounded
         float sph, cph, sth, cth, sps, cps;
-        fast_sincos(x[3], sph, cph);
-        fast_sincos(x[4], sth, cth);
+        __sincosf(x[3], &sph, &cph);
+        __sincosf(x[4], &sth, &cth);
         fast_sincos(x[5], sps, cps);
         // the hardware's approximate reciprocal (about 1 ulp): cos(theta) >= cos(pi/4)
         // within the state bounds, and propagate, append and re-validation share it
@@ -147,19 +153,25 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
         dx[6] = a * r13;
         dx[7] = a * r23;
         dx[8] = fmaf(a, r33, -P.param[1]);
-        dx[9] = fmaf(-P.dJ[0] * q, r, u[1]) * P.inv_J[0];
-        dx[10] = fmaf(-P.dJ[1] * r, p, u[2]) * P.inv_J[1];
-        dx[11] = fmaf(-P.dJ[2] * p, q, u[3]) * P.inv_J[2];
+        if constexpr (ISO) {
+            dx[9] = u[1] * P.inv_J[0];
+            dx[10] = u[2] * P.inv_J[1];
+            dx[11] = u[3] * P.inv_J[2];
+        } else {
+            dx[9] = fmaf(-P.dJ[0] * q, r, u[1]) * P.inv_J[0];
+            dx[10] = fmaf(-P.dJ[1] * r, p, u[2]) * P.inv_J[1];
+            dx[11] = fmaf(-P.dJ[2] * p, q, u[3]) * P.inv_J[2];
+        }
     }
 }
 
 // One PropagateODE step: forward Euler or classic RK4, control held constant.
-template <int DYN, int INTEG>
+template <int DYN, int INTEG, bool ISO = false>
 __device__ __forceinline__ void step(const DevParams& P, float (&x)[Dims<DYN>::n], const float (&u)[Dims<DYN>::m]) {
     constexpr int n = Dims<DYN>::n;
     const float h = P.h;
     float k1[n];
-    deriv<DYN>(P, x, u, k1);
+    deriv<DYN, ISO>(P, x, u, k1);
     if constexpr (INTEG == KPX_EULER) {
 #pragma unroll
         for (int i = 0; i < n; ++i) x[i] = fmaf(h, k1[i], x[i]);
@@ -173,19 +185,19 @@ __device__ __forceinline__ void step(const DevParams& P, float (&x)[Dims<DYN>::n
             acc[i] = k1[i];
             xt[i] = fmaf(hh, k1[i], x[i]);
         }
-        deriv<DYN>(P, xt, u, k1);
+        deriv<DYN, ISO>(P, xt, u, k1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             acc[i] = fmaf(2.0f, k1[i], acc[i]);
             xt[i] = fmaf(hh, k1[i], x[i]);
         }
-        deriv<DYN>(P, xt, u, k1);
+        deriv<DYN, ISO>(P, xt, u, k1);
 #pragma unroll
         for (int i = 0; i < n; ++i) {
             acc[i] = fmaf(2.0f, k1[i], acc[i]);
             xt[i] = fmaf(h, k1[i], x[i]);
         }
-        deriv<DYN>(P, xt, u, k1);
+        deriv<DYN, ISO>(P, xt, u, k1);
 #pragma unroll
         for (int i = 0; i < n; ++i) x[i] = fmaf(h6, acc[i] + k1[i], x[i]);
     }
@@ -305,6 +317,21 @@ struct Stepper {
     __device__ __forceinline__ void init(const DevParams&, const float (&)[n], const float (&)[m]) {}
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
         step<DYN, INTEG>(P, x, u);
+    }
+};
+
+// The quadcopter's RK4: with isotropic inertia (flag set by the host when
+// J_x = J_y = J_z exactly) the body rates' derivative is the constant tau / J,
+// which the compiler keeps out of the step loop.  One uniform branch per step.
+template <>
+struct Stepper<KPX_QUAD12, KPX_RK4> {
+    static constexpr int n = 12, m = 4;
+    __device__ __forceinline__ void init(const DevParams&, const float (&)[n], const float (&)[m]) {}
+    __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
+        if (P.iso_inertia)
+            step<KPX_QUAD12, KPX_RK4, true>(P, x, u);
+        else
+            step<KPX_QUAD12, KPX_RK4, false>(P, x, u);
     }
 };
 

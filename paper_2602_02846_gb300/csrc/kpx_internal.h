@@ -55,6 +55,7 @@ struct DevParams {
     float mg, inv_mg, inv_tau_max, inv_mass;
     float inv_J[3], J[3];
     float dJ[3];                 // J[2] - J[1], J[0] - J[2], J[1] - J[0] (FP32, as the device would round them)
+    int32_t iso_inertia;         // quadcopter: J[0] = J[1] = J[2] exactly (omega' = tau / J)
     float pos_lo[3], pos_hi[3];  // the workspace box intersected with the state bounds of x, y, z
     int32_t n_axes;
     int32_t ax_dim[8], ax_bins[8], ax_wrap[8];
@@ -191,6 +192,7 @@ inline void fill_dynamics(DevParams& P, const kpx_dynamics* dyn) {
         P.dJ[0] = P.J[2] - P.J[1];
         P.dJ[1] = P.J[0] - P.J[2];
         P.dJ[2] = P.J[1] - P.J[0];
+        P.iso_inertia = (P.J[0] == P.J[1] && P.J[1] == P.J[2]) ? 1 : 0;
     }
 }
 

@@ -46,7 +46,15 @@ CASES = {
     "dubins_forest": lambda: scenes.dubins_scene(0),
     "dubins_open": lambda: scenes.dubins_scene(1, n_obstacles=0, tree_cap=1 << 16, lam=16),
     "quad_small": lambda: scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8),
+    # anisotropic inertia: the general body-rate dynamics with the gyroscopic term
+    "quad_aniso": lambda: _anisotropic(scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8)),
 }
+
+
+def _anisotropic(prob):
+    p = list(prob.param)
+    p[2:5] = [scenes.f32(0.008), scenes.f32(0.011), scenes.f32(0.015)]
+    return prob.replace(param=p)
 
 
 @pytest.mark.parametrize("case", list(CASES))
@@ -54,7 +62,7 @@ def test_iteration_lockstep(kpx, case):
     """Several consecutive iterations, each checked phase by phase."""
     prob = CASES[case]()
     iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "dubins_forest": 6,
-             "dubins_open": 8, "quad_small": 3}[case]
+             "dubins_open": 8, "quad_small": 3, "quad_aniso": 3}[case]
     pl, reps = _run_lockstep(kpx, prob, iters)
     assert reps, "no iteration ran"
     tot = sum(r["slots"] for r in reps)
