@@ -6,11 +6,15 @@
 //
 // Layout: one warp per trajectory, taken in the caller's order (longest
 // first balances the launch).  The state integration is sequential, so
-// every lane integrates the same RK4 step (registers, no broadcast).  The
-// obstacle sum, the expensive part (every box at every step), is split across
-// the lanes and reduced with warp shuffles.  The boxes sit in shared memory
-// in SoA form.  A box whose softplus term is negligible (beta (margin - d) <
-// -30) is rejected on the squared distance, without a square root.
+// every lane integrates the same RK4 step (registers, no broadcast), and the
+// launch takes as long as the longest trajectory's chain of dependent steps.
+// The obstacle terms are kept off that chain: the forward pass integrates 32
+// steps while lane t keeps the point after step t, then every lane sums the
+// box terms of its own point; the backward pass re-integrates an interval,
+// then lane t computes the penalty gradient at step t + 1 into shared memory
+// before the serial adjoint recursion reads it.  The boxes sit in shared
+// memory in SoA form.  A box whose softplus term is negligible (beta (margin
+// - d) < -30) is rejected on the squared distance, without a square root.
 //
 // Gradient: the forward pass stores the state every REFINE_CKPT_STEPS steps.
 // The backward pass walks the checkpoint intervals from the last one back,
@@ -428,16 +432,15 @@ __device__ __forceinline__ void candidates(const BoxSource& S, int n_obs, float 
 
 __device__ __forceinline__ int box_of(const BoxSource& S, int e) { return S.grid ? (int)S.ids[e] : e; }
 
-// this lane's share of beta * sum_b sp(margin - d_b(p)); far2 = the squared
-// distance beyond which a box's term is dropped
-__device__ __forceinline__ float penalty_lane(const RefineParams& R, const ObsSmem& O, const BoxSource& S, float px,
-                                              float py, float pz, float far2, int lane, uint32_t& n_test,
-                                              uint32_t& n_near) {
+// beta * sum_b sp(margin - d_b(p)) at one point, every candidate box of its
+// cell in order; far2 = the squared distance beyond which a box's term is
+// dropped
+__device__ __forceinline__ float penalty_point(const RefineParams& R, const ObsSmem& O, const BoxSource& S, float px,
+                                               float py, float pz, float far2, uint32_t& n_test, uint32_t& n_near) {
     float acc = 0.0f;
     int e0, e1;
     candidates(S, R.n_obs, px, py, pz, e0, e1);
-#pragma unroll 4
-    for (int e = e0 + lane; e < e1; e += 32) {
+    for (int e = e0; e < e1; ++e) {
         const int b = box_of(S, e);
         float dx, dy, dz;
         const float o2 = box_offset(px, py, pz, O, b, dx, dy, dz);
@@ -451,15 +454,14 @@ __device__ __forceinline__ float penalty_lane(const RefineParams& R, const ObsSm
     return acc;
 }
 
-// this lane's share of d/dp sum_b sp(margin - d_b(p)) = -sum_b sigma(t) grad d_b
-__device__ __forceinline__ void penalty_grad_lane(const RefineParams& R, const ObsSmem& O, const BoxSource& S,
-                                                  float px, float py, float pz, float far2, int lane, float& ox,
-                                                  float& oy, float& oz, uint32_t& n_test, uint32_t& n_near) {
+// d/dp sum_b sp(margin - d_b(p)) = -sum_b sigma(t) grad d_b at one point
+__device__ __forceinline__ void penalty_grad_point(const RefineParams& R, const ObsSmem& O, const BoxSource& S,
+                                                   float px, float py, float pz, float far2, float& ox, float& oy,
+                                                   float& oz, uint32_t& n_test, uint32_t& n_near) {
     ox = oy = oz = 0.0f;
     int e0, e1;
     candidates(S, R.n_obs, px, py, pz, e0, e1);
-#pragma unroll 4
-    for (int e = e0 + lane; e < e1; e += 32) {
+    for (int e = e0; e < e1; ++e) {
         const int b = box_of(S, e);
         float dx, dy, dz;
         const float o2 = box_offset(px, py, pz, O, b, dx, dy, dz);
@@ -564,6 +566,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_forward(RefineParams 
 #pragma unroll
     for (int i = 0; i < 12; ++i) x[i] = R.x0[tr * 12 + i];
     float effort = 0.0f, pen = 0.0f;
+    float px = 0.0f, py = 0.0f, pz = 0.0f;  // this lane's point of the current block of 32 steps
     int step = 0;
     for (int s = 0; s < S; ++s) {
         float u[4], gdummy[4];
@@ -580,9 +583,16 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_forward(RefineParams 
                 if (lane == 13) c[13] = __int_as_float(j);
             }
             rk4_step(R, x, u);
-            pen += penalty_lane(R, O, BS, x[0], x[1], x[2], far2, lane, n_test, n_near);
+            const int t = step & 31;
+            if (lane == t) {
+                px = x[0];
+                py = x[1];
+                pz = x[2];
+            }
+            if (t == 31) pen += penalty_point(R, O, BS, px, py, pz, far2, n_test, n_near);  // 32 points, one a lane
         }
     }
+    if (lane < (step & 31)) pen += penalty_point(R, O, BS, px, py, pz, far2, n_test, n_near);  // the last block
     count_tests(R, 0, n_test, n_near);
     pen = warp_sum(pen);
     if (lane == 0) {
@@ -596,15 +606,18 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_forward(RefineParams 
 // ---------------------------------------------------------------------------
 // backward: dJ/du by the adjoint recursion, interval by interval
 // ---------------------------------------------------------------------------
-constexpr int BWD_WARP_FLOATS = (REFINE_CKPT_STEPS + 1) * 12 + REFINE_CKPT_STEPS;
+// per warp: the interval's states, segment ids and penalty gradients
+constexpr int BWD_WARP_FLOATS = (REFINE_CKPT_STEPS + 1) * 12 + REFINE_CKPT_STEPS + 3 * REFINE_CKPT_STEPS;
 
 __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams R) {
     extern __shared__ float smem[];
     const ObsSmem O = stage_obstacles(R, smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per-warp scratch after the boxes: the interval's states and segment ids
+    // per-warp scratch after the boxes: the interval's states, segment ids and
+    // the penalty gradient at each step's end point
     float* xs = smem + 6 * R.n_obs + warp * BWD_WARP_FLOATS;
     int* seg_of = reinterpret_cast<int*>(xs + (REFINE_CKPT_STEPS + 1) * 12);
+    float* pg = xs + (REFINE_CKPT_STEPS + 1) * 12 + REFINE_CKPT_STEPS;
     const int64_t slot = (int64_t)blockIdx.x * ADJ_WARPS + warp;
     if (slot >= R.count) return;
     const int64_t tr = R.order ? R.order[slot] : slot;
@@ -663,23 +676,26 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
         for (int i = 0; i < 12; ++i)
             if (lane == i) xs[len * 12 + i] = x[i];
         __syncwarp();
+        // the penalty at p_{k+1} of every step of the interval, one step a
+        // lane: d/dp w_obs sp(margin - d) = -w_obs sigma grad d (it depends on
+        // the stored states only, not on the adjoint)
+        if (lane < len) {
+            float ox, oy, oz;
+            penalty_grad_point(R, O, BS, xs[(lane + 1) * 12 + 0], xs[(lane + 1) * 12 + 1], xs[(lane + 1) * 12 + 2],
+                               far2, ox, oy, oz, n_test, n_near);
+            pg[3 * lane] = ox;
+            pg[3 * lane + 1] = oy;
+            pg[3 * lane + 2] = oz;
+        }
+        __syncwarp();
         if (c == n_ck - 1) {  // dJ/dx_N of the goal pull
 #pragma unroll
             for (int a = 0; a < 3; ++a) lam[a] = 2.0f * R.w_goal * (x[a] - R.goal[a]);
         }
         for (int t = len - 1; t >= 0; --t) {
-            // the penalty at p_{k+1}: d/dp w_obs sp(margin - d) = -w_obs sigma grad d
-            float ox, oy, oz;
-            const uint32_t near0 = n_near;
-            penalty_grad_lane(R, O, BS, xs[(t + 1) * 12 + 0], xs[(t + 1) * 12 + 1], xs[(t + 1) * 12 + 2], far2, lane,
-                              ox, oy, oz, n_test, n_near);
-            // most steps have no box within the far distance: then every
-            // lane's share is 0 and the three reductions are skipped
-            if (__any_sync(0xFFFFFFFFu, n_near != near0)) {
-                lam[0] += R.w_obs * warp_sum(ox);
-                lam[1] += R.w_obs * warp_sum(oy);
-                lam[2] += R.w_obs * warp_sum(oz);
-            }
+            lam[0] += R.w_obs * pg[3 * t];
+            lam[1] += R.w_obs * pg[3 * t + 1];
+            lam[2] += R.w_obs * pg[3 * t + 2];
             const int sk = seg_of[t];
             if (sk != cur_seg) {  // entering an earlier segment: commit the later one
                 if (cur_seg >= 0 && lane == 0) {
