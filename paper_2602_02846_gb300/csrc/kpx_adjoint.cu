@@ -54,9 +54,9 @@ __device__ __forceinline__ Trig trig_of(const float (&x)[12]) {
 // dynamics: x' = f(x, u) (p, ZYX Euler angles, v, body rates; u = thrust,
 // torques) and a^T df/dx, a^T df/du
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void quad_f(const RefineParams& R, const float (&x)[12], const float (&u)[4],
-                                       float (&dx)[12]) {
-    const Trig T = trig_of(x);
+// f at a state whose angles' sine and cosine are T
+__device__ __forceinline__ void quad_f_t(const RefineParams& R, const Trig& T, const float (&x)[12],
+                                         const float (&u)[4], float (&dx)[12]) {
     const float tth = T.sth * T.ic;
     const float p = x[9], q = x[10], r = x[11];
     const float A = u[0] * R.inv_mass;
@@ -75,12 +75,17 @@ __device__ __forceinline__ void quad_f(const RefineParams& R, const float (&x)[1
     dx[11] = (u[3] - (R.J[1] - R.J[0]) * p * q) * R.inv_J[2];
 }
 
-__device__ __forceinline__ void quad_vjp(const RefineParams& R, const float (&x)[12], const float (&u)[4],
-                                         const float (&a)[12], float (&gx)[12], float (&gu)[4]) {
-    const Trig T = trig_of(x);
+__device__ __forceinline__ void quad_f(const RefineParams& R, const float (&x)[12], const float (&u)[4],
+                                       float (&dx)[12]) {
+    quad_f_t(R, trig_of(x), x, u, dx);
+}
+
+// a^T df/dx and a^T df/du at a state with angle sine/cosine T and body rates (p, q, r)
+__device__ __forceinline__ void quad_vjp_t(const RefineParams& R, const Trig& T, float p, float q, float r,
+                                           const float (&u)[4], const float (&a)[12], float (&gx)[12],
+                                           float (&gu)[4]) {
     const float sphi = T.sphi, cphi = T.cphi, sth = T.sth, cth = T.cth, spsi = T.spsi, cpsi = T.cpsi, ic = T.ic;
     const float tth = sth * ic;
-    const float p = x[9], q = x[10], r = x[11];
     const float A = u[0] * R.inv_mass;
     const float w = sphi * q + cphi * r;   // psi' cos(theta)
     const float wp = cphi * q - sphi * r;  // d w / d phi
@@ -142,29 +147,85 @@ __device__ __forceinline__ void rk4_step(const RefineParams& R, float (&x)[12], 
     for (int i = 0; i < 12; ++i) x[i] += (h / 6.0f) * (acc[i] + k[i]);
 }
 
-// Adjoint of one RK4 step at x: lam (dJ/dx_{k+1}) becomes dJ/dx_k; gu gets
-// dJ/du through this step.
-__device__ __forceinline__ void rk4_adjoint(const RefineParams& R, const float (&x)[12], const float (&u)[4],
-                                            float (&lam)[12], float (&gu)[4]) {
+// One RK4 stage as the adjoint needs it: the sine/cosine of the stage state's
+// angles (and 1 / cos(theta)) and its body rates.
+constexpr int STAGE_WORDS = 10;
+
+__device__ __forceinline__ void put_stage(float* w, const Trig& T, const float (&x)[12]) {
+    w[0] = T.sphi;
+    w[1] = T.cphi;
+    w[2] = T.sth;
+    w[3] = T.cth;
+    w[4] = T.spsi;
+    w[5] = T.cpsi;
+    w[6] = T.ic;
+    w[7] = x[9];
+    w[8] = x[10];
+    w[9] = x[11];
+}
+
+// rk4_step() that also writes its four stages to rec[4 * STAGE_WORDS] (lane 0)
+__device__ __forceinline__ void rk4_step_rec(const RefineParams& R, float (&x)[12], const float (&u)[4], float* rec,
+                                             bool writer) {
     const float h = R.h;
-    float k[12], x2[12], x3[12], x4[12];
-    quad_f(R, x, u, k);
+    float k[12], acc[12], xs[12];
+    Trig T = trig_of(x);
+    if (writer) put_stage(rec, T, x);
+    quad_f_t(R, T, x, u, k);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) x2[i] = x[i] + 0.5f * h * k[i];
-    quad_f(R, x2, u, k);
+    for (int i = 0; i < 12; ++i) {
+        acc[i] = k[i];
+        xs[i] = x[i] + 0.5f * h * k[i];
+    }
+    T = trig_of(xs);
+    if (writer) put_stage(rec + STAGE_WORDS, T, xs);
+    quad_f_t(R, T, xs, u, k);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) x3[i] = x[i] + 0.5f * h * k[i];
-    quad_f(R, x3, u, k);
+    for (int i = 0; i < 12; ++i) {
+        acc[i] += 2.0f * k[i];
+        xs[i] = x[i] + 0.5f * h * k[i];
+    }
+    T = trig_of(xs);
+    if (writer) put_stage(rec + 2 * STAGE_WORDS, T, xs);
+    quad_f_t(R, T, xs, u, k);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) x4[i] = x[i] + h * k[i];
-    // x_{k+1} = x + h/6 (k1 + 2 k2 + 2 k3 + k4)
+    for (int i = 0; i < 12; ++i) {
+        acc[i] += 2.0f * k[i];
+        xs[i] = x[i] + h * k[i];
+    }
+    T = trig_of(xs);
+    if (writer) put_stage(rec + 3 * STAGE_WORDS, T, xs);
+    quad_f_t(R, T, xs, u, k);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) x[i] += (h / 6.0f) * (acc[i] + k[i]);
+}
+
+__device__ __forceinline__ void vjp_stage(const RefineParams& R, const float* w, const float (&u)[4],
+                                          const float (&a)[12], float (&gx)[12], float (&gu)[4]) {
+    Trig T;
+    T.sphi = w[0];
+    T.cphi = w[1];
+    T.sth = w[2];
+    T.cth = w[3];
+    T.spsi = w[4];
+    T.cpsi = w[5];
+    T.ic = w[6];
+    quad_vjp_t(R, T, w[7], w[8], w[9], u, a, gx, gu);
+}
+
+// Adjoint of one RK4 step: lam (dJ/dx_{k+1}) becomes dJ/dx_k; gu gets dJ/du
+// through this step.  The four stages come from rk4_step_rec(), so no stage
+// is re-evaluated on the serial chain of the backward pass.
+__device__ __forceinline__ void rk4_adjoint_rec(const RefineParams& R, const float* rec, const float (&u)[4],
+                                                float (&lam)[12], float (&gu)[4]) {
+    const float h = R.h;
     float ax[12], ak[12], g[12], gus[4];
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
         ax[i] = lam[i];
         ak[i] = (h / 6.0f) * lam[i];  // adjoint of k4
     }
-    quad_vjp(R, x4, u, ak, g, gus);  // k4 = f(x + h k3)
+    vjp_stage(R, rec + 3 * STAGE_WORDS, u, ak, g, gus);  // k4 = f(x + h k3)
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
         ax[i] += g[i];
@@ -172,7 +233,7 @@ __device__ __forceinline__ void rk4_adjoint(const RefineParams& R, const float (
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
-    quad_vjp(R, x3, u, ak, g, gus);  // k3 = f(x + h/2 k2)
+    vjp_stage(R, rec + 2 * STAGE_WORDS, u, ak, g, gus);  // k3 = f(x + h/2 k2)
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
         ax[i] += g[i];
@@ -180,7 +241,7 @@ __device__ __forceinline__ void rk4_adjoint(const RefineParams& R, const float (
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
-    quad_vjp(R, x2, u, ak, g, gus);  // k2 = f(x + h/2 k1)
+    vjp_stage(R, rec + STAGE_WORDS, u, ak, g, gus);  // k2 = f(x + h/2 k1)
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
         ax[i] += g[i];
@@ -188,7 +249,7 @@ __device__ __forceinline__ void rk4_adjoint(const RefineParams& R, const float (
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
-    quad_vjp(R, x, u, ak, g, gus);  // k1 = f(x)
+    vjp_stage(R, rec, u, ak, g, gus);  // k1 = f(x)
 #pragma unroll
     for (int i = 0; i < 12; ++i) lam[i] = ax[i] + g[i];
 #pragma unroll
@@ -606,8 +667,9 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_forward(RefineParams 
 // ---------------------------------------------------------------------------
 // backward: dJ/du by the adjoint recursion, interval by interval
 // ---------------------------------------------------------------------------
-// per warp: the interval's states, segment ids and penalty gradients
-constexpr int BWD_WARP_FLOATS = (REFINE_CKPT_STEPS + 1) * 12 + REFINE_CKPT_STEPS + 3 * REFINE_CKPT_STEPS;
+// per warp: the interval's states, segment ids, penalty gradients and RK4 stages
+constexpr int BWD_WARP_FLOATS =
+    (REFINE_CKPT_STEPS + 1) * 12 + REFINE_CKPT_STEPS + 3 * REFINE_CKPT_STEPS + 4 * STAGE_WORDS * REFINE_CKPT_STEPS;
 
 __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams R) {
     extern __shared__ float smem[];
@@ -618,6 +680,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
     float* xs = smem + 6 * R.n_obs + warp * BWD_WARP_FLOATS;
     int* seg_of = reinterpret_cast<int*>(xs + (REFINE_CKPT_STEPS + 1) * 12);
     float* pg = xs + (REFINE_CKPT_STEPS + 1) * 12 + REFINE_CKPT_STEPS;
+    float* stages = pg + 3 * REFINE_CKPT_STEPS;  // [step][4 stages][STAGE_WORDS]
     const int64_t slot = (int64_t)blockIdx.x * ADJ_WARPS + warp;
     if (slot >= R.count) return;
     const int64_t tr = R.order ? R.order[slot] : slot;
@@ -669,7 +732,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
             for (int i = 0; i < 12; ++i)
                 if (lane == i) xs[t * 12 + i] = x[i];
             if (lane == 0) seg_of[t] = s;
-            rk4_step(R, x, u);
+            rk4_step_rec(R, x, u, stages + t * 4 * STAGE_WORDS, lane == 0);
             ++j;
         }
 #pragma unroll
@@ -707,10 +770,7 @@ __global__ void __launch_bounds__(ADJ_WARPS * 32) k_refine_backward(RefineParams
                 cur_seg = sk;
                 load_u(R, tr, sk, u);
             }
-            float xk[12];
-#pragma unroll
-            for (int i = 0; i < 12; ++i) xk[i] = xs[t * 12 + i];
-            rk4_adjoint(R, xk, u, lam, gu);
+            rk4_adjoint_rec(R, stages + t * 4 * STAGE_WORDS, u, lam, gu);
         }
         __syncwarp();
     }
