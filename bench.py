@@ -540,12 +540,16 @@ def run_kpx(args):
     achieved = (ops_step / max(1, iters_done)) / (prop_launch_ms / 1e3) / 1e12 if prop_ms > 0 else 0.0
     kernel, launch_ms = "k_propagate", prop_launch_ms
     traffic = PROPAGATE_DRAM_BYTES.get(args.workload)
+    bound_note = "k_propagate is bound by instruction issue (FP32, SFU and compare work of the rollouts)"
     if fused and fused_iters == iters_done and graph_launches:
         # every iteration ran in the fused kernel: it is the step (the reset
         # kernel aside), so its time per launch comes from the timed region
         kernel, launch_ms = "k_fused (whole iterations, one cluster)", ms / args.steps / graph_launches
         achieved = ops_step / (ms / args.steps / 1e3) / 1e12
         traffic = FUSED_DRAM_BYTES.get(args.workload)
+        bound_note = ("k_fused runs each iteration on one thread-block cluster: its time is the iteration's "
+                      "dependent chain (the longest rollout, then the phases' cluster barriers), so the ALU "
+                      "fraction below measures occupancy of the chip, not the kernel's distance from its bound")
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -604,7 +608,8 @@ def run_kpx(args):
                        "integration_steps_per_step": steps_per_step, "box_tests_per_step": tests_per_step,
                        "tree_nodes": int(st["n_nodes"]), "solution_cost": (None if math.isinf(st["best_cost"])
                                                                           else float(st["best_cost"]))},
-            "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "roofline": {"bound": "alu", "bound_note": bound_note, "kernel": kernel, "achieved": achieved,
+                         "peak": peak,
                          "unit": "TFLOP/s", "frac": achieved / peak if peak else 0.0,
                          "traffic": traffic,
                          "traffic_note": "DRAM bytes per launch of this kernel (ncu capture, profiles/); the "

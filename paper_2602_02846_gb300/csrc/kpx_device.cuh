@@ -208,13 +208,21 @@ __device__ __forceinline__ void step(const DevParams& P, float (&x)[Dims<DYN>::n
 // closed workspace box, and no closed obstacle box containing the position.
 // NaN fails every comparison and is therefore invalid.
 // --------------------------------------------------------------------------
-template <int N>
+// SYM: every non-position state bound is symmetric (x_lo[d] = -x_hi[d],
+// infinities included, checked on the host), so x_lo[d] <= x <= x_hi[d] is
+// exactly |x| <= x_hi[d] (NaN fails both forms): one comparison, not two.
+template <int N, bool SYM = false>
 __device__ __forceinline__ bool bounds_ok(const DevParams& P, const float (&x)[N]) {
     bool ok = true;
 #pragma unroll
     for (int a = 0; a < 3; ++a) ok &= (x[a] >= P.pos_lo[a]) & (x[a] <= P.pos_hi[a]);  // workspace and bounds
 #pragma unroll
-    for (int d = 3; d < N; ++d) ok &= (x[d] >= P.x_lo[d]) & (x[d] <= P.x_hi[d]);
+    for (int d = 3; d < N; ++d) {
+        if constexpr (SYM)
+            ok &= fabsf(x[d]) <= P.x_hi[d];
+        else
+            ok &= (x[d] >= P.x_lo[d]) & (x[d] <= P.x_hi[d]);
+    }
     return ok;
 }
 
@@ -502,10 +510,10 @@ struct LaneRollout {
 
     // One step; returns whether the new point is valid (bounds, and the
     // obstacles when OBST).
-    template <bool OBST, bool SMEM = false>
+    template <bool OBST, bool SMEM = false, bool SYM = false>
     __device__ __forceinline__ bool advance_in(const DevParams& P, const GridView& G, uint32_t& tests) {
         integrate(P);
-        if (!bounds_ok(P, x)) return false;
+        if (!bounds_ok<n, SYM>(P, x)) return false;
         if (OBST && hits_obstacle_in<SMEM>(P, G, x[0], x[1], x[2], tests)) return false;
         return true;
     }

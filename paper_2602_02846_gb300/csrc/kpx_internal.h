@@ -56,6 +56,7 @@ struct DevParams {
     float inv_J[3], J[3];
     float dJ[3];                 // J[2] - J[1], J[0] - J[2], J[1] - J[0] (FP32, as the device would round them)
     int32_t iso_inertia;         // quadcopter: J[0] = J[1] = J[2] exactly (omega' = tau / J)
+    int32_t sym_bounds;          // x_lo[d] = -x_hi[d] for every state component d >= 3 (bounds_ok<SYM>)
     float pos_lo[3], pos_hi[3];  // the workspace box intersected with the state bounds of x, y, z
     int32_t n_axes;
     int32_t ax_dim[8], ax_bins[8], ax_wrap[8];
@@ -180,6 +181,9 @@ inline void fill_dynamics(DevParams& P, const kpx_dynamics* dyn) {
         P.x_lo[i] = i < n ? dyn->x_lo[i] : -__builtin_huge_valf();
         P.x_hi[i] = i < n ? dyn->x_hi[i] : __builtin_huge_valf();
     }
+    P.sym_bounds = 1;
+    for (int i = 3; i < n; ++i)
+        if (!(P.x_lo[i] == -P.x_hi[i])) P.sym_bounds = 0;  // a NaN bound is not symmetric
     if (dyn->kind == KPX_QUAD12) {
         P.mg = dyn->param[0] * dyn->param[1];
         P.inv_mg = 1.0f / P.mg;

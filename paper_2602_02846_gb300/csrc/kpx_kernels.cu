@@ -206,7 +206,7 @@ struct PropOccupancy {
     static constexpr int blocks = DYN == KPX_QUAD12 ? KPX_QUAD_MIN_BLOCKS : 4;
 };
 
-template <int DYN, int INTEG>
+template <int DYN, int INTEG, bool SYM>
 __global__ void __launch_bounds__(PROP_THREADS, PropOccupancy<DYN>::blocks)
     k_propagate(DevParams P, kpx_debug_records rec, int rec_on) {
     kpx_device_header* H = P.hdr;
@@ -220,8 +220,8 @@ __global__ void __launch_bounds__(PROP_THREADS, PropOccupancy<DYN>::blocks)
     int64_t chunk = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     uint32_t steps = 0, tests = 0, n_valid = 0;
     while (chunk * 32 < n_slots) {
-        propagate_chunk<DYN, INTEG>(P, n_slots, lam, iter, va, early, chunk, rec, rec_on, steps, tests, n_valid,
-                                    P.slot_order);
+        propagate_chunk<DYN, INTEG, SYM>(P, n_slots, lam, iter, va, early, chunk, rec, rec_on, steps, tests, n_valid,
+                                         P.slot_order);
         unsigned long long t = 0ull;
         if ((threadIdx.x & 31) == 0) t = atomicAdd((unsigned long long*)&H->prop_ticket, 1ull);
         chunk = n_warps + (int64_t)__shfl_sync(FULL, t, 0);
@@ -406,27 +406,27 @@ int persistent_blocks(int64_t work_blocks, int per_sm) {
     return (int)(g < 1 ? 1 : g);
 }
 
-template <int DYN, int INTEG>
+template <int DYN, int INTEG, bool SYM>
 int propagate_blocks_per_sm() {
     static int per_sm = 0;
     if (!per_sm) {
         int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_propagate<DYN, INTEG>, PROP_THREADS, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_propagate<DYN, INTEG, SYM>, PROP_THREADS, 0);
         per_sm = v < 1 ? 1 : v;
     }
     return per_sm;
 }
 
 template <int DYN, int INTEG>
-int propagate_occupancy_t(const DevParams&, int) {
-    return propagate_blocks_per_sm<DYN, INTEG>();
+int propagate_occupancy_t(const DevParams& P, int) {
+    return P.sym_bounds ? propagate_blocks_per_sm<DYN, INTEG, true>() : propagate_blocks_per_sm<DYN, INTEG, false>();
 }
 
 int propagate_occupancy(const DevParams& P) { KPX_DISPATCH(propagate_occupancy_t, P, 0); }
 
 template <int DYN, int INTEG>
 cudaError_t launch_propagate_t(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s) {
-    const int fit = propagate_blocks_per_sm<DYN, INTEG>();
+    const int fit = propagate_occupancy_t<DYN, INTEG>(P, 0);
     const int per_sm = P.prop_bps > 0 && P.prop_bps < fit ? P.prop_bps : fit;
     const int grid = persistent_blocks((P.slot_cap + PROP_THREADS - 1) / PROP_THREADS, per_sm);
     kpx_debug_records r{};
@@ -435,7 +435,10 @@ cudaError_t launch_propagate_t(const DevParams& P, const kpx_debug_records* rec,
         r = *rec;
         on = 1;
     }
-    k_propagate<DYN, INTEG><<<grid, PROP_THREADS, 0, s>>>(P, r, on);
+    if (P.sym_bounds)
+        k_propagate<DYN, INTEG, true><<<grid, PROP_THREADS, 0, s>>>(P, r, on);
+    else
+        k_propagate<DYN, INTEG, false><<<grid, PROP_THREADS, 0, s>>>(P, r, on);
     return cudaGetLastError();
 }
 

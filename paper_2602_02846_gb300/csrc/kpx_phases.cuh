@@ -239,7 +239,8 @@ struct Candidate {
 };
 
 // G: where the obstacle grid is read (SMEM: a shared-memory copy)
-template <int DYN, int INTEG, bool SMEM = false>
+// SYM: the state bounds are symmetric (bounds_ok's one-comparison form)
+template <int DYN, int INTEG, bool SMEM = false, bool SYM = false>
 __device__ __forceinline__ void roll_candidate(const DevParams& P, const GridView& G, int lam, uint32_t iter,
                                                const int32_t* va, bool early, int64_t slot, Candidate<DYN, INTEG>& C,
                                                uint32_t& steps, uint32_t& tests) {
@@ -248,8 +249,8 @@ __device__ __forceinline__ void roll_candidate(const DevParams& P, const GridVie
     bool ok = true;
     while (ok && C.R.k < C.R.K) {
         ++steps;
-        ok = early ? C.R.template advance_in<false, SMEM>(P, G, tests)
-                   : C.R.template advance_in<true, SMEM>(P, G, tests);
+        ok = early ? C.R.template advance_in<false, SMEM, SYM>(P, G, tests)
+                   : C.R.template advance_in<true, SMEM, SYM>(P, G, tests);
     }
     C.r = -1;
     C.c = 0.0f;
@@ -416,7 +417,7 @@ __device__ __forceinline__ void roll_candidate_coop(const DevParams& P, const Gr
 // position of its ORDER_CHUNK-slot chunk sorted by K, so that a warp's lanes
 // run similar step counts.  The slots past n_slots sort last in the final
 // chunk, so a position below n_slots always names a live slot.
-template <int DYN, int INTEG>
+template <int DYN, int INTEG, bool SYM = false>
 __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_slots, int lam, uint32_t iter,
                                                 const int32_t* va, bool early, int64_t chunk,
                                                 const kpx_debug_records& rec, int rec_on, uint32_t& steps,
@@ -426,7 +427,8 @@ __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_sl
     if (pos >= n_slots) return;
     const int64_t slot = order ? (pos & ~(int64_t)(ORDER_CHUNK - 1)) + order[pos] : pos;
     Candidate<DYN, INTEG> C;
-    roll_candidate<DYN, INTEG>(P, GridView{P.cell_start, P.cell_box}, lam, iter, va, early, slot, C, steps, tests);
+    roll_candidate<DYN, INTEG, false, SYM>(P, GridView{P.cell_start, P.cell_box}, lam, iter, va, early, slot, C, steps,
+                                           tests);
     n_valid += C.ok ? 1u : 0u;
     if (rec_on && slot < rec.capacity) {
         rec.valid[slot] = C.ok ? 1 : 0;
