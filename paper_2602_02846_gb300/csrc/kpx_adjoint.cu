@@ -41,12 +41,16 @@ struct Trig {
     float sphi, cphi, sth, cth, spsi, cpsi, ic;  // ic = 1 / cos(theta)
 };
 
+// Roll and pitch of a quadcopter trajectory stay within a few radians, where
+// the hardware sine and cosine need no range reduction (absolute error grows
+// like |angle| 1e-7); yaw keeps the reduction.  1 / cos(theta) is the
+// hardware's approximate reciprocal (about 1 ulp).
 __device__ __forceinline__ Trig trig_of(const float (&x)[12]) {
     Trig T;
-    fast_sincos(x[3], T.sphi, T.cphi);
-    fast_sincos(x[4], T.sth, T.cth);
+    __sincosf(x[3], &T.sphi, &T.cphi);
+    __sincosf(x[4], &T.sth, &T.cth);
     fast_sincos(x[5], T.spsi, T.cpsi);
-    T.ic = __frcp_rn(T.cth);
+    T.ic = __fdividef(1.0f, T.cth);
     return T;
 }
 

@@ -485,8 +485,10 @@ struct LaneRollout {
 
     __device__ __forceinline__ void start(const DevParams& P, const int32_t* va, int lam, uint32_t iter,
                                           int64_t slot) {
-        const int j = (int)(slot / lam);
-        const int s = (int)(slot - (int64_t)j * lam);
+        // slot < 2^32 (create checks tree_cap + slot capacity): 32-bit division
+        const uint32_t su = (uint32_t)slot;
+        const int j = (int)(su / (uint32_t)lam);
+        const int s = (int)(su - (uint32_t)j * (uint32_t)lam);
         node = va[j];
 #pragma unroll
         for (int d = 0; d < n; ++d) x[d] = P.x[(int64_t)d * P.N + node];

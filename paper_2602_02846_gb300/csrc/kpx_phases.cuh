@@ -210,8 +210,9 @@ __device__ __forceinline__ void order_chunk(const DevParams& P, const int32_t* v
         const uint32_t off = (uint32_t)(lane + 32 * e);
         const int64_t slot = c * ORDER_CHUNK + off;
         if (slot < n_slots) {
-            const int j = (int)(slot / lam);
-            const int s = (int)(slot - (int64_t)j * lam);
+            const uint32_t su = (uint32_t)slot;  // < 2^32, as in LaneRollout::start
+            const int j = (int)(su / (uint32_t)lam);
+            const int s = (int)(su - (uint32_t)j * (uint32_t)lam);
             v[e] = ((uint32_t)sample_steps<M>(P, iter, (uint32_t)va[j], (uint32_t)s) << 7) | off;  // K < 2^16
         } else {
             v[e] = 0xFFFFFF80u | off;
