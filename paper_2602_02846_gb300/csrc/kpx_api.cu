@@ -181,6 +181,7 @@ Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs
     L.win_mask = seg((size_t)L.mask_words * sizeof(uint32_t));
     L.win_tiles = seg((size_t)L.n_win_tiles * sizeof(uint64_t));
     L.prune_tiles = seg((size_t)L.n_prune_tiles * sizeof(uint64_t));
+    L.clean = seg((size_t)N * sizeof(uint32_t));
     L.slot_order = seg((size_t)((L.slot_cap + ORDER_CHUNK - 1) / ORDER_CHUNK) * ORDER_CHUNK);
     L.path = seg((size_t)N * sizeof(int32_t));
     L.traj = seg((size_t)L.traj_rows * (n + m + 1) * sizeof(float));
@@ -293,6 +294,7 @@ void bind_pointers(kpx_planner* p) {
     P.win_mask = reinterpret_cast<uint32_t*>(b + L.win_mask);
     P.win_tiles = reinterpret_cast<uint64_t*>(b + L.win_tiles);
     P.prune_tiles = reinterpret_cast<uint64_t*>(b + L.prune_tiles);
+    P.clean = reinterpret_cast<uint32_t*>(b + L.clean);
     P.slot_order = (P.flags & KPX_FLAG_NO_SLOT_ORDER) ? nullptr : reinterpret_cast<uint8_t*>(b + L.slot_order);
     P.path = reinterpret_cast<int32_t*>(b + L.path);
     P.traj = reinterpret_cast<float*>(b + L.traj);

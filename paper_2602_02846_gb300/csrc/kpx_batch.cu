@@ -308,7 +308,7 @@ cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const
         e = [&]() -> cudaError_t { KPX_CLASS_DISPATCH(launch_b_append_t, cls_kind[c], bp, s); }();
     }
     if (e != cudaSuccess) return e;
-    k_b_prune<<<b_sm_count() * 4, PRUNE_THREADS, 0, s>>>(base);
+    k_b_prune<<<b_sm_count() * 6, PRUNE_THREADS, 0, s>>>(base);  // 40 registers: 6 blocks per SM
     k_b_end<<<(base.B + 255) / 256, 256, 0, s>>>(base);
     return cudaGetLastError();
 }

@@ -104,6 +104,7 @@ struct DevParams {
     int32_t* box_cells;   // [6*n_obs]: per box cell range lo x,y,z, hi x,y,z
     int32_t* cell_start;  // [n_cells + 1]: CSR offsets into cell_box
     float4* cell_box;     // [2*grid_cap]: boxes of each cell, in box order
+    uint32_t* clean;      // [N]: the epoch of the prune that found the node's strict ancestors not dominated
     uint8_t* slot_order;  // [slot_cap rounded up to ORDER_CHUNK]: per chunk, the slots (offsets in the chunk)
                           // in ascending K; null: slots in index order
     int32_t* path;        // [N] node ids root -> goal
@@ -129,8 +130,8 @@ __host__ __device__ inline int grid_cell(float c, float lo, float inv, int n) {
 // Workspace layout (byte offsets from the workspace base).
 struct Layout {
     size_t hdr, obs, box_cells, cell_start, cell_box, x, u, K, parent, key, region, set, icount;
-    size_t region_key, region_snap, region_owner, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, slot_order,
-        path, traj;
+    size_t region_key, region_snap, region_owner, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, clean,
+        slot_order, path, traj;
     size_t total;
     int32_t va_cap;
     int64_t slot_cap, mask_words;

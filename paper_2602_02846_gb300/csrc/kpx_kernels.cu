@@ -52,6 +52,7 @@ __global__ void k_init(DevParams P, int first_time) {
     if (first_time) {
         for (int64_t t = tid; t < P.n_win_tiles; t += stride) P.win_tiles[t] = 0ull;
         for (int64_t t = tid; t < P.n_prune_tiles; t += stride) P.prune_tiles[t] = 0ull;
+        for (int64_t i = tid; i < P.N; i += stride) P.clean[i] = 0u;  // epoch 0 is never current
     }
     if (tid == 0) {
         kpx_device_header* H = P.hdr;
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(128) k_append(DevParams P) {
         append_winner<DYN, INTEG>(P, H, w, kept, n_old, lam, iter, va);
 }
 
-__global__ void __launch_bounds__(PRUNE_THREADS) k_prune(DevParams P) {
+__global__ void __launch_bounds__(PRUNE_THREADS, 8) k_prune(DevParams P) {
     __shared__ uint32_t s_tile, s_prefix;
     __shared__ int32_t s_parent[PRUNE_TILE];
     __shared__ uint8_t s_set[PRUNE_TILE];
@@ -503,7 +504,9 @@ cudaError_t launch_scan(const DevParams& P, cudaStream_t s) {
 cudaError_t launch_append(const DevParams& P, cudaStream_t s) { KPX_DISPATCH(launch_append_t, P, s); }
 
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
-    k_prune<<<persistent_blocks(P.n_prune_tiles, 4), PRUNE_THREADS, 0, s>>>(P);
+    // a tile's time is its deepest ancestor walk: as many tiles in flight as fit
+    // (32 registers and 6 KB of shared memory a block: 8 blocks per SM)
+    k_prune<<<persistent_blocks(P.n_prune_tiles, 8), PRUNE_THREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 

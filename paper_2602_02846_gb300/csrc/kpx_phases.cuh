@@ -673,8 +673,14 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
         int nst = sb & SET_MASK;
         bool anc = (sb & SET_ANC) != 0;
         if (!prune_rules_123(sb, i_max, ic, nst)) {
-            // rule 4: whether a strict ancestor is dominated (the ANC flag
-            // memoises a positive answer; it is monotone)
+            // rule 4: whether a strict ancestor is dominated.  The ANC flag
+            // memoises a positive answer (it is monotone); clean[] memoises a
+            // negative one for this prune only: a walk that finds no dominated
+            // strict ancestor stamps its node with the epoch, and a later walk
+            // stops at a stamped ancestor that is not dominated itself.  The
+            // dominated bits do not change during prune, so a stamp seen in
+            // this epoch stays true; a stamp not yet visible only means a
+            // longer walk.
             if (!anc) {
                 int p = s_parent[k];
                 while (p >= tile0) {  // inside the tile: shared memory (a stale set byte
@@ -688,8 +694,13 @@ __device__ __forceinline__ void prune_tile(const DevParams& P, kpx_device_header
                 }
                 for (; !anc && p >= 0; p = P.parent[p]) {
                     const uint8_t sp = *(volatile const uint8_t*)&P.set[p];
-                    if (sp & (SET_DOM | SET_ANC)) anc = true;
+                    if (sp & (SET_DOM | SET_ANC)) {
+                        anc = true;
+                    } else if (*(volatile const uint32_t*)&P.clean[p] == epoch) {
+                        break;  // p's strict ancestors are clean, and p is not dominated
+                    }
                 }
+                if (!anc) P.clean[i] = epoch;
             }
             if (anc) nst = SET_I;
         }
