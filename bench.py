@@ -56,7 +56,7 @@ SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
 FUSED_DRAM_BYTES = {
-    "dubins6_forest300": 236800,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
+    "dubins6_forest300": 224768,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
 }
 PROPAGATE_DRAM_BYTES = {
     "quad12_building1000": 6721024,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
@@ -81,8 +81,8 @@ def update_row_bytes(n, m):
 # the ncu captures in profiles/ (each kernel from a cold L2, as ncu flushes
 # caches between captured kernels): workload -> (iteration, bytes)
 UPDATE_DRAM_BYTES = {
-    "quad12_building1000": (100, 3561472),   # profiles/update_quad12_building1000.md
-    "quad12_clutter1000": (300, 24233984),   # profiles/update_quad12_clutter1000.md
+    "quad12_building1000": (100, 3569664),   # profiles/update_quad12_building1000.md
+    "quad12_clutter1000": (300, 24210688),   # profiles/update_quad12_clutter1000.md
 }
 
 

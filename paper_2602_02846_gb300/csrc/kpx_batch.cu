@@ -298,7 +298,7 @@ cudaError_t launch_batch_iteration(const BatchParams& base, int n_classes, const
     }
     if (e != cudaSuccess) return e;
     k_b_mark<<<dim3(8, base.B), 256, 0, s>>>(base);
-    k_b_scan<<<b_sm_count() * 2, WIN_THREADS, 0, s>>>(base);
+    k_b_scan<<<b_sm_count() * 8, WIN_THREADS, 0, s>>>(base);
     k_b_prefix<<<1, 1024, 0, s>>>(base);
     for (int c = 0; c < n_classes && e == cudaSuccess; ++c) {
         BatchParams bp = base;

@@ -492,12 +492,13 @@ cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, c
 }
 
 cudaError_t launch_mark(const DevParams& P, cudaStream_t s) {
-    k_mark<<<persistent_blocks((P.R + 255) / 256, 4), 256, 0, s>>>(P);
+    k_mark<<<persistent_blocks((P.R + 255) / 256, 8), 256, 0, s>>>(P);
     return cudaGetLastError();
 }
 
+// every tile of a large iteration in flight at once (31 registers: 8 blocks per SM)
 cudaError_t launch_scan(const DevParams& P, cudaStream_t s) {
-    k_scan<<<persistent_blocks(P.n_win_tiles, 2), WIN_THREADS, 0, s>>>(P);
+    k_scan<<<persistent_blocks(P.n_win_tiles, 8), WIN_THREADS, 0, s>>>(P);
     return cudaGetLastError();
 }
 

@@ -486,13 +486,20 @@ __device__ __forceinline__ void mark_region(const DevParams& P, int r) {
 __device__ __forceinline__ void scan_tile(const DevParams& P, kpx_device_header* H, uint32_t tile, int64_t n_tiles,
                                           int64_t live_words, uint32_t* s_warp, uint32_t& s_prefix) {
     const int64_t w0 = (int64_t)tile * WIN_TILE_WORDS + (int64_t)threadIdx.x * WIN_WORDS_PER_THREAD;
+    static_assert(WIN_WORDS_PER_THREAD == 8, "two 16-byte loads a thread");
     uint32_t w[WIN_WORDS_PER_THREAD];
     uint32_t cnt = 0;
+    if (w0 + WIN_WORDS_PER_THREAD <= live_words) {  // w0 is a multiple of 8 words: 32-byte aligned
+        const uint4 a = *reinterpret_cast<const uint4*>(P.win_mask + w0);
+        const uint4 b = *reinterpret_cast<const uint4*>(P.win_mask + w0 + 4);
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    } else {
 #pragma unroll
-    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) {
-        w[i] = (w0 + i < live_words) ? P.win_mask[w0 + i] : 0u;
-        cnt += __popc(w[i]);
+        for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) w[i] = (w0 + i < live_words) ? P.win_mask[w0 + i] : 0u;
     }
+#pragma unroll
+    for (int i = 0; i < WIN_WORDS_PER_THREAD; ++i) cnt += __popc(w[i]);
     uint32_t agg;
     const uint32_t excl = block_exclusive_scan<WIN_THREADS>(cnt, agg, s_warp);
     if (threadIdx.x == 0) {
