@@ -196,7 +196,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="batch workloads: keep the default launch choices")
     ap.add_argument("--no-fused", action="store_true",
-                    help="run every iteration as the seven phase kernels (KPX_FLAG_NO_FUSED; same results)")
+                    help="run every iteration as the phase kernels (KPX_FLAG_NO_FUSED; same results)")
     ap.add_argument("--no-slot-order", action="store_true",
                     help="propagate slots in index order, not sorted by step count (KPX_FLAG_NO_SLOT_ORDER; "
                          "same results)")
@@ -467,8 +467,9 @@ def run_kpx(args):
     value = valid_all / (ms_max / 1e3)
 
     # launches of one step (kpx_graph_info): one graph launch per kpx_iterate
-    # call, holding 1 fused launch plus 7 phase launches per iteration the
-    # fused kernel left to the loop; 7 per iteration without the fused kernel
+    # call, holding 1 fused launch plus 8 kernel launches per iteration the
+    # fused kernel left to the loop (begin, propagate, stage, mark, scan, append,
+    # prune, end); 8 per iteration without the fused kernel
     max_g, fused = pl.graph_info()
     plan = kpx.Planner.launch_plan(iters, max_g) if max_g else [1] * iters
     pl.reset()
@@ -477,9 +478,9 @@ def run_kpx(args):
     fused_iters = int(pl.header().fused_iterations)
     graph_launches = len(plan) if max_g else 0
     if fused:
-        launches_per_step = 1 + len(plan) + 7 * (iters - fused_iters)  # k_init (reset) first
+        launches_per_step = 1 + len(plan) + 8 * (iters - fused_iters)  # k_init (reset) first
     else:
-        launches_per_step = 1 + 7 * iters
+        launches_per_step = 1 + 8 * iters
 
     # per-phase device time over one step (same launches, CUDA events on the
     # planner's stream; nothing synchronises inside the pass, so the host

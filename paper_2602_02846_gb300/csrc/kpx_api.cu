@@ -18,6 +18,13 @@
 
 using namespace kpx;
 
+// The second stream and the two events with which a captured iteration forks
+// the winners' re-integration off the main chain and joins it again.
+struct SideBranch {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 struct kpx_planner {
     DevParams P;
     Layout L;
@@ -29,6 +36,7 @@ struct kpx_planner {
     int graph_state = 0;  // 0 not decided, 1 graph, -1 unavailable (plain launches)
     bool graph_fused = false;  // the graph starts with the fused kernel
     cudaStream_t capture_stream = nullptr;
+    SideBranch side;                       // used while capturing the loop body
     cudaGraph_t loop_graph = nullptr;      // kept: its count node is updated before each launch
     cudaGraphExec_t loop_exec = nullptr;
     cudaGraphNode_t count_node = nullptr;  // memset node: the launch's iteration count
@@ -182,6 +190,7 @@ Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs
     L.win_tiles = seg((size_t)L.n_win_tiles * sizeof(uint64_t));
     L.prune_tiles = seg((size_t)L.n_prune_tiles * sizeof(uint64_t));
     L.clean = seg((size_t)N * sizeof(uint32_t));
+    L.slot_region = seg((size_t)L.slot_cap * sizeof(int32_t));
     L.slot_order = seg((size_t)((L.slot_cap + ORDER_CHUNK - 1) / ORDER_CHUNK) * ORDER_CHUNK);
     L.path = seg((size_t)N * sizeof(int32_t));
     L.traj = seg((size_t)L.traj_rows * (n + m + 1) * sizeof(float));
@@ -295,6 +304,7 @@ void bind_pointers(kpx_planner* p) {
     P.win_tiles = reinterpret_cast<uint64_t*>(b + L.win_tiles);
     P.prune_tiles = reinterpret_cast<uint64_t*>(b + L.prune_tiles);
     P.clean = reinterpret_cast<uint32_t*>(b + L.clean);
+    P.slot_region = reinterpret_cast<int32_t*>(b + L.slot_region);
     P.slot_order = (P.flags & KPX_FLAG_NO_SLOT_ORDER) ? nullptr : reinterpret_cast<uint8_t*>(b + L.slot_order);
     P.path = reinterpret_cast<int32_t*>(b + L.path);
     P.traj = reinterpret_cast<float*>(b + L.traj);
@@ -307,13 +317,14 @@ kpx_status read_header(kpx_planner* p, kpx_device_header* h) {
     return KPX_OK;
 }
 
-// One iteration of the phase kernels (plain launches).
+// One iteration of the phase kernels (plain launches, one stream).
 cudaError_t enqueue_iteration(const DevParams& P, cudaStream_t s) {
     cudaError_t e = launch_begin(P, s);
     if (e == cudaSuccess) e = launch_propagate(P, nullptr, s);
     if (e == cudaSuccess) e = launch_mark(P, s);
     if (e == cudaSuccess) e = launch_scan(P, s);
     if (e == cudaSuccess) e = launch_append(P, s);
+    if (e == cudaSuccess) e = launch_stage(P, s);
     if (e == cudaSuccess) e = launch_prune(P, s);
     if (e == cudaSuccess) e = launch_end(P, s);
     return e;
@@ -331,13 +342,22 @@ constexpr int kLoopIterationsFused = 2;
 // One iteration of the phase kernels in the body of the graph's loop: it
 // runs only while iterations are owed, and its last kernel counts it off
 // graph_pending (the body's last iteration sets the loop's handle).
-cudaError_t enqueue_loop_iteration(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s) {
+// The kept winners' re-integration (stage) forks onto the side stream after
+// the winner scan and joins before the iteration's end, so that it runs
+// beside append and prune (which need no end state).
+cudaError_t enqueue_loop_iteration(const DevParams& P, cudaGraphConditionalHandle h, bool last, cudaStream_t s,
+                                   const SideBranch& side) {
     cudaError_t e = launch_begin(P, s, true);
     if (e == cudaSuccess) e = launch_propagate(P, nullptr, s);
     if (e == cudaSuccess) e = launch_mark(P, s);
     if (e == cudaSuccess) e = launch_scan(P, s);
+    if (e == cudaSuccess) e = cudaEventRecord(side.fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(side.stream, side.fork, 0);
+    if (e == cudaSuccess) e = launch_stage(P, side.stream);
+    if (e == cudaSuccess) e = cudaEventRecord(side.join, side.stream);
     if (e == cudaSuccess) e = launch_append(P, s);
     if (e == cudaSuccess) e = launch_prune(P, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, side.join, 0);
     if (e == cudaSuccess) e = launch_end_loop(P, h, last, s);
     return e;
 }
@@ -413,7 +433,7 @@ cudaError_t build_loop_graph(kpx_planner* p, bool fused) {
         if (e == cudaSuccess) {
             const int unroll = fused ? kLoopIterationsFused : kLoopIterations;
             for (int u = 0; u < unroll && le == cudaSuccess; ++u)
-                le = enqueue_loop_iteration(p->P, h, u == unroll - 1, p->capture_stream);
+                le = enqueue_loop_iteration(p->P, h, u == unroll - 1, p->capture_stream, p->side);
             cudaGraph_t out = nullptr;
             e = cudaStreamEndCapture(p->capture_stream, &out);
             if (le != cudaSuccess) e = le;
@@ -445,24 +465,39 @@ void drop_graphs(kpx_planner* p) {
 struct CaptureStreams {
     static constexpr int kDevices = 64;
     cudaStream_t s[kDevices] = {};
-    ~CaptureStreams() {
-        for (cudaStream_t x : s)
-            if (x) cudaStreamDestroy(x);  // fails harmlessly once the context is gone
+    SideBranch side[kDevices];
+    ~CaptureStreams() {  // each call fails harmlessly once the context is gone
+        for (int d = 0; d < kDevices; ++d) {
+            if (s[d]) cudaStreamDestroy(s[d]);
+            if (side[d].stream) cudaStreamDestroy(side[d].stream);
+            if (side[d].fork) cudaEventDestroy(side[d].fork);
+            if (side[d].join) cudaEventDestroy(side[d].join);
+        }
     }
 };
 
-cudaStream_t capture_stream_here() {
+// The capture stream and side branch of this host thread on the current
+// device (made on first use and kept); false when they cannot be made.
+bool capture_resources_here(cudaStream_t* stream, SideBranch* side) {
     thread_local CaptureStreams streams;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= CaptureStreams::kDevices) {
         cudaGetLastError();
-        return nullptr;
+        return false;
     }
-    if (!streams.s[dev] && cudaStreamCreateWithFlags(&streams.s[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    SideBranch& b = streams.side[dev];
+    bool ok = true;
+    if (!streams.s[dev]) ok = cudaStreamCreateWithFlags(&streams.s[dev], cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && !b.stream) ok = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok && !b.fork) ok = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && !b.join) ok = cudaEventCreateWithFlags(&b.join, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
         cudaGetLastError();
-        streams.s[dev] = nullptr;
+        return false;
     }
-    return streams.s[dev];
+    *stream = streams.s[dev];
+    *side = b;
+    return true;
 }
 
 // Decides once how kpx_iterate launches: a graph that starts with the fused
@@ -475,8 +510,10 @@ void ensure_graphs(kpx_planner* p) {
     prepare_launches(p->P);
     p->graph_fused = !(p->P.flags & KPX_FLAG_NO_FUSED) && fused_cluster_size(p->P) > 0;
     cudaGetLastError();
-    p->capture_stream = capture_stream_here();
-    if (!p->capture_stream) return;
+    if (!capture_resources_here(&p->capture_stream, &p->side)) {
+        p->capture_stream = nullptr;
+        return;
+    }
     p->graph_state = 1;
 }
 
@@ -502,7 +539,10 @@ kpx_status run_phase(kpx_planner* p, int phase, const kpx_debug_records* rec) {
         case KPX_PHASE_PROPAGATE: e = launch_propagate(p->P, rec, p->stream); break;
         case KPX_PHASE_MARK: e = launch_mark(p->P, p->stream); break;
         case KPX_PHASE_SCAN: e = launch_scan(p->P, p->stream); break;
-        case KPX_PHASE_APPEND: e = launch_append(p->P, p->stream); break;
+        case KPX_PHASE_APPEND:  // both halves of UpdateTree
+            e = launch_append(p->P, p->stream);
+            if (e == cudaSuccess) e = launch_stage(p->P, p->stream);
+            break;
         case KPX_PHASE_PRUNE: e = launch_prune(p->P, p->stream); break;
         case KPX_PHASE_END: e = launch_end(p->P, p->stream); break;
         default: return fail(p, KPX_E_INVALID, "unknown phase");

@@ -105,6 +105,7 @@ struct DevParams {
     int32_t* cell_start;  // [n_cells + 1]: CSR offsets into cell_box
     float4* cell_box;     // [2*grid_cap]: boxes of each cell, in box order
     uint32_t* clean;      // [N]: the epoch of the prune that found the node's strict ancestors not dominated
+    int32_t* slot_region; // [slot_cap]: region of a winning slot (written by mark)
     uint8_t* slot_order;  // [slot_cap rounded up to ORDER_CHUNK]: per chunk, the slots (offsets in the chunk)
                           // in ascending K; null: slots in index order
     int32_t* path;        // [N] node ids root -> goal
@@ -131,7 +132,7 @@ __host__ __device__ inline int grid_cell(float c, float lo, float inv, int n) {
 struct Layout {
     size_t hdr, obs, box_cells, cell_start, cell_box, x, u, K, parent, key, region, set, icount;
     size_t region_key, region_snap, region_owner, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, clean,
-        slot_order, path, traj;
+        slot_region, slot_order, path, traj;
     size_t total;
     int32_t va_cap;
     int64_t slot_cap, mask_words;
@@ -255,7 +256,10 @@ cudaError_t launch_begin(const DevParams& P, cudaStream_t s, bool loop = false);
 cudaError_t launch_propagate(const DevParams& P, const kpx_debug_records* rec, cudaStream_t s);
 cudaError_t launch_mark(const DevParams& P, cudaStream_t s);
 cudaError_t launch_scan(const DevParams& P, cudaStream_t s);
+// UpdateTree in two halves (kpx_phases.cuh): append (rows, keys, owners,
+// capacity rule) and stage (the kept winners' end states and the goal test)
 cudaError_t launch_append(const DevParams& P, cudaStream_t s);
+cudaError_t launch_stage(const DevParams& P, cudaStream_t s);
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s);
 cudaError_t launch_end(const DevParams& P, cudaStream_t s);
 // the end of an iteration in the loop body of a planner's graph: counts the

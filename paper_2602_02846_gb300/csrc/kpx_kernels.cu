@@ -8,8 +8,11 @@
 //   mark       V_U filter: a region whose key holds a candidate id marks
 //              that candidate's slot in a bitmask
 //   scan       winners ranked in ascending slot order (decoupled look-back)
-//   append     UpdateTree (Alg. 4): winners re-materialised from Philox and
-//              appended at n_nodes + rank; capacity rule; solution update
+//   append     UpdateTree (Alg. 4): winners appended at n_nodes + rank
+//              (everything but the end states); capacity rule
+//   stage      the kept winners re-materialised from Philox: their end
+//              states and the solution update (beside append and prune in
+//              the graphs)
 //   prune      PruneNodes (Alg. 3) over the pre-append tree, fused with the
 //              compaction of the next V_A list (Alg. 5)
 //   end        counters
@@ -269,7 +272,24 @@ __global__ void __launch_bounds__(128) k_append(DevParams P) {
     const uint32_t iter = (uint32_t)H->iter;
     const int32_t* va = va_current(P, H);
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < W; w += gridDim.x * blockDim.x)
-        append_winner<DYN, INTEG>(P, H, w, kept, n_old, lam, iter, va);
+        append_meta<DYN, INTEG>(P, H, w, kept, n_old, lam, iter, va);
+}
+
+// The kept winners' end states (one thread per winner, re-materialised) and
+// the solution update; in the planner's graphs beside append and prune.
+template <int DYN, int INTEG>
+__global__ void __launch_bounds__(128) k_stage(DevParams P) {
+    kpx_device_header* H = P.hdr;
+    if (!H->active) return;
+    const int W = H->n_win;
+    const int n_old = H->n_nodes;  // end_counters advances it only after both halves
+    const int room = P.N - n_old;
+    const int kept = W < room ? W : room;
+    const int lam = H->lambda;
+    const uint32_t iter = (uint32_t)H->iter;
+    const int32_t* va = va_current(P, H);
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < kept; w += gridDim.x * blockDim.x)
+        stage_winner<DYN, INTEG>(P, H, w, n_old, lam, iter, va);
 }
 
 __global__ void __launch_bounds__(PRUNE_THREADS, 8) k_prune(DevParams P) {
@@ -449,6 +469,12 @@ cudaError_t launch_append_t(const DevParams& P, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int DYN, int INTEG>
+cudaError_t launch_stage_t(const DevParams& P, cudaStream_t s) {
+    k_stage<DYN, INTEG><<<persistent_blocks((P.R + 127) / 128, 4), 128, 0, s>>>(P);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_init(const DevParams& P, bool first_time, cudaStream_t s) {
@@ -503,6 +529,8 @@ cudaError_t launch_scan(const DevParams& P, cudaStream_t s) {
 }
 
 cudaError_t launch_append(const DevParams& P, cudaStream_t s) { KPX_DISPATCH(launch_append_t, P, s); }
+
+cudaError_t launch_stage(const DevParams& P, cudaStream_t s) { KPX_DISPATCH(launch_stage_t, P, s); }
 
 cudaError_t launch_prune(const DevParams& P, cudaStream_t s) {
     // a tile's time is its deepest ancestor walk: as many tiles in flight as fit

@@ -476,6 +476,7 @@ __device__ __forceinline__ void mark_region(const DevParams& P, int r) {
         return;
     }
     atomicOr(&P.win_mask[slot >> 5], 1u << (slot & 31));
+    P.slot_region[slot] = r;
 }
 
 // ---------------------------------------------------------------------------
@@ -591,6 +592,80 @@ __device__ __forceinline__ void append_winner(const DevParams& P, kpx_device_hea
         return;
     }
     append_row<DYN, INTEG>(P, H, w, kept, n_old, Rw, c, r, P.region_owner[r]);
+}
+
+// UpdateTree split in two for the planner's graphs, which run the halves on
+// two branches after the winner scan:
+// - append_meta writes everything that needs no end state: the row's parent,
+//   control, step count, key, region and sets, the region's key and owner,
+//   the previous owner's dominated mark, and the capacity rule's restores.
+//   The winner's region comes from mark (slot_region), its cost from the
+//   region's key.  PruneNodes needs only these.
+// - stage_winner re-materialises a kept winner's rollout from Philox (the
+//   propagate kernel's arithmetic, bit for bit), writes its end state into
+//   the tree row and lowers the solution key for a goal node.  It checks the
+//   rollout's region and cost against the region's key, whose cost bits the
+//   other half leaves as they are.
+template <int DYN, int INTEG>
+__device__ __forceinline__ void append_meta(const DevParams& P, kpx_device_header* H, int w, int kept, int n_old,
+                                            int lam, uint32_t iter, const int32_t* va) {
+    constexpr int m = Dims<DYN>::m;
+    const int slot = P.win_slot[w];
+    const int r = P.slot_region[slot];
+    // the mapped region must hold this slot's key (a stale entry would not)
+    if (r < 0 || r >= P.R || (uint32_t)P.region_key[r] != (uint32_t)P.N + (uint32_t)slot) {
+        set_status(H, KPX_E_INTERNAL);
+        H->err_info[1] = (uint32_t)slot;
+        return;
+    }
+    if (w >= kept) {  // dropped by the capacity rule: the region's key before this iteration
+        P.region_key[r] = P.region_snap[r];
+        return;
+    }
+    const uint32_t su = (uint32_t)slot;  // < 2^32, as in LaneRollout::start
+    const int j = (int)(su / (uint32_t)lam);
+    const int s = (int)(su - (uint32_t)j * (uint32_t)lam);
+    const int node = va[j];
+    float u[m];
+    int K;
+    sample_control<m>(P, iter, (uint32_t)node, (uint32_t)s, u, K);
+    const int id = n_old + w;
+#pragma unroll
+    for (int d = 0; d < m; ++d) P.u[(int64_t)d * P.N + id] = u[d];
+    P.K[id] = (uint16_t)K;
+    P.parent[id] = node;
+    const uint64_t k = pack_key(key_cost(P.region_key[r]), (uint32_t)id);
+    P.key[id] = k;
+    P.region[id] = r;
+    P.set[id] = SET_A;
+    P.icount[id] = 0;
+    const int old = P.region_owner[r];
+    P.region_key[r] = k;
+    if (old >= 0) P.set[old] = (uint8_t)(P.set[old] | SET_DOM);  // one winner per region: the only writer
+    P.region_owner[r] = id;
+}
+
+template <int DYN, int INTEG>
+__device__ __forceinline__ void stage_winner(const DevParams& P, kpx_device_header* H, int w, int n_old, int lam,
+                                             uint32_t iter, const int32_t* va) {
+    constexpr int n = Dims<DYN>::n;
+    const int slot = P.win_slot[w];
+    const int r = P.slot_region[slot];
+    if (r < 0 || r >= P.R) return;  // append_meta reports it
+    LaneRollout<DYN, INTEG> Rw;
+    Rw.start(P, va, lam, iter, (int64_t)slot);
+    uint32_t te_unused = 0;
+    for (int k = 0; k < Rw.K; ++k) Rw.template advance<false>(P, te_unused);
+    const float c = Rw.cost(P);
+    if ((uint32_t)(P.region_key[r] >> 32) != __float_as_uint(c) || region_of<n>(P, Rw.x) != r) {
+        set_status(H, KPX_E_INTERNAL);
+        H->err_info[1] = (uint32_t)slot;
+        return;
+    }
+    const int id = n_old + w;
+#pragma unroll
+    for (int d = 0; d < n; ++d) P.x[(int64_t)d * P.N + id] = Rw.x[d];
+    if (in_goal(P, Rw.x[0], Rw.x[1], Rw.x[2])) goal_key_min(H, pack_key(c, (uint32_t)id));
 }
 
 // Rules 1-3 of Alg. 3 (literal order, first match wins) for a node that is
