@@ -88,14 +88,56 @@ struct Dims<KPX_QUAD12> {
 // sin and cos through the special-function unit after a two-constant
 // Cody-Waite reduction of the angle to [-pi, pi] (the hardware sine and
 // cosine are accurate to about 4e-7 absolute on that interval).
-__device__ __forceinline__ void fast_sincos(float a, float& s, float& c) {
+__device__ __forceinline__ float reduce_angle(float a) {
     constexpr float INV_TWO_PI = 0.15915494309189535f;
     constexpr float TWO_PI_HI = 6.28125f;                   // few significant bits: k * TWO_PI_HI is exact
     constexpr float TWO_PI_LO = 1.9353071795864769e-3f;     // 2 pi - TWO_PI_HI
     const float k = rintf(a * INV_TWO_PI);
-    float r = fmaf(-k, TWO_PI_HI, a);
-    r = fmaf(-k, TWO_PI_LO, r);
-    __sincosf(r, &s, &c);
+    const float r = fmaf(-k, TWO_PI_HI, a);
+    return fmaf(-k, TWO_PI_LO, r);
+}
+
+__device__ __forceinline__ void fast_sincos(float a, float& s, float& c) { __sincosf(reduce_angle(a), &s, &c); }
+
+// The quadcopter's x' = f(x, u) with the sine and cosine of the yaw given:
+// p' = v; v' = (T/m) R(phi,theta,psi) e3 - g e3 (R = Rz Ry Rx);
+// (phi,theta,psi)' = W(phi,theta) omega; omega' = J^-1 (tau - omega x J omega).
+// Roll and pitch stay near the state bounds' range (|phi|, |theta| <= pi/4 at
+// every checked point; a stage point passes it by at most h |rate|), where the
+// hardware sine and cosine need no range reduction.
+template <bool ISO>
+__device__ __forceinline__ void quad_deriv(const DevParams& P, const float (&x)[12], float sps, float cps,
+                                           const float (&u)[4], float (&dx)[12]) {
+    float sph, cph, sth, cth;
+    __sincosf(x[3], &sph, &cph);
+    __sincosf(x[4], &sth, &cth);
+    const float inv_cth = __fdividef(1.0f, cth);
+    const float tth = sth * inv_cth;
+    const float p = x[9], q = x[10], r = x[11];
+    const float a = u[0] * P.inv_mass;
+    const float sthcph = sth * cph;
+    const float r13 = fmaf(cps, sthcph, sps * sph);
+    const float r23 = fmaf(sps, sthcph, -(cps * sph));
+    const float r33 = cth * cph;
+    dx[0] = x[6];
+    dx[1] = x[7];
+    dx[2] = x[8];
+    const float t1 = fmaf(sph, q, cph * r);
+    dx[3] = fmaf(tth, t1, p);
+    dx[4] = fmaf(cph, q, -(sph * r));
+    dx[5] = t1 * inv_cth;
+    dx[6] = a * r13;
+    dx[7] = a * r23;
+    dx[8] = fmaf(a, r33, -P.param[1]);
+    if constexpr (ISO) {
+        dx[9] = u[1] * P.inv_J[0];
+        dx[10] = u[2] * P.inv_J[1];
+        dx[11] = u[3] * P.inv_J[2];
+    } else {
+        dx[9] = fmaf(-P.dJ[0] * q, r, u[1]) * P.inv_J[0];
+        dx[10] = fmaf(-P.dJ[1] * r, p, u[2]) * P.inv_J[1];
+        dx[11] = fmaf(-P.dJ[2] * p, q, u[3]) * P.inv_J[2];
+    }
 }
 
 // ISO (quadcopter only): the inertia is isotropic (J_x = J_y = J_z), so the
@@ -124,44 +166,9 @@ __device__ __forceinline__ void deriv(const DevParams& P, const float (&x)[Dims<
         dx[4] = u[1];
         dx[5] = u[2];
     } else {
-        // p' = v; v' = (T/m) R(phi,theta,psi) e3 - g e3 (R = Rz Ry Rx);
-        // (phi,theta,psi)' = W(phi,theta) omega; omega' = J^-1 (tau - omega x J omega)
-        // roll and pitch stay near the state bounds' range (|phi|, |theta| <= pi/4 at
-        // every checked point; a stage point passes it by at most h |rate|), where the
-        // hardware sine and cosine need no range reduction; yaw is unbounded
-        float sph, cph, sth, cth, sps, cps;
-        __sincosf(x[3], &sph, &cph);
-        __sincosf(x[4], &sth, &cth);
-        fast_sincos(x[5], sps, cps);
-        // the hardware's approximate reciprocal (about 1 ulp): cos(theta) >= cos(pi/4)
-        // within the state bounds, and propagate, append and re-validation share it
-        const float inv_cth = __fdividef(1.0f, cth);
-        const float tth = sth * inv_cth;
-        const float p = x[9], q = x[10], r = x[11];
-        const float a = u[0] * P.inv_mass;
-        const float sthcph = sth * cph;
-        const float r13 = fmaf(cps, sthcph, sps * sph);
-        const float r23 = fmaf(sps, sthcph, -(cps * sph));
-        const float r33 = cth * cph;
-        dx[0] = x[6];
-        dx[1] = x[7];
-        dx[2] = x[8];
-        const float t1 = fmaf(sph, q, cph * r);
-        dx[3] = fmaf(tth, t1, p);
-        dx[4] = fmaf(cph, q, -(sph * r));
-        dx[5] = t1 * inv_cth;
-        dx[6] = a * r13;
-        dx[7] = a * r23;
-        dx[8] = fmaf(a, r33, -P.param[1]);
-        if constexpr (ISO) {
-            dx[9] = u[1] * P.inv_J[0];
-            dx[10] = u[2] * P.inv_J[1];
-            dx[11] = u[3] * P.inv_J[2];
-        } else {
-            dx[9] = fmaf(-P.dJ[0] * q, r, u[1]) * P.inv_J[0];
-            dx[10] = fmaf(-P.dJ[1] * r, p, u[2]) * P.inv_J[1];
-            dx[11] = fmaf(-P.dJ[2] * p, q, u[3]) * P.inv_J[2];
-        }
+        float sps, cps;
+        fast_sincos(x[5], sps, cps);  // yaw is unbounded
+        quad_deriv<ISO>(P, x, sps, cps, u, dx);
     }
 }
 
@@ -328,18 +335,67 @@ struct Stepper {
     }
 };
 
-// The quadcopter's RK4: with isotropic inertia (flag set by the host when
-// J_x = J_y = J_z exactly) the body rates' derivative is the constant tau / J,
-// which the compiler keeps out of the step loop.  One uniform branch per step.
+// The quadcopter's RK4.  The yaw enters f only through its sine and cosine,
+// so the stepper carries beside x[5] a copy yr of the yaw reduced to
+// [-pi, pi] when the rollout starts and advanced by the same RK4 increments;
+// a step that takes it past pi folds it back by 2 pi.  The stage yaws
+// yr + c k then lie within [-pi, pi] widened by one stage's turn (about
+// 0.02 rad), where the hardware sine and cosine need no reduction: four
+// reductions fewer per step.  The copy rounds differently from a reduction
+// of x[5] (both approximate the same angle to a few FP32 ulps of pi).  With
+// isotropic inertia (flag set by the host when J_x = J_y = J_z exactly) the
+// body rates' derivative is the constant tau / J, which the compiler keeps
+// out of the step loop.  One uniform branch per step.
+template <bool ISO>
+__device__ __forceinline__ void quad_rk4_step(const DevParams& P, float (&x)[12], float& yr, const float (&u)[4]) {
+    constexpr float PI_F = 3.14159265358979323846f;
+    constexpr float TWO_PI_F = 6.28318530717958647692f;
+    const float h = P.h;
+    const float hh = 0.5f * h;
+    const float h6 = h * (1.0f / 6.0f);
+    float k[12], acc[12], xt[12];
+    float s, c;
+    __sincosf(yr, &s, &c);
+    quad_deriv<ISO>(P, x, s, c, u, k);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        acc[i] = k[i];
+        xt[i] = fmaf(hh, k[i], x[i]);
+    }
+    __sincosf(fmaf(hh, k[5], yr), &s, &c);
+    quad_deriv<ISO>(P, xt, s, c, u, k);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        acc[i] = fmaf(2.0f, k[i], acc[i]);
+        xt[i] = fmaf(hh, k[i], x[i]);
+    }
+    __sincosf(fmaf(hh, k[5], yr), &s, &c);
+    quad_deriv<ISO>(P, xt, s, c, u, k);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        acc[i] = fmaf(2.0f, k[i], acc[i]);
+        xt[i] = fmaf(h, k[i], x[i]);
+    }
+    __sincosf(fmaf(h, k[5], yr), &s, &c);
+    quad_deriv<ISO>(P, xt, s, c, u, k);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) x[i] = fmaf(h6, acc[i] + k[i], x[i]);
+    yr = fmaf(h6, acc[5] + k[5], yr);
+    if (fabsf(yr) > PI_F) yr -= copysignf(TWO_PI_F, yr);
+}
+
 template <>
 struct Stepper<KPX_QUAD12, KPX_RK4> {
     static constexpr int n = 12, m = 4;
-    __device__ __forceinline__ void init(const DevParams&, const float (&)[n], const float (&)[m]) {}
+    float yr;  // the yaw x[5] reduced to [-pi, pi]
+    __device__ __forceinline__ void init(const DevParams&, const float (&x)[n], const float (&)[m]) {
+        yr = reduce_angle(x[5]);
+    }
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
         if (P.iso_inertia)
-            step<KPX_QUAD12, KPX_RK4, true>(P, x, u);
+            quad_rk4_step<true>(P, x, yr, u);
         else
-            step<KPX_QUAD12, KPX_RK4, false>(P, x, u);
+            quad_rk4_step<false>(P, x, yr, u);
     }
 };
 

@@ -248,10 +248,16 @@ __device__ __forceinline__ void roll_candidate(const DevParams& P, const GridVie
     constexpr int n = Dims<DYN>::n;
     C.R.start(P, va, lam, iter, slot);
     bool ok = true;
-    while (ok && C.R.k < C.R.K) {
-        ++steps;
-        ok = early ? C.R.template advance_in<false, SMEM, SYM>(P, G, tests)
-                   : C.R.template advance_in<true, SMEM, SYM>(P, G, tests);
+    if (early) {  // one loop per mode: no per-step test of the flag
+        while (ok && C.R.k < C.R.K) {
+            ++steps;
+            ok = C.R.template advance_in<false, SMEM, SYM>(P, G, tests);
+        }
+    } else {
+        while (ok && C.R.k < C.R.K) {
+            ++steps;
+            ok = C.R.template advance_in<true, SMEM, SYM>(P, G, tests);
+        }
     }
     C.r = -1;
     C.c = 0.0f;
