@@ -59,7 +59,7 @@ FUSED_DRAM_BYTES = {
     "dubins6_forest300": 224768,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
 }
 PROPAGATE_DRAM_BYTES = {
-    "quad12_building1000": 6721024,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
+    "quad12_building1000": 6719744,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
 }
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
@@ -70,19 +70,20 @@ HBM_FALLBACK_GBS = 6800.0
 # the state and control (4 n + 4 m), K 2, parent 4, key 8, region 4, set 1,
 # inactivity count 1 and its region's key 8; one bit per candidate slot.
 UPDATE_BYTES_PER_NODE = 23
-UPDATE_PHASES = ("mark", "scan", "append", "prune")
+UPDATE_PHASES = ("mark", "scan", "append", "prune")  # the append phase runs k_append, then k_stage
 
 
 def update_row_bytes(n, m):
     return 4 * n + 4 * m + 28
 
 
-# DRAM bytes (read + write) of the four update kernels of one iteration, from
-# the ncu captures in profiles/ (each kernel from a cold L2, as ncu flushes
-# caches between captured kernels): workload -> (iteration, bytes)
+# DRAM bytes (read + write) of the five update kernels of one iteration
+# (k_mark, k_scan, k_append, k_stage, k_prune), from the ncu captures in
+# profiles/ (each kernel from a cold L2, as ncu flushes caches between
+# captured kernels): workload -> (iteration, bytes)
 UPDATE_DRAM_BYTES = {
-    "quad12_building1000": (100, 3569664),   # profiles/update_quad12_building1000.md
-    "quad12_clutter1000": (300, 24210688),   # profiles/update_quad12_clutter1000.md
+    "quad12_building1000": (100, 3749888),   # profiles/update_quad12_building1000.md
+    "quad12_clutter1000": (300, 25001472),   # profiles/update_quad12_clutter1000.md
 }
 
 
@@ -519,14 +520,15 @@ def run_kpx(args):
     l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0) or 0)
     work_set = UPDATE_BYTES_PER_NODE * int(st["n_nodes"]) + 8 * int(prob.n_regions)
     roofline_update = {
-        "bound": "hbm", "kernel": "tree update: k_mark + k_scan + k_append + k_prune (phase kernels)",
+        "bound": "hbm",
+        "kernel": "tree update: k_mark + k_scan + k_append + k_stage + k_prune (phase kernels, one after another)",
         "achieved": upd_gbs, "peak": hbm, "unit": "GB/s", "frac": upd_gbs / hbm if hbm else 0.0,
         "peak_basis": hbm_basis,
         "traffic": UPDATE_DRAM_BYTES[args.workload][1] if args.workload in UPDATE_DRAM_BYTES else None,
         "traffic_iteration": UPDATE_DRAM_BYTES[args.workload][0] if args.workload in UPDATE_DRAM_BYTES else None,
         "algorithmic_bytes_at_traffic_iteration": (upd_bytes_at.get(UPDATE_DRAM_BYTES[args.workload][0])
                                                    if args.workload in UPDATE_DRAM_BYTES else None),
-        "traffic_note": "DRAM bytes of the four update kernels of one iteration (ncu capture, each kernel from a "
+        "traffic_note": "DRAM bytes of the five update kernels of one iteration (ncu capture, each kernel from a "
                         "cold L2; profiles/), beside the algorithmic bytes of the same iteration",
         "algorithmic_bytes_per_step": upd_bytes, "update_ms_per_step": upd_ms,
         "bytes_basis": "per iteration: %d B per pre-append node + %d B per appended row + 1 bit per candidate slot"
