@@ -346,6 +346,32 @@ struct Stepper {
 // isotropic inertia (flag set by the host when J_x = J_y = J_z exactly) the
 // body rates' derivative is the constant tau / J, which the compiler keeps
 // out of the step loop.  One uniform branch per step.
+// d[i] = a b[i] + c[i] and d[i] = b[i] + c[i] over the components, two per
+// packed FP32 instruction (sm_100 and later): each component rounds as the
+// scalar fmaf / add does, so the results are those of the scalar loops.
+template <int N>
+__device__ __forceinline__ void fma_pairs(float (&d)[N], float a, const float (&b)[N], const float (&c)[N]) {
+    static_assert(N % 2 == 0, "pairs");
+    const float2 a2 = make_float2(a, a);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+        const float2 r = __ffma2_rn(a2, make_float2(b[i], b[i + 1]), make_float2(c[i], c[i + 1]));
+        d[i] = r.x;
+        d[i + 1] = r.y;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void add_pairs(float (&d)[N], const float (&b)[N], const float (&c)[N]) {
+    static_assert(N % 2 == 0, "pairs");
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+        const float2 r = __fadd2_rn(make_float2(b[i], b[i + 1]), make_float2(c[i], c[i + 1]));
+        d[i] = r.x;
+        d[i + 1] = r.y;
+    }
+}
+
 template <bool ISO>
 __device__ __forceinline__ void quad_rk4_step(const DevParams& P, float (&x)[12], float& yr, const float (&u)[4]) {
     constexpr float PI_F = 3.14159265358979323846f;
@@ -358,29 +384,21 @@ __device__ __forceinline__ void quad_rk4_step(const DevParams& P, float (&x)[12]
     __sincosf(yr, &s, &c);
     quad_deriv<ISO>(P, x, s, c, u, k);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] = k[i];
-        xt[i] = fmaf(hh, k[i], x[i]);
-    }
+    for (int i = 0; i < 12; ++i) acc[i] = k[i];
+    fma_pairs(xt, hh, k, x);
     __sincosf(fmaf(hh, k[5], yr), &s, &c);
     quad_deriv<ISO>(P, xt, s, c, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] = fmaf(2.0f, k[i], acc[i]);
-        xt[i] = fmaf(hh, k[i], x[i]);
-    }
+    fma_pairs(acc, 2.0f, k, acc);
+    fma_pairs(xt, hh, k, x);
     __sincosf(fmaf(hh, k[5], yr), &s, &c);
     quad_deriv<ISO>(P, xt, s, c, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] = fmaf(2.0f, k[i], acc[i]);
-        xt[i] = fmaf(h, k[i], x[i]);
-    }
+    fma_pairs(acc, 2.0f, k, acc);
+    fma_pairs(xt, h, k, x);
     __sincosf(fmaf(h, k[5], yr), &s, &c);
     quad_deriv<ISO>(P, xt, s, c, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) x[i] = fmaf(h6, acc[i] + k[i], x[i]);
-    yr = fmaf(h6, acc[5] + k[5], yr);
+    add_pairs(acc, acc, k);  // acc + k4
+    yr = fmaf(h6, acc[5], yr);
+    fma_pairs(x, h6, acc, x);
     if (fabsf(yr) > PI_F) yr -= copysignf(TWO_PI_F, yr);
 }
 
