@@ -108,27 +108,34 @@ __device__ __forceinline__ void fast_sincos(float a, float& s, float& c) { __sin
 template <bool ISO>
 __device__ __forceinline__ void quad_deriv(const DevParams& P, const float (&x)[12], float sps, float cps,
                                            const float (&u)[4], float (&dx)[12]) {
+    // The products and sums are paired into packed FP32 operations (two per
+    // instruction, each component rounded as its scalar form; a negated
+    // factor is exact), so the values are those of the scalar expressions
+    //   r13 = cps (sth cph) + sps sph,  r23 = sps (sth cph) - cps sph,
+    //   r33 = cth cph,  t1 = sph q + cph r,  theta' = cph q - sph r,
+    //   phi' = (sth / cth) t1 + p,  psi' = t1 / cth,  v' = a (r13, r23, r33) - g e3.
     float sph, cph, sth, cth;
     __sincosf(x[3], &sph, &cph);
     __sincosf(x[4], &sth, &cth);
     const float inv_cth = __fdividef(1.0f, cth);
-    const float tth = sth * inv_cth;
     const float p = x[9], q = x[10], r = x[11];
     const float a = u[0] * P.inv_mass;
-    const float sthcph = sth * cph;
-    const float r13 = fmaf(cps, sthcph, sps * sph);
-    const float r23 = fmaf(sps, sthcph, -(cps * sph));
-    const float r33 = cth * cph;
+    const float2 sc_c = __fmul2_rn(make_float2(sth, cth), make_float2(cph, cph));      // (sth cph, r33)
+    const float2 ss_c = __fmul2_rn(make_float2(sps, -cps), make_float2(sph, sph));     // (sps sph, -cps sph)
+    const float2 rr = __ffma2_rn(make_float2(cps, sps), make_float2(sc_c.x, sc_c.x), ss_c);  // (r13, r23)
+    const float2 cr = __fmul2_rn(make_float2(cph, -sph), make_float2(r, r));           // (cph r, -sph r)
+    const float2 tq = __ffma2_rn(make_float2(sph, cph), make_float2(q, q), cr);        // (t1, theta')
+    const float2 td = __fmul2_rn(make_float2(sth, tq.x), make_float2(inv_cth, inv_cth));  // (tan theta, psi')
+    const float2 av = __fmul2_rn(make_float2(a, a), rr);                               // v'_x, v'_y
     dx[0] = x[6];
     dx[1] = x[7];
     dx[2] = x[8];
-    const float t1 = fmaf(sph, q, cph * r);
-    dx[3] = fmaf(tth, t1, p);
-    dx[4] = fmaf(cph, q, -(sph * r));
-    dx[5] = t1 * inv_cth;
-    dx[6] = a * r13;
-    dx[7] = a * r23;
-    dx[8] = fmaf(a, r33, -P.param[1]);
+    dx[3] = fmaf(td.x, tq.x, p);
+    dx[4] = tq.y;
+    dx[5] = td.y;
+    dx[6] = av.x;
+    dx[7] = av.y;
+    dx[8] = fmaf(a, sc_c.y, -P.param[1]);
     if constexpr (ISO) {
         dx[9] = u[1] * P.inv_J[0];
         dx[10] = u[2] * P.inv_J[1];
