@@ -99,6 +99,22 @@ __device__ __forceinline__ float reduce_angle(float a) {
 
 __device__ __forceinline__ void fast_sincos(float a, float& s, float& c) { __sincosf(reduce_angle(a), &s, &c); }
 
+// The special-function unit's approximate sine and cosine and reciprocal in
+// their flush-to-zero forms (PTX sin / cos / rcp.approx.ftz.f32): they differ
+// from the non-flushing forms only for subnormal arguments or results, which
+// the quadcopter's angles (a subnormal angle is flushed to 0, whose sine is
+// 0 either way) and cos(theta) >= cos(pi/4) do not produce.
+__device__ __forceinline__ void sincos_sfu(float a, float& s, float& c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(a));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(a));
+}
+
+__device__ __forceinline__ float rcp_sfu(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 // The quadcopter's x' = f(x, u) with the sine and cosine of the yaw given:
 // p' = v; v' = (T/m) R(phi,theta,psi) e3 - g e3 (R = Rz Ry Rx);
 // (phi,theta,psi)' = W(phi,theta) omega; omega' = J^-1 (tau - omega x J omega).
@@ -115,9 +131,9 @@ __device__ __forceinline__ void quad_deriv(const DevParams& P, const float (&x)[
     //   r33 = cth cph,  t1 = sph q + cph r,  theta' = cph q - sph r,
     //   phi' = (sth / cth) t1 + p,  psi' = t1 / cth,  v' = a (r13, r23, r33) - g e3.
     float sph, cph, sth, cth;
-    __sincosf(x[3], &sph, &cph);
-    __sincosf(x[4], &sth, &cth);
-    const float inv_cth = __fdividef(1.0f, cth);
+    sincos_sfu(x[3], sph, cph);
+    sincos_sfu(x[4], sth, cth);
+    const float inv_cth = rcp_sfu(cth);
     const float p = x[9], q = x[10], r = x[11];
     const float a = u[0] * P.inv_mass;
     const float2 sc_c = __fmul2_rn(make_float2(sth, cth), make_float2(cph, cph));      // (sth cph, r33)
@@ -388,20 +404,20 @@ __device__ __forceinline__ void quad_rk4_step(const DevParams& P, float (&x)[12]
     const float h6 = h * (1.0f / 6.0f);
     float k[12], acc[12], xt[12];
     float s, c;
-    __sincosf(yr, &s, &c);
+    sincos_sfu(yr, s, c);
     quad_deriv<ISO>(P, x, s, c, u, k);
 #pragma unroll
     for (int i = 0; i < 12; ++i) acc[i] = k[i];
     fma_pairs(xt, hh, k, x);
-    __sincosf(fmaf(hh, k[5], yr), &s, &c);
+    sincos_sfu(fmaf(hh, k[5], yr), s, c);
     quad_deriv<ISO>(P, xt, s, c, u, k);
     fma_pairs(acc, 2.0f, k, acc);
     fma_pairs(xt, hh, k, x);
-    __sincosf(fmaf(hh, k[5], yr), &s, &c);
+    sincos_sfu(fmaf(hh, k[5], yr), s, c);
     quad_deriv<ISO>(P, xt, s, c, u, k);
     fma_pairs(acc, 2.0f, k, acc);
     fma_pairs(xt, h, k, x);
-    __sincosf(fmaf(h, k[5], yr), &s, &c);
+    sincos_sfu(fmaf(h, k[5], yr), s, c);
     quad_deriv<ISO>(P, xt, s, c, u, k);
     add_pairs(acc, acc, k);  // acc + k4
     yr = fmaf(h6, acc[5], yr);
