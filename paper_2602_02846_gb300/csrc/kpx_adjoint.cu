@@ -44,13 +44,14 @@ struct Trig {
 // Roll and pitch of a quadcopter trajectory stay within a few radians, where
 // the hardware sine and cosine need no range reduction (absolute error grows
 // like |angle| 1e-7); yaw keeps the reduction.  1 / cos(theta) is the
-// hardware's approximate reciprocal (about 1 ulp).
+// hardware's approximate reciprocal (about 1 ulp).  The flush-to-zero forms
+// differ only on subnormal values, which these angles and cos(theta) are not.
 __device__ __forceinline__ Trig trig_of(const float (&x)[12]) {
     Trig T;
-    __sincosf(x[3], &T.sphi, &T.cphi);
-    __sincosf(x[4], &T.sth, &T.cth);
+    sincos_sfu(x[3], T.sphi, T.cphi);
+    sincos_sfu(x[4], T.sth, T.cth);
     fast_sincos(x[5], T.spsi, T.cpsi);
-    T.ic = __fdividef(1.0f, T.cth);
+    T.ic = rcp_sfu(T.cth);
     return T;
 }
 
@@ -124,31 +125,24 @@ __device__ __forceinline__ void quad_vjp_t(const RefineParams& R, const Trig& T,
     gu[3] = a[11] * R.inv_J[2];
 }
 
-// classic RK4 with the control held over the step
+// classic RK4 with the control held over the step (the stage sums two
+// components per packed FP32 instruction)
 __device__ __forceinline__ void rk4_step(const RefineParams& R, float (&x)[12], const float (&u)[4]) {
     const float h = R.h;
     float k[12], acc[12], xs[12];
     quad_f(R, x, u, k);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] = k[i];
-        xs[i] = x[i] + 0.5f * h * k[i];
-    }
+    for (int i = 0; i < 12; ++i) acc[i] = k[i];
+    fma_pairs(xs, 0.5f * h, k, x);
     quad_f(R, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] += 2.0f * k[i];
-        xs[i] = x[i] + 0.5f * h * k[i];
-    }
+    fma_pairs(acc, 2.0f, k, acc);
+    fma_pairs(xs, 0.5f * h, k, x);
     quad_f(R, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] += 2.0f * k[i];
-        xs[i] = x[i] + h * k[i];
-    }
+    fma_pairs(acc, 2.0f, k, acc);
+    fma_pairs(xs, h, k, x);
     quad_f(R, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) x[i] += (h / 6.0f) * (acc[i] + k[i]);
+    add_pairs(acc, acc, k);
+    fma_pairs(x, h / 6.0f, acc, x);
 }
 
 // One RK4 stage as the adjoint needs it: the sine/cosine of the stage state's
@@ -177,31 +171,23 @@ __device__ __forceinline__ void rk4_step_rec(const RefineParams& R, float (&x)[1
     if (writer) put_stage(rec, T, x);
     quad_f_t(R, T, x, u, k);
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] = k[i];
-        xs[i] = x[i] + 0.5f * h * k[i];
-    }
+    for (int i = 0; i < 12; ++i) acc[i] = k[i];
+    fma_pairs(xs, 0.5f * h, k, x);
     T = trig_of(xs);
     if (writer) put_stage(rec + STAGE_WORDS, T, xs);
     quad_f_t(R, T, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] += 2.0f * k[i];
-        xs[i] = x[i] + 0.5f * h * k[i];
-    }
+    fma_pairs(acc, 2.0f, k, acc);
+    fma_pairs(xs, 0.5f * h, k, x);
     T = trig_of(xs);
     if (writer) put_stage(rec + 2 * STAGE_WORDS, T, xs);
     quad_f_t(R, T, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        acc[i] += 2.0f * k[i];
-        xs[i] = x[i] + h * k[i];
-    }
+    fma_pairs(acc, 2.0f, k, acc);
+    fma_pairs(xs, h, k, x);
     T = trig_of(xs);
     if (writer) put_stage(rec + 3 * STAGE_WORDS, T, xs);
     quad_f_t(R, T, xs, u, k);
-#pragma unroll
-    for (int i = 0; i < 12; ++i) x[i] += (h / 6.0f) * (acc[i] + k[i]);
+    add_pairs(acc, acc, k);
+    fma_pairs(x, h / 6.0f, acc, x);
 }
 
 __device__ __forceinline__ void vjp_stage(const RefineParams& R, const float* w, const float (&u)[4],
@@ -219,43 +205,34 @@ __device__ __forceinline__ void vjp_stage(const RefineParams& R, const float* w,
 
 // Adjoint of one RK4 step: lam (dJ/dx_{k+1}) becomes dJ/dx_k; gu gets dJ/du
 // through this step.  The four stages come from rk4_step_rec(), so no stage
-// is re-evaluated on the serial chain of the backward pass.
+// is re-evaluated on the serial chain of the backward pass.  The
+// component-wise sums run two per packed FP32 instruction.
 __device__ __forceinline__ void rk4_adjoint_rec(const RefineParams& R, const float* rec, const float (&u)[4],
                                                 float (&lam)[12], float (&gu)[4]) {
     const float h = R.h;
-    float ax[12], ak[12], g[12], gus[4];
+    float ax[12], ak[12], g[12], t[12], gus[4];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        ax[i] = lam[i];
-        ak[i] = (h / 6.0f) * lam[i];  // adjoint of k4
-    }
+    for (int i = 0; i < 12; ++i) ax[i] = lam[i];
+    mul_pairs(ak, h / 6.0f, lam);                        // adjoint of k4
     vjp_stage(R, rec + 3 * STAGE_WORDS, u, ak, g, gus);  // k4 = f(x + h k3)
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        ax[i] += g[i];
-        ak[i] = (h / 3.0f) * lam[i] + h * g[i];  // adjoint of k3
-    }
+    add_pairs(ax, ax, g);
+    mul_pairs(t, h / 3.0f, lam);
+    fma_pairs(ak, h, g, t);  // adjoint of k3
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
     vjp_stage(R, rec + 2 * STAGE_WORDS, u, ak, g, gus);  // k3 = f(x + h/2 k2)
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        ax[i] += g[i];
-        ak[i] = (h / 3.0f) * lam[i] + 0.5f * h * g[i];  // adjoint of k2
-    }
+    add_pairs(ax, ax, g);
+    fma_pairs(ak, 0.5f * h, g, t);  // adjoint of k2
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
     vjp_stage(R, rec + STAGE_WORDS, u, ak, g, gus);  // k2 = f(x + h/2 k1)
-#pragma unroll
-    for (int i = 0; i < 12; ++i) {
-        ax[i] += g[i];
-        ak[i] = (h / 6.0f) * lam[i] + 0.5f * h * g[i];  // adjoint of k1
-    }
+    add_pairs(ax, ax, g);
+    mul_pairs(t, h / 6.0f, lam);
+    fma_pairs(ak, 0.5f * h, g, t);  // adjoint of k1
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
     vjp_stage(R, rec, u, ak, g, gus);  // k1 = f(x)
-#pragma unroll
-    for (int i = 0; i < 12; ++i) lam[i] = ax[i] + g[i];
+    add_pairs(lam, ax, g);
 #pragma unroll
     for (int i = 0; i < 4; ++i) gu[i] += gus[i];
 }

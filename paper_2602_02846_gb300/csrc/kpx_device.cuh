@@ -369,8 +369,8 @@ struct Stepper {
 // isotropic inertia (flag set by the host when J_x = J_y = J_z exactly) the
 // body rates' derivative is the constant tau / J, which the compiler keeps
 // out of the step loop.  One uniform branch per step.
-// d[i] = a b[i] + c[i] and d[i] = b[i] + c[i] over the components, two per
-// packed FP32 instruction (sm_100 and later): each component rounds as the
+// d[i] = a b[i] + c[i], d[i] = a b[i] and d[i] = b[i] + c[i] over the
+// components, two per packed FP32 instruction (sm_100 and later): each component rounds as the
 // scalar fmaf / add does, so the results are those of the scalar loops.
 template <int N>
 __device__ __forceinline__ void fma_pairs(float (&d)[N], float a, const float (&b)[N], const float (&c)[N]) {
@@ -379,6 +379,18 @@ __device__ __forceinline__ void fma_pairs(float (&d)[N], float a, const float (&
 #pragma unroll
     for (int i = 0; i < N; i += 2) {
         const float2 r = __ffma2_rn(a2, make_float2(b[i], b[i + 1]), make_float2(c[i], c[i + 1]));
+        d[i] = r.x;
+        d[i + 1] = r.y;
+    }
+}
+
+template <int N>
+__device__ __forceinline__ void mul_pairs(float (&d)[N], float a, const float (&b)[N]) {
+    static_assert(N % 2 == 0, "pairs");
+    const float2 a2 = make_float2(a, a);
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+        const float2 r = __fmul2_rn(a2, make_float2(b[i], b[i + 1]));
         d[i] = r.x;
         d[i + 1] = r.y;
     }
