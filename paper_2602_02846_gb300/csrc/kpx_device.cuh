@@ -452,14 +452,6 @@ struct Stepper<KPX_QUAD12, KPX_RK4> {
     }
 };
 
-// (s, c) <- sin and cos of (a + d), from those of a and of d
-__device__ __forceinline__ void rotate(float& s, float& c, float sd, float cd) {
-    const float s1 = fmaf(s, cd, c * sd);
-    const float c1 = fmaf(c, cd, -(s * sd));
-    s = s1;
-    c = c1;
-}
-
 template <>
 struct Stepper<KPX_DUBINS6, KPX_RK4> {
     static constexpr int n = 6, m = 3;
@@ -472,33 +464,41 @@ struct Stepper<KPX_DUBINS6, KPX_RK4> {
         sincosf(hh * u[0], &sdp, &cdp);
         sincosf(hh * u[1], &sdg, &cdg);
     }
+    // (s, c) = sin and cos of (a + d) from those of a and of d:
+    // (s cd + c sd, c cd - s sd), one packed FP32 multiply and one packed FMA
+    __device__ __forceinline__ static float2 rotate2(float2 sc, float sd, float cd) {
+        const float2 t = __fmul2_rn(make_float2(sc.y, -sc.x), make_float2(sd, sd));
+        return __ffma2_rn(sc, make_float2(cd, cd), t);
+    }
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
         const float h = P.h;
         const float hh = 0.5f * h;
         const float h6 = h * (1.0f / 6.0f);
         const float vs = x[5];
         const float vm = fmaf(hh, u[2], x[5]), ve = fmaf(h, u[2], x[5]);
-        float spm = sp, cpm = cp, sgm = sg, cgm = cg;
-        rotate(spm, cpm, sdp, cdp);
-        rotate(sgm, cgm, sdg, cdg);
-        float spe = spm, cpe = cpm, sge = sgm, cge = cgm;
-        rotate(spe, cpe, sdp, cdp);
-        rotate(sge, cge, sdg, cdg);
-        // f = v (cos yaw cos pitch, sin yaw cos pitch, sin pitch) at start, mid, end
-        const float as = vs * cg, am = vm * cgm, ae = ve * cge;
-        const float fx = fmaf(4.0f, am * cpm, fmaf(as, cp, ae * cpe));
-        const float fy = fmaf(4.0f, am * spm, fmaf(as, sp, ae * spe));
-        const float fz = fmaf(4.0f, vm * sgm, fmaf(vs, sg, ve * sge));
-        x[0] = fmaf(h6, fx, x[0]);
-        x[1] = fmaf(h6, fy, x[1]);
+        const float2 pm = rotate2(make_float2(sp, cp), sdp, cdp);  // yaw at the midpoint
+        const float2 gm = rotate2(make_float2(sg, cg), sdg, cdg);  // pitch at the midpoint
+        const float2 pe = rotate2(pm, sdp, cdp);                    // and at the end
+        const float2 ge = rotate2(gm, sdg, cdg);
+        // f = v (cos yaw cos pitch, sin yaw cos pitch, sin pitch) at start, mid, end;
+        // (fx, fy) in packed pairs, (cos yaw, sin yaw) swapped into (x, y) order
+        const float as = vs * cg, am = vm * gm.y, ae = ve * ge.y;
+        const float2 fe = __fmul2_rn(make_float2(ae, ae), make_float2(pe.y, pe.x));
+        const float2 fs = __ffma2_rn(make_float2(as, as), make_float2(cp, sp), fe);
+        const float2 fm = __fmul2_rn(make_float2(am, am), make_float2(pm.y, pm.x));
+        const float2 fxy = __ffma2_rn(make_float2(4.0f, 4.0f), fm, fs);
+        const float fz = fmaf(4.0f, vm * gm.x, fmaf(vs, sg, ve * ge.x));
+        const float2 pxy = __ffma2_rn(make_float2(h6, h6), fxy, make_float2(x[0], x[1]));
+        x[0] = pxy.x;
+        x[1] = pxy.y;
         x[2] = fmaf(h6, fz, x[2]);
         x[3] = fmaf(h, u[0], x[3]);
         x[4] = fmaf(h, u[1], x[4]);
         x[5] = ve;
-        sp = spe;
-        cp = cpe;
-        sg = sge;
-        cg = cge;
+        sp = pe.x;
+        cp = pe.y;
+        sg = ge.x;
+        cg = ge.y;
     }
 };
 
