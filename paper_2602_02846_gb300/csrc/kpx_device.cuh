@@ -291,6 +291,23 @@ __device__ __forceinline__ void cell_range(const DevParams& P, const GridView& G
     e1 = min(grid_ld<SMEM>(G.cell_start + c + 1), SMEM ? P.grid_entries : P.grid_cap);
 }
 
+// cell_range() for a point inside the workspace box (bounds_ok() passed:
+// c >= pos_lo >= ws_lo on each axis), where (c - lo) * inv >= 0 needs no
+// lower clamp; x and y in one packed pair.  The cell is cell_range()'s.
+template <bool SMEM>
+__device__ __forceinline__ void cell_range_ws(const DevParams& P, const GridView& G, float px, float py, float pz,
+                                              int& e0, int& e1) {
+    const float2 txy = __fmul2_rn(__fadd2_rn(make_float2(px, py), make_float2(-P.ws_lo[0], -P.ws_lo[1])),
+                                  make_float2(P.grid_inv[0], P.grid_inv[1]));
+    const float tz = __fmul_rn(__fsub_rn(pz, P.ws_lo[2]), P.grid_inv[2]);
+    const int cx = (int)fminf(txy.x, (float)(P.grid_n[0] - 1));
+    const int cy = (int)fminf(txy.y, (float)(P.grid_n[1] - 1));
+    const int cz = (int)fminf(tz, (float)(P.grid_n[2] - 1));
+    const int c = (cz * P.grid_n[1] + cy) * P.grid_n[0] + cx;
+    e0 = grid_ld<SMEM>(G.cell_start + c);
+    e1 = min(grid_ld<SMEM>(G.cell_start + c + 1), SMEM ? P.grid_entries : P.grid_cap);
+}
+
 // Tests the point against the boxes e0..e1-1 in order and stops at the
 // first that contains it; `tests` accumulates the boxes examined.
 template <bool SMEM>
@@ -625,7 +642,11 @@ struct LaneRollout {
     __device__ __forceinline__ bool advance_in(const DevParams& P, const GridView& G, uint32_t& tests) {
         integrate(P);
         if (!bounds_ok<n, SYM>(P, x)) return false;
-        if (OBST && hits_obstacle_in<SMEM>(P, G, x[0], x[1], x[2], tests)) return false;
+        if (OBST && P.n_obs > 0) {  // hits_obstacle_in() for a point in the workspace
+            int e0, e1;
+            cell_range_ws<SMEM>(P, G, x[0], x[1], x[2], e0, e1);
+            if (walk_cell<SMEM>(G, x[0], x[1], x[2], e0, e1, tests)) return false;
+        }
         return true;
     }
 
