@@ -370,6 +370,7 @@ template <int DYN, int INTEG>
 struct Stepper {
     static constexpr int n = Dims<DYN>::n, m = Dims<DYN>::m;
     __device__ __forceinline__ void init(const DevParams&, const float (&)[n], const float (&)[m]) {}
+    template <int ISO = -1>
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
         step<DYN, INTEG>(P, x, u);
     }
@@ -461,8 +462,10 @@ struct Stepper<KPX_QUAD12, KPX_RK4> {
     __device__ __forceinline__ void init(const DevParams&, const float (&x)[n], const float (&)[m]) {
         yr = reduce_angle(x[5]);
     }
+    // ISO: 1 or 0 when the caller has read P.iso_inertia already, -1 to read it here
+    template <int ISO = -1>
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
-        if (P.iso_inertia)
+        if (ISO == 1 || (ISO < 0 && P.iso_inertia))
             quad_rk4_step<true>(P, x, yr, u);
         else
             quad_rk4_step<false>(P, x, yr, u);
@@ -487,6 +490,7 @@ struct Stepper<KPX_DUBINS6, KPX_RK4> {
         const float2 t = __fmul2_rn(make_float2(sc.y, -sc.x), make_float2(sd, sd));
         return __ffma2_rn(sc, make_float2(cd, cd), t);
     }
+    template <int ISO = -1>
     __device__ __forceinline__ void advance(const DevParams& P, float (&x)[n], const float (&u)[m]) {
         const float h = P.h;
         const float hh = 0.5f * h;
@@ -625,12 +629,15 @@ struct LaneRollout {
         k = 0;
     }
 
-    // One integration step and its path length, no checks.
+    // One integration step and its path length, no checks.  PL and ISO: 1 or
+    // 0 when the caller has read the cost kind (path length or not) and the
+    // inertia flag already, so that its loop tests neither; -1 to read them.
+    template <int PL = -1, int ISO = -1>
     __device__ __forceinline__ void integrate(const DevParams& P) {
         const float p0 = x[0], p1 = x[1], p2 = x[2];
-        st.advance(P, x, u);
+        st.template advance<ISO>(P, x, u);
         ++k;
-        if (P.cost_kind == KPX_COST_PATH_LENGTH) {
+        if (PL == 1 || (PL < 0 && P.cost_kind == KPX_COST_PATH_LENGTH)) {
             const float dx = x[0] - p0, dy = x[1] - p1, dz = x[2] - p2;
             len = len + sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
         }
@@ -638,9 +645,9 @@ struct LaneRollout {
 
     // One step; returns whether the new point is valid (bounds, and the
     // obstacles when OBST).
-    template <bool OBST, bool SMEM = false, bool SYM = false>
+    template <bool OBST, bool SMEM = false, bool SYM = false, int PL = -1, int ISO = -1>
     __device__ __forceinline__ bool advance_in(const DevParams& P, const GridView& G, uint32_t& tests) {
-        integrate(P);
+        integrate<PL, ISO>(P);
         if (!bounds_ok<n, SYM>(P, x)) return false;
         if (OBST && P.n_obs > 0) {  // hits_obstacle_in() for a point in the workspace
             int e0, e1;

@@ -239,6 +239,19 @@ struct Candidate {
     uint64_t key;
 };
 
+// The steps of a started rollout until its K-th or its first invalid point;
+// returns whether every point was valid.
+template <bool OBST, bool SMEM, bool SYM, int PL = -1, int ISO = -1, int DYN, int INTEG>
+__device__ __forceinline__ bool rollout_steps(const DevParams& P, const GridView& G, LaneRollout<DYN, INTEG>& R,
+                                              uint32_t& steps, uint32_t& tests) {
+    bool ok = true;
+    while (ok && R.k < R.K) {
+        ++steps;
+        ok = R.template advance_in<OBST, SMEM, SYM, PL, ISO>(P, G, tests);
+    }
+    return ok;
+}
+
 // G: where the obstacle grid is read (SMEM: a shared-memory copy)
 // SYM: the state bounds are symmetric (bounds_ok's one-comparison form)
 template <int DYN, int INTEG, bool SMEM = false, bool SYM = false>
@@ -253,11 +266,21 @@ __device__ __forceinline__ void roll_candidate(const DevParams& P, const GridVie
             ++steps;
             ok = C.R.template advance_in<false, SMEM, SYM>(P, G, tests);
         }
-    } else {
-        while (ok && C.R.k < C.R.K) {
-            ++steps;
-            ok = C.R.template advance_in<true, SMEM, SYM>(P, G, tests);
+    } else if (DYN == KPX_QUAD12 && INTEG == KPX_RK4) {  // the cost kind and inertia flag read once
+        const bool pl = P.cost_kind == KPX_COST_PATH_LENGTH;
+        if (P.iso_inertia) {
+            if (pl)
+                ok = rollout_steps<true, SMEM, SYM, 1, 1>(P, G, C.R, steps, tests);
+            else
+                ok = rollout_steps<true, SMEM, SYM, 0, 1>(P, G, C.R, steps, tests);
+        } else {
+            if (pl)
+                ok = rollout_steps<true, SMEM, SYM, 1, 0>(P, G, C.R, steps, tests);
+            else
+                ok = rollout_steps<true, SMEM, SYM, 0, 0>(P, G, C.R, steps, tests);
         }
+    } else {
+        ok = rollout_steps<true, SMEM, SYM>(P, G, C.R, steps, tests);
     }
     C.r = -1;
     C.c = 0.0f;
