@@ -171,6 +171,7 @@ Layout make_layout(const kpx_dynamics* dyn, const kpx_config* cfg, int32_t n_obs
     L.obs = seg((size_t)(n_obs > 0 ? n_obs : 1) * 2 * sizeof(float4));
     L.box_cells = seg((size_t)(n_obs > 0 ? n_obs : 1) * 6 * sizeof(int32_t));
     L.cell_start = seg((size_t)(GRID_MAX_CELLS + 1) * sizeof(int32_t));
+    L.cell_pair = seg((size_t)GRID_MAX_CELLS * sizeof(int2));
     L.cell_box = seg((size_t)grid_entry_budget(n_obs) * 2 * sizeof(float4));
     L.x = seg((size_t)n * N * sizeof(float));
     L.u = seg((size_t)m * N * sizeof(float));
@@ -285,6 +286,7 @@ void bind_pointers(kpx_planner* p) {
     P.obs = reinterpret_cast<float4*>(b + L.obs);
     P.box_cells = reinterpret_cast<int32_t*>(b + L.box_cells);
     P.cell_start = reinterpret_cast<int32_t*>(b + L.cell_start);
+    P.cell_pair = reinterpret_cast<int2*>(b + L.cell_pair);
     P.cell_box = reinterpret_cast<float4*>(b + L.cell_box);
     P.x = reinterpret_cast<float*>(b + L.x);
     P.u = reinterpret_cast<float*>(b + L.u);

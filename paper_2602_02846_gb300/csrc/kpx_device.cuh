@@ -304,8 +304,14 @@ __device__ __forceinline__ void cell_range_ws(const DevParams& P, const GridView
     const int cy = (int)fminf(txy.y, (float)(P.grid_n[1] - 1));
     const int cz = (int)fminf(tz, (float)(P.grid_n[2] - 1));
     const int c = (cz * P.grid_n[1] + cy) * P.grid_n[0] + cx;
-    e0 = grid_ld<SMEM>(G.cell_start + c);
-    e1 = min(grid_ld<SMEM>(G.cell_start + c + 1), SMEM ? P.grid_entries : P.grid_cap);
+    if constexpr (SMEM) {
+        e0 = G.cell_start[c];
+        e1 = min(G.cell_start[c + 1], P.grid_entries);
+    } else {  // the cell's (start, clamped end) pair, one load
+        const int2 r = __ldg(P.cell_pair + c);
+        e0 = r.x;
+        e1 = r.y;
+    }
 }
 
 // Tests the point against the boxes e0..e1-1 in order and stops at the

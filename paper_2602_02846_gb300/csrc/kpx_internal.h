@@ -103,6 +103,7 @@ struct DevParams {
     float4* obs;          // [2*n_obs]: lo (x,y,z,0), hi (x,y,z,0)
     int32_t* box_cells;   // [6*n_obs]: per box cell range lo x,y,z, hi x,y,z
     int32_t* cell_start;  // [n_cells + 1]: CSR offsets into cell_box
+    int2* cell_pair;      // [n_cells]: (cell_start[c], min(cell_start[c + 1], grid_cap)), one 8-byte load
     float4* cell_box;     // [2*grid_cap]: boxes of each cell, in box order
     uint32_t* clean;      // [N]: the epoch of the prune that found the node's strict ancestors not dominated
     int32_t* slot_region; // [slot_cap]: region of a winning slot (written by mark)
@@ -130,7 +131,7 @@ __host__ __device__ inline int grid_cell(float c, float lo, float inv, int n) {
 
 // Workspace layout (byte offsets from the workspace base).
 struct Layout {
-    size_t hdr, obs, box_cells, cell_start, cell_box, x, u, K, parent, key, region, set, icount;
+    size_t hdr, obs, box_cells, cell_start, cell_pair, cell_box, x, u, K, parent, key, region, set, icount;
     size_t region_key, region_snap, region_owner, va0, va1, win_slot, win_mask, win_tiles, prune_tiles, clean,
         slot_region, slot_order, path, traj;
     size_t total;

@@ -131,6 +131,7 @@ __global__ void k_grid_cells(DevParams P) {
             count += __popc(bal);
         }
         if (!FILL && lane == 0) P.cell_start[c + 1] = count;
+        if (FILL && lane == 0) P.cell_pair[c] = make_int2(start, min(P.cell_start[c + 1], P.grid_cap));
     }
     if (!FILL && blockIdx.x == 0 && threadIdx.x == 0) P.cell_start[0] = 0;
 }
