@@ -48,6 +48,9 @@ CASES = {
     "quad_small": lambda: scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8),
     # anisotropic inertia: the general body-rate dynamics with the gyroscopic term
     "quad_aniso": lambda: _anisotropic(scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8)),
+    # path-length cost: the quadcopter rollout loop's path-length variant
+    "quad_pathlen": lambda: scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8).replace(
+        cost_kind=scenes.COST_PATH_LENGTH, w_effort=0.0),
 }
 
 
@@ -62,7 +65,7 @@ def test_iteration_lockstep(kpx, case):
     """Several consecutive iterations, each checked phase by phase."""
     prob = CASES[case]()
     iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "dubins_forest": 6,
-             "dubins_open": 8, "quad_small": 3, "quad_aniso": 3}[case]
+             "dubins_open": 8, "quad_small": 3, "quad_aniso": 3, "quad_pathlen": 3}[case]
     pl, reps = _run_lockstep(kpx, prob, iters)
     assert reps, "no iteration ran"
     tot = sum(r["slots"] for r in reps)
