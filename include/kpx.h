@@ -127,7 +127,7 @@ enum {
     KPX_FLAG_EARLY_REJECT = 1,
     /* Never run whole iterations in the single-launch cluster kernel (used
      * while an iteration has at most a few thousand slots); every iteration
-     * then launches the seven phase kernels.  Results are identical. */
+     * then launches the eight phase kernels.  Results are identical. */
     KPX_FLAG_NO_FUSED = 2,
     /* Roll the propagate kernel's slots out in index order instead of in
      * ascending step count K within each aligned chunk of 128 slots.
@@ -254,14 +254,14 @@ kpx_status kpx_set_regions(kpx_planner* p, int32_t n_axes, const kpx_region_axis
 /* How kpx_iterate launches (the graph is built on first use): each call
  * kpx_iterate(n) is one launch of one CUDA graph per planner
  * (*max_iterations_per_launch = INT32_MAX; 0 when no graph can be made and
- * every iteration is seven plain launches).  The graph's first node writes
+ * every iteration is eight plain launches).  The graph's first node writes
  * n into the header's graph_pending.  *fused = 1 when a fused
  * single-launch kernel follows: it runs iterations in one thread-block
  * cluster while an iteration has at most one 32-slot chunk per warp of the
  * cluster and the tree at most 32,768 nodes, and leaves the iterations it
  * did not run in graph_pending.  A loop (a WHILE conditional node) then runs
- * the seven phase kernels once per iteration left, counting graph_pending
- * down to 0.  A launch of n iterations thus starts 1 + 7 m kernels, m = the
+ * the eight phase kernels once per iteration left, counting graph_pending
+ * down to 0.  A launch of n iterations thus starts 1 + 8 m kernels, m = the
  * iterations the fused kernel left (the header's fused_iterations counts the
  * ones it ran); without the fused kernel, 7 n. */
 kpx_status kpx_graph_info(kpx_planner* p, int32_t* max_iterations_per_launch, int32_t* fused);

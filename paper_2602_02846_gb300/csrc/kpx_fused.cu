@@ -1,7 +1,7 @@
 // kpx_fused.cu -- whole Kino-PAX+ iterations in one launch while the problem
 // is small.
 //
-// With a few thousand slots per iteration, the seven phase kernels are
+// With a few thousand slots per iteration, the eight phase kernels are
 // bound by launch and dependency latency rather than by work: every kernel
 // boundary costs a few microseconds, while the iteration's rollouts need a
 // few in total.  This kernel runs whole iterations inside one thread-block
