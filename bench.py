@@ -56,7 +56,7 @@ SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
 FUSED_DRAM_BYTES = {
-    "dubins6_forest300": 224768,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
+    "dubins6_forest300": 177920,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
 }
 PROPAGATE_DRAM_BYTES = {
     "quad12_building1000": 6738176,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
