@@ -382,20 +382,10 @@ struct Stepper {
     }
 };
 
-// The quadcopter's RK4.  The yaw enters f only through its sine and cosine,
-// so the stepper carries beside x[5] a copy yr of the yaw reduced to
-// [-pi, pi] when the rollout starts and advanced by the same RK4 increments;
-// a step that takes it past pi folds it back by 2 pi.  The stage yaws
-// yr + c k then lie within [-pi, pi] widened by one stage's turn (about
-// 0.02 rad), where the hardware sine and cosine need no reduction: four
-// reductions fewer per step.  The copy rounds differently from a reduction
-// of x[5] (both approximate the same angle to a few FP32 ulps of pi).  With
-// isotropic inertia (flag set by the host when J_x = J_y = J_z exactly) the
-// body rates' derivative is the constant tau / J, which the compiler keeps
-// out of the step loop.  One uniform branch per step.
 // d[i] = a b[i] + c[i], d[i] = a b[i] and d[i] = b[i] + c[i] over the
-// components, two per packed FP32 instruction (sm_100 and later): each component rounds as the
-// scalar fmaf / add does, so the results are those of the scalar loops.
+// components, two per packed FP32 instruction (sm_100 and later): each
+// component rounds as the scalar fmaf / mul / add does, so the results are
+// those of the scalar loops.
 template <int N>
 __device__ __forceinline__ void fma_pairs(float (&d)[N], float a, const float (&b)[N], const float (&c)[N]) {
     static_assert(N % 2 == 0, "pairs");
@@ -431,6 +421,18 @@ __device__ __forceinline__ void add_pairs(float (&d)[N], const float (&b)[N], co
     }
 }
 
+// The quadcopter's RK4.  The yaw enters f only through its sine and cosine,
+// so the stepper carries beside x[5] a copy yr of the yaw reduced to
+// [-pi, pi] when the rollout starts and advanced by the same RK4 increments;
+// a step that takes it past pi folds it back by 2 pi.  The stage yaws
+// yr + c k then lie within [-pi, pi] widened by one stage's turn (about
+// 0.02 rad), where the hardware sine and cosine need no reduction: four
+// reductions fewer per step.  The copy rounds differently from a reduction
+// of x[5] (both approximate the same angle to a few FP32 ulps of pi).  With
+// isotropic inertia (flag set by the host when J_x = J_y = J_z exactly) the
+// body rates' derivative is the constant tau / J, which the compiler keeps
+// out of the step loop.  The stage sums run two components per packed FP32
+// instruction.
 template <bool ISO>
 __device__ __forceinline__ void quad_rk4_step(const DevParams& P, float (&x)[12], float& yr, const float (&u)[4]) {
     constexpr float PI_F = 3.14159265358979323846f;
