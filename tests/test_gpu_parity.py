@@ -43,6 +43,8 @@ CASES = {
     "di_16grid": lambda: scenes.di_scene(1, grid_pos=16, tree_cap=32768),
     "di_adaptive": lambda: scenes.di_scene(2, grid_pos=15, tree_cap=100000, lam=0),
     "di_empty": lambda: scenes.di_scene(3, n_obstacles=0, grid_pos=12, tree_cap=20000),
+    # one step count for every sample (k_min = k_max): equal sort keys, ties in slot order
+    "di_fixed_k": lambda: scenes.di_scene(1, grid_pos=16, tree_cap=32768).replace(k_min=12, k_max=12),
     "dubins_forest": lambda: scenes.dubins_scene(0),
     "dubins_open": lambda: scenes.dubins_scene(1, n_obstacles=0, tree_cap=1 << 16, lam=16),
     "quad_small": lambda: scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8),
@@ -64,7 +66,7 @@ def _anisotropic(prob):
 def test_iteration_lockstep(kpx, case):
     """Several consecutive iterations, each checked phase by phase."""
     prob = CASES[case]()
-    iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "dubins_forest": 6,
+    iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "di_fixed_k": 5, "dubins_forest": 6,
              "dubins_open": 8, "quad_small": 3, "quad_aniso": 3, "quad_pathlen": 3}[case]
     pl, reps = _run_lockstep(kpx, prob, iters)
     assert reps, "no iteration ran"
@@ -191,14 +193,14 @@ def test_production_iteration_equals_phases_and_early_reject(kpx):
     pe.close()
 
 
-@pytest.mark.parametrize("case", ["quad_full", "quad_small", "di_adaptive", "dubins_forest"])
+@pytest.mark.parametrize("case", ["quad_full", "quad_small", "di_adaptive", "di_fixed_k", "dubins_forest"])
 def test_slot_order_sorts_by_steps_and_leaves_results_unchanged(kpx, case):
     """The begin phase orders each 128-slot chunk by (K, offset): a
     permutation of the chunk whose live slots come first in non-decreasing K.
     Rolling the slots out in that order changes no result: workspaces and the
     step, box-test and valid counters equal those of index order."""
     prob = scenes.quad_scene(0) if case == "quad_full" else CASES[case]()
-    iters = {"quad_full": 4, "quad_small": 4, "di_adaptive": 3, "dubins_forest": 8}[case]
+    iters = {"quad_full": 4, "quad_small": 4, "di_adaptive": 3, "di_fixed_k": 3, "dubins_forest": 8}[case]
     flags = kpx.KPX_FLAG_NO_FUSED
     pa = kpx.Planner(prob, flags=flags)
     pb = kpx.Planner(prob, flags=flags | kpx.KPX_FLAG_NO_SLOT_ORDER)
