@@ -45,6 +45,8 @@ CASES = {
     "di_empty": lambda: scenes.di_scene(3, n_obstacles=0, grid_pos=12, tree_cap=20000),
     # one step count for every sample (k_min = k_max): equal sort keys, ties in slot order
     "di_fixed_k": lambda: scenes.di_scene(1, grid_pos=16, tree_cap=32768).replace(k_min=12, k_max=12),
+    # a wide step-count range (1 to 300 steps): long rollouts, K spanning many values in each chunk
+    "di_long_k": lambda: scenes.di_scene(1, grid_pos=16, tree_cap=32768).replace(k_min=1, k_max=300),
     "dubins_forest": lambda: scenes.dubins_scene(0),
     "dubins_open": lambda: scenes.dubins_scene(1, n_obstacles=0, tree_cap=1 << 16, lam=16),
     "quad_small": lambda: scenes.quad_scene(0, clutter=200, certify=False, tree_cap=1 << 16, lam=8),
@@ -66,7 +68,7 @@ def _anisotropic(prob):
 def test_iteration_lockstep(kpx, case):
     """Several consecutive iterations, each checked phase by phase."""
     prob = CASES[case]()
-    iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "di_fixed_k": 5, "dubins_forest": 6,
+    iters = {"di_config": 6, "di_16grid": 6, "di_adaptive": 4, "di_empty": 5, "di_fixed_k": 5, "di_long_k": 4, "dubins_forest": 6,
              "dubins_open": 8, "quad_small": 3, "quad_aniso": 3, "quad_pathlen": 3}[case]
     pl, reps = _run_lockstep(kpx, prob, iters)
     assert reps, "no iteration ran"
