@@ -221,7 +221,7 @@ kpx_status kpx_reset(kpx_planner* p);
  *   propagate_blocks_per_sm: resident propagate blocks per SM of the
  *     persistent grid (0: as many as fit; capped at that);
  *   grid_scale: obstacle-grid cell edge as a multiple of the mean box extent
- *     per axis (1: the default; 0: keep the current).  The broad phase is
+ *     per axis (0.75: the default; 0: keep the current).  The broad phase is
  *     exact at any cell size, so only the split between cell lookups and
  *     box tests moves.
  * kpx_set_launch applies them to one planner; kpx_batch_set_launch to every

@@ -603,7 +603,7 @@ class BatchPlanner:
         if st != KPX_OK:
             raise KpxError(st, load().kpx_batch_last_error(self.h).decode())
 
-    def autotune(self, iters: int = 4, blocks=(0, 1, 2, 3), scales=(0.5, 1.0, 2.0)):
+    def autotune(self, iters: int = 4, blocks=(0, 1, 2, 3), scales=(0.5, 0.75, 1.0, 2.0)):
         """Per dynamics class, times ``iters`` batched iterations from the
         current state for every (blocks per SM, grid scale) pair, one class at
         a time with the others at their chosen settings, and keeps the

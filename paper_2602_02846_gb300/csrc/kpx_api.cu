@@ -41,7 +41,7 @@ struct kpx_planner {
     cudaGraphExec_t loop_exec = nullptr;
     cudaGraphNode_t count_node = nullptr;  // memset node: the launch's iteration count
     int32_t count_value = 1;               // the count node's current value
-    float grid_scale = 1.0f;     // obstacle-grid cell edge / mean box extent
+    float grid_scale = GRID_SCALE_DEFAULT;  // obstacle-grid cell edge / mean box extent
     std::vector<float> host_obs; // the boxes (lo xyz, hi xyz), to rebuild the grid
     std::vector<float4> upload;  // source of kpx_create's obstacle copy, alive until destroy
 };
@@ -221,7 +221,7 @@ bool host_point_valid(const DevParams& P, const float* x, const float* obs, int 
 // (capped by GRID_MAX_AXIS, GRID_MAX_CELLS and the entry budget).  Any grid
 // gives the same verdicts (the broad phase is exact); the scale only moves
 // work between cell lookups and box tests.
-void choose_grid(DevParams& P, const float* aabb, int n_obs, float scale = 1.0f) {
+void choose_grid(DevParams& P, const float* aabb, int n_obs, float scale = GRID_SCALE_DEFAULT) {
     P.grid_cap = (int32_t)grid_entry_budget(n_obs);
     int g[3] = {1, 1, 1};
     float W[3];

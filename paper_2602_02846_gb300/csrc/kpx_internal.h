@@ -36,6 +36,11 @@ constexpr int TRAJ_STAGE_ROWS = 65536;                               // trajecto
 constexpr int ORDER_CHUNK = 128;
 // obstacle broad phase: a uniform grid over the workspace box
 constexpr int GRID_MAX_CELLS = 65536;
+// Default obstacle-grid cell edge as a multiple of the mean box extent per
+// axis: finer than the boxes themselves, so that a cell lists fewer boxes
+// (measured: the Dubins forest 3 % and the quadcopter building 1 % faster at
+// 0.75 than at 1; finer still is slower on the forest)
+constexpr float GRID_SCALE_DEFAULT = 0.75f;
 constexpr int GRID_MAX_AXIS = 64;
 inline int64_t grid_entry_budget(int32_t n_obs) { return 32 * (int64_t)n_obs + 4096; }
 
