@@ -56,10 +56,10 @@ SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
 FUSED_DRAM_BYTES = {
-    "dubins6_forest300": 177920,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
+    "dubins6_forest300": 303872,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
 }
 PROPAGATE_DRAM_BYTES = {
-    "quad12_building1000": 6738176,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
+    "quad12_building1000": 6858752,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
 }
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
@@ -82,8 +82,8 @@ def update_row_bytes(n, m):
 # profiles/ (each kernel from a cold L2, as ncu flushes caches between
 # captured kernels): workload -> (iteration, bytes)
 UPDATE_DRAM_BYTES = {
-    "quad12_building1000": (100, 3752192),   # profiles/update_quad12_building1000.md
-    "quad12_clutter1000": (300, 25010944),   # profiles/update_quad12_clutter1000.md
+    "quad12_building1000": (100, 3755264),   # profiles/update_quad12_building1000.md
+    "quad12_clutter1000": (300, 25002240),   # profiles/update_quad12_clutter1000.md
 }
 
 
