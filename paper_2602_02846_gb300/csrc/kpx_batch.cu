@@ -55,9 +55,8 @@ __device__ void block_prefix(int B, int64_t* out, F value_of) {
 __global__ void __launch_bounds__(1024) k_b_begin(BatchParams BP) {
     for (int p = threadIdx.x; p < BP.B; p += blockDim.x) begin_counters(BP.Ps[p], BP.Ps[p].hdr);
     __syncthreads();
-    block_prefix(BP.B, BP.chunk_prefix, [&](int p) {
-        const int64_t n = BP.Ps[p].hdr->n_slots;
-        return (n + 31) / 32;
+    block_prefix(BP.B, BP.chunk_prefix, [&](int p) {  // each problem's propagate units
+        return propagate_units(BP.Ps[p].hdr->n_slots, BP.Ps[p].slot_order != nullptr);
     });
     block_prefix(BP.B, BP.scan_prefix, [&](int p) {
         const int64_t words = (BP.Ps[p].hdr->n_slots + 31) / 32;
@@ -115,8 +114,9 @@ __global__ void __launch_bounds__(PROP_THREADS, BatchPropOccupancy<DYN>::blocks)
         }
         const kpx_device_header* H = P.hdr;
         const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) != 0;
-        propagate_chunk<DYN, INTEG>(P, H->n_slots, H->lambda, (uint32_t)H->iter, va_current(P, H), early,
-                                    chunk - BP.chunk_prefix[p], no_rec, 0, steps, tests, n_valid, P.slot_order);
+        const int64_t unit = propagate_unit_chunk(chunk - BP.chunk_prefix[p], H->n_slots, P.slot_order != nullptr);
+        propagate_chunk<DYN, INTEG>(P, H->n_slots, H->lambda, (uint32_t)H->iter, va_current(P, H), early, unit,
+                                    no_rec, 0, steps, tests, n_valid, P.slot_order);
         unsigned long long t = 0ull;
         if ((threadIdx.x & 31) == 0) t = atomicAdd(&BP.bh->prop_ticket[BP.cls], 1ull);
         chunk = c_lo + n_warps + (int64_t)__shfl_sync(FULL, t, 0);

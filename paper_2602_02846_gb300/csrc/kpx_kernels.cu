@@ -222,16 +222,12 @@ __global__ void __launch_bounds__(PROP_THREADS, PropOccupancy<DYN>::blocks)
     const int32_t* va = va_current(P, H);
     const bool early = (P.flags & KPX_FLAG_EARLY_REJECT) && !rec_on;
     const int64_t n_warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    // With the slots of each 128-slot chunk sorted by K, the 32-slot units
-    // are handed out longest quarter first: unit q is quarter 3 - q / n128 of
-    // 128-slot chunk q % n128, so that the launch ends on the short rollouts
-    // (a longest-first schedule; a unit past n_slots is empty).
-    const int64_t n128 = (n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK;
-    const int64_t n_units = P.slot_order ? n128 * (ORDER_CHUNK / 32) : (n_slots + 31) / 32;
+    const bool ordered = P.slot_order != nullptr;
+    const int64_t n_units = propagate_units(n_slots, ordered);  // longest first when ordered
     int64_t q = (int64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     uint32_t steps = 0, tests = 0, n_valid = 0;
     while (q < n_units) {
-        const int64_t chunk = P.slot_order ? (q % n128) * (ORDER_CHUNK / 32) + (ORDER_CHUNK / 32 - 1 - q / n128) : q;
+        const int64_t chunk = propagate_unit_chunk(q, n_slots, ordered);
         propagate_chunk<DYN, INTEG, SYM>(P, n_slots, lam, iter, va, early, chunk, rec, rec_on, steps, tests, n_valid,
                                          P.slot_order);
         unsigned long long t = 0ull;

@@ -472,6 +472,21 @@ __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_sl
     }
 }
 
+// The propagate's work units: 32 slots each.  With the slots of each
+// 128-slot chunk sorted by K (ordered) they are handed out longest quarter
+// first: unit q is quarter 3 - q / n128 of 128-slot chunk q % n128, so that
+// a launch ends on the short rollouts (a longest-first schedule); units past
+// n_slots are empty.  Otherwise unit q is slots [32 q, 32 q + 32).
+__device__ __forceinline__ int64_t propagate_units(int64_t n_slots, bool ordered) {
+    return ordered ? (n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK * (ORDER_CHUNK / 32) : (n_slots + 31) / 32;
+}
+
+__device__ __forceinline__ int64_t propagate_unit_chunk(int64_t q, int64_t n_slots, bool ordered) {
+    if (!ordered) return q;
+    const int64_t n128 = (n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK;
+    return (q % n128) * (ORDER_CHUNK / 32) + (ORDER_CHUNK / 32 - 1 - q / n128);
+}
+
 // warp-wide: add the lane counters to the problem's header (one atomic each)
 __device__ __forceinline__ void flush_propagate_counters(kpx_device_header* H, uint32_t& steps, uint32_t& tests,
                                                          uint32_t& n_valid) {
