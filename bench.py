@@ -56,10 +56,10 @@ SM_COUNT_FALLBACK = 152
 # DRAM bytes (read + write) of one propagate launch from the ncu captures in
 # profiles/ (the kernel build named there); None for a workload not captured.
 FUSED_DRAM_BYTES = {
-    "dubins6_forest300": 303872,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
+    "dubins6_forest300": 195072,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
 }
 PROPAGATE_DRAM_BYTES = {
-    "quad12_building1000": 6858752,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
+    "quad12_building1000": 6862848,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
 }
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
@@ -82,8 +82,8 @@ def update_row_bytes(n, m):
 # profiles/ (each kernel from a cold L2, as ncu flushes caches between
 # captured kernels): workload -> (iteration, bytes)
 UPDATE_DRAM_BYTES = {
-    "quad12_building1000": (100, 3755264),   # profiles/update_quad12_building1000.md
-    "quad12_clutter1000": (300, 25002240),   # profiles/update_quad12_clutter1000.md
+    "quad12_building1000": (100, 3744000),   # profiles/update_quad12_building1000.md
+    "quad12_clutter1000": (300, 25003264),   # profiles/update_quad12_clutter1000.md
 }
 
 
@@ -163,6 +163,10 @@ BATCH_WORKLOADS = {
 }
 SERVE_WORKLOADS = {
     "serve_poisson200": dict(rate=200.0, desc="request loop: Poisson arrivals at 200 queries/s drawn from the "
+                                              "mixed-batch problem mix, admitted by device memory into per-class "
+                                              "slots, iterations of all resident queries batched"),
+    # the same loop under four times the load (context for where batching pays)
+    "serve_poisson800": dict(rate=800.0, desc="request loop: Poisson arrivals at 800 queries/s drawn from the "
                                               "mixed-batch problem mix, admitted by device memory into per-class "
                                               "slots, iterations of all resident queries batched"),
 }
