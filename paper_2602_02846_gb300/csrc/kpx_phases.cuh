@@ -196,8 +196,55 @@ __device__ __forceinline__ void warp_sort128(uint32_t (&v)[4]) {
     }
 }
 
+// The sort key of a quadcopter slot: K, or fewer steps when the velocity,
+// extrapolated from the parent's at the start's acceleration (the sampled
+// thrust along the parent's body z axis, gravity), leaves its bounds first.
+// Most quadcopter rollouts end on a velocity bound, so this predicts a
+// rollout's length better than K alone; only the order in which the slots
+// are rolled out depends on it, not any result.  The parent's part (its
+// body z axis and velocity) is computed once per parent.
+struct QuadOrderParent {
+    float zx, zy, zz, v[3];
+};
+
+__device__ __forceinline__ QuadOrderParent quad_order_parent(const DevParams& P, int node) {
+    const int64_t N = P.N;
+    float sph, cph, sth, cth, sps, cps;
+    __sincosf(P.x[3 * N + node], &sph, &cph);
+    __sincosf(P.x[4 * N + node], &sth, &cth);
+    fast_sincos(P.x[5 * N + node], sps, cps);
+    QuadOrderParent q;
+    q.zx = fmaf(cps, sth * cph, sps * sph);
+    q.zy = fmaf(sps, sth * cph, -(cps * sph));
+    q.zz = cth * cph;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) q.v[i] = P.x[(6 + i) * N + node];
+    return q;
+}
+
+__device__ __forceinline__ uint32_t quad_order_key(const DevParams& P, const QuadOrderParent& q, int node,
+                                                   uint32_t iter, uint32_t s) {
+    // the thrust (word 0 of block 0) and K (word 0 of block 1), as sample_control() draws them
+    const uint2 key = make_uint2(P.seed_lo, P.seed_hi);
+    const uint32_t w0 = philox4x32_10(make_uint4(iter, (uint32_t)node, s, 0u), key).x;
+    const uint32_t w1 = philox4x32_10(make_uint4(iter, (uint32_t)node, s, 1u), key).x;
+    const float f = __fmul_rn(__uint2float_rn(w0 >> 8), 0x1p-24f);
+    const float thrust = __fadd_rn(P.u_lo[0], __fmul_rn(__fsub_rn(P.u_hi[0], P.u_lo[0]), f));
+    const int K = steps_from_word(P, w1);
+    const float ah = thrust * P.inv_mass * P.h;  // velocity change per step along the body z axis
+    const float dv[3] = {ah * q.zx, ah * q.zy, fmaf(ah, q.zz, -P.param[1] * P.h)};
+    float n = (float)K;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (dv[i] > 0.0f) n = fminf(n, __fdividef(P.x_hi[6 + i] - q.v[i], dv[i]));
+        if (dv[i] < 0.0f) n = fminf(n, __fdividef(P.x_lo[6 + i] - q.v[i], dv[i]));
+    }
+    return (uint32_t)fmaxf(n, 0.0f);  // <= K < 2^16
+}
+
 // Chunk c of this iteration's slots: order[c * 128 + p] = offset in the
-// chunk of the slot with the p-th smallest (K, offset).  Slots past n_slots
+// chunk of the slot with the p-th smallest (key, offset), the key being K
+// (the quadcopter's: K or its predicted step count, quad_order_key).  Slots past n_slots
 // take keys above every live slot's, so they sort to the chunk's end.
 template <int M>
 __device__ __forceinline__ void order_chunk(const DevParams& P, const int32_t* va, int lam, uint32_t iter,
@@ -205,6 +252,8 @@ __device__ __forceinline__ void order_chunk(const DevParams& P, const int32_t* v
     static_assert(ORDER_CHUNK == 128, "one warp sorts 4 slots per lane");
     const int lane = threadIdx.x & 31;
     uint32_t v[4];
+    int j_parent = -1;  // the parent whose part of the quadcopter key qp holds
+    QuadOrderParent qp;
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
         const uint32_t off = (uint32_t)(lane + 32 * e);
@@ -213,7 +262,17 @@ __device__ __forceinline__ void order_chunk(const DevParams& P, const int32_t* v
             const uint32_t su = (uint32_t)slot;  // < 2^32, as in LaneRollout::start
             const int j = (int)(su / (uint32_t)lam);
             const int s = (int)(su - (uint32_t)j * (uint32_t)lam);
-            v[e] = ((uint32_t)sample_steps<M>(P, iter, (uint32_t)va[j], (uint32_t)s) << 7) | off;  // K < 2^16
+            uint32_t key;
+            if constexpr (M == 4) {
+                if (j != j_parent) {
+                    qp = quad_order_parent(P, va[j]);
+                    j_parent = j;
+                }
+                key = quad_order_key(P, qp, va[j], iter, (uint32_t)s);
+            } else {
+                key = (uint32_t)sample_steps<M>(P, iter, (uint32_t)va[j], (uint32_t)s);
+            }
+            v[e] = (key << 7) | off;  // key < 2^16
         } else {
             v[e] = 0xFFFFFF80u | off;
         }

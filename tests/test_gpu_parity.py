@@ -195,12 +195,37 @@ def test_production_iteration_equals_phases_and_early_reject(kpx):
     pe.close()
 
 
+def _quad_order_keys(prob, x_nodes, va, lam, K, u, slots):
+    """FP64 form of the quadcopter's order key: K, or the steps after which
+    the velocity, extrapolated at the start's acceleration (thrust along the
+    parent's body z axis, gravity), leaves its bounds."""
+    node = va[slots // lam]
+    xs = x_nodes[node].astype(np.float64)
+    phi, th, psi = xs[:, 3], xs[:, 4], xs[:, 5]
+    a = u[slots, 0].astype(np.float64) / float(prob.param[0])
+    acc = [a * (np.cos(psi) * np.sin(th) * np.cos(phi) + np.sin(psi) * np.sin(phi)),
+           a * (np.sin(psi) * np.sin(th) * np.cos(phi) - np.cos(psi) * np.sin(phi)),
+           a * np.cos(th) * np.cos(phi) - float(prob.param[1])]
+    n = K[slots].astype(np.float64)
+    for i in range(3):
+        v0 = xs[:, 6 + i]
+        dv = acc[i] * float(prob.h)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            up = np.where(dv > 0, (float(prob.x_hi[6 + i]) - v0) / dv, np.inf)
+            down = np.where(dv < 0, (float(prob.x_lo[6 + i]) - v0) / dv, np.inf)
+        n = np.minimum(n, np.minimum(up, down))
+    return np.floor(np.maximum(n, 0.0))
+
+
 @pytest.mark.parametrize("case", ["quad_full", "quad_small", "di_adaptive", "di_fixed_k", "dubins_forest"])
 def test_slot_order_sorts_by_steps_and_leaves_results_unchanged(kpx, case):
-    """The begin phase orders each 128-slot chunk by (K, offset): a
-    permutation of the chunk whose live slots come first in non-decreasing K.
-    Rolling the slots out in that order changes no result: workspaces and the
-    step, box-test and valid counters equal those of index order."""
+    """The begin phase orders each 128-slot chunk by (key, offset), the key
+    being K (the quadcopter's: K or its predicted step count): a permutation
+    of the chunk whose live slots come first in non-decreasing key.  Rolling
+    the slots out in that order changes no result: workspaces and the step,
+    box-test and valid counters equal those of index order.  The
+    quadcopter's key is checked against its FP64 form, to one step (the
+    device rounds in FP32 with the hardware sine and cosine)."""
     prob = scenes.quad_scene(0) if case == "quad_full" else CASES[case]()
     iters = {"quad_full": 4, "quad_small": 4, "di_adaptive": 3, "di_fixed_k": 3, "dubins_forest": 8}[case]
     flags = kpx.KPX_FLAG_NO_FUSED
@@ -210,6 +235,7 @@ def test_slot_order_sorts_by_steps_and_leaves_results_unchanged(kpx, case):
     pb.iterate(iters)
     # the order of the next iteration against the K the propagate records carry
     rec = pa.make_records()
+    before = pa.arrays()
     pa.debug_step("begin")
     h = pa.header()
     ns = int(h.n_slots)
@@ -219,14 +245,26 @@ def test_slot_order_sorts_by_steps_and_leaves_results_unchanged(kpx, case):
     pb.debug_step("propagate")
     assert ns > 0 and order is not None and pb.slot_order(ns) is None
     K = rec["K"][:ns].cpu().numpy()
+    quad = prob.m == 4
+    if quad:
+        u = rec["u"].view(prob.m, -1)[:, :ns].T.cpu().numpy()
     chunks = order.reshape(-1, 128).astype(np.int64)
+    inversions = pairs = 0
     for c, perm in enumerate(chunks):
         assert np.array_equal(np.sort(perm), np.arange(128)), "chunk %d is not a permutation" % c
         live = min(128, ns - 128 * c)
         slots = 128 * c + perm[:live]
         assert np.all(slots < ns), "a dead slot sorted before a live one"
-        key = K[slots].astype(np.int64) * 128 + perm[:live]
-        assert np.all(np.diff(key) > 0), "chunk %d not in ascending (K, offset)" % c
+        if quad:
+            qk = _quad_order_keys(prob, before["x"], before["VA"], int(h.lam), K, u, slots)
+            assert np.all(np.diff(qk) >= -1), "chunk %d not in ascending predicted steps" % c
+            inversions += int(np.sum(np.diff(qk) < 0))
+            pairs += max(0, live - 1)
+        else:
+            key = K[slots].astype(np.int64) * 128 + perm[:live]
+            assert np.all(np.diff(key) > 0), "chunk %d not in ascending (K, offset)" % c
+    if quad:
+        assert inversions <= 0.01 * pairs, (inversions, pairs)
     for ph in kpx.PHASES[2:]:
         pa.debug_step(ph)
         pb.debug_step(ph)
