@@ -687,7 +687,7 @@ cudaError_t upload_and_init(kpx_planner* p, const kpx_obstacles* obs, std::vecto
 size_t batch_header_bytes(int B) {
     size_t off = align_up(sizeof(BatchHeader), 256);
     off += align_up((size_t)B * sizeof(DevParams), 256);
-    off += 4 * align_up((size_t)(B + 1) * sizeof(int64_t), 256);
+    off += 5 * align_up((size_t)(B + 1) * sizeof(int64_t), 256);
     off += align_up((size_t)B * sizeof(SlotState), 256);
     off += align_up((size_t)B * sizeof(kpx_device_header), 256);
     return off;
@@ -1096,8 +1096,8 @@ kpx_status kpx_batch_create(int32_t count, const kpx_problem* problems, void* de
     h += align_up(sizeof(BatchHeader), 256);
     BP.Ps = reinterpret_cast<const DevParams*>(base + h);
     h += align_up((size_t)count * sizeof(DevParams), 256);
-    int64_t* pre[4];
-    for (int t = 0; t < 4; ++t) {
+    int64_t* pre[5];
+    for (int t = 0; t < 5; ++t) {
         pre[t] = reinterpret_cast<int64_t*>(base + h);
         h += align_up((size_t)(count + 1) * sizeof(int64_t), 256);
     }
@@ -1105,6 +1105,7 @@ kpx_status kpx_batch_create(int32_t count, const kpx_problem* problems, void* de
     BP.scan_prefix = pre[1];
     BP.win_prefix = pre[2];
     BP.prune_prefix = pre[3];
+    BP.order_prefix = pre[4];
     BP.slots = reinterpret_cast<SlotState*>(base + h);
     h += align_up((size_t)count * sizeof(SlotState), 256);
     b->poll_buf.assign(count, SlotState{});

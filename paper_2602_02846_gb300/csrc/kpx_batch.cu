@@ -58,6 +58,10 @@ __global__ void __launch_bounds__(1024) k_b_begin(BatchParams BP) {
     block_prefix(BP.B, BP.chunk_prefix, [&](int p) {  // each problem's propagate units
         return propagate_units(BP.Ps[p].hdr->n_slots, BP.Ps[p].slot_order != nullptr);
     });
+    block_prefix(BP.B, BP.order_prefix, [&](int p) {
+        const DevParams& P = BP.Ps[p];
+        return P.hdr->active && P.slot_order ? (P.hdr->n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK : (int64_t)0;
+    });
     block_prefix(BP.B, BP.scan_prefix, [&](int p) {
         const int64_t words = (BP.Ps[p].hdr->n_slots + 31) / 32;
         return (words + WIN_TILE_WORDS - 1) / WIN_TILE_WORDS;
@@ -68,24 +72,26 @@ __global__ void __launch_bounds__(1024) k_b_begin(BatchParams BP) {
     }
 }
 
-// region snapshot where the capacity rule could trigger, and the propagate
-// order of the problem's slots (each 128-slot chunk sorted by K; grid.y =
-// problem)
+// region snapshot where the capacity rule could trigger (grid.y = problem),
+// and the propagate order of every problem's slots (each 128-slot chunk
+// sorted by the single planner's key): the chunks of all problems are
+// spread over all warps of the grid, so that a few large problems (a
+// request loop's) do not wait on their own blocks alone
 __global__ void k_b_snapshot(BatchParams BP) {
-    const DevParams& P = BP.Ps[blockIdx.y];
-    const kpx_device_header* H = P.hdr;
-    if (H->active && P.slot_order) {
-        const int64_t n_slots = H->n_slots;
-        const int64_t n_chunks = (n_slots + ORDER_CHUNK - 1) / ORDER_CHUNK;
-        const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-        const int32_t* va = va_current(P, H);
-        for (int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < n_chunks; c += warps) {
-            if (P.m == 4)
-                order_chunk<4>(P, va, H->lambda, (uint32_t)H->iter, n_slots, c);
-            else
-                order_chunk<3>(P, va, H->lambda, (uint32_t)H->iter, n_slots, c);
-        }
+    const int64_t total = BP.order_prefix[BP.B];
+    const int64_t warps = ((int64_t)gridDim.x * gridDim.y * blockDim.x) >> 5;
+    const int64_t w0 = (((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    for (int64_t g = w0; g < total; g += warps) {
+        const int p = find_problem(BP.order_prefix, 0, BP.B, g);
+        const DevParams& Q = BP.Ps[p];
+        const kpx_device_header* HQ = Q.hdr;
+        const int64_t c = g - BP.order_prefix[p];
+        if (Q.m == 4)
+            order_chunk<4>(Q, va_current(Q, HQ), HQ->lambda, (uint32_t)HQ->iter, HQ->n_slots, c);
+        else
+            order_chunk<3>(Q, va_current(Q, HQ), HQ->lambda, (uint32_t)HQ->iter, HQ->n_slots, c);
     }
+    const DevParams& P = BP.Ps[blockIdx.y];
     if (!begin_needs_snapshot(P, P.hdr)) return;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < P.R; r += gridDim.x * blockDim.x)
         P.region_snap[r] = P.region_key[r];

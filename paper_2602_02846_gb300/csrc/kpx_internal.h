@@ -245,6 +245,7 @@ struct BatchParams {
     int64_t* scan_prefix;    // [B+1] winner-scan tiles before p
     int64_t* win_prefix;     // [B+1] winners before p
     int64_t* prune_prefix;   // [B+1] prune tiles before p
+    int64_t* order_prefix;   // [B+1] 128-slot order chunks before p (0 for a problem without the order)
     SlotState* slots;        // [B] poll staging
 };
 
