@@ -59,7 +59,7 @@ FUSED_DRAM_BYTES = {
     "dubins6_forest300": 195072,     # profiles/k_fused_dubins6_forest300.md (the timed step's graph launch)
 }
 PROPAGATE_DRAM_BYTES = {
-    "quad12_building1000": 6862848,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
+    "quad12_building1000": 6868736,  # profiles/k_propagate_quad12_building1000.md (iteration 100)
 }
 FP32_LANES_PER_SM = 128
 HBM_FALLBACK_GBS = 6800.0
@@ -82,8 +82,8 @@ def update_row_bytes(n, m):
 # profiles/ (each kernel from a cold L2, as ncu flushes caches between
 # captured kernels): workload -> (iteration, bytes)
 UPDATE_DRAM_BYTES = {
-    "quad12_building1000": (100, 3744000),   # profiles/update_quad12_building1000.md
-    "quad12_clutter1000": (300, 25003264),   # profiles/update_quad12_clutter1000.md
+    "quad12_building1000": (100, 3745536),   # profiles/update_quad12_building1000.md
+    "quad12_clutter1000": (300, 25009920),   # profiles/update_quad12_clutter1000.md
 }
 
 
