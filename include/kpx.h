@@ -130,7 +130,9 @@ enum {
      * then launches the eight phase kernels.  Results are identical. */
     KPX_FLAG_NO_FUSED = 2,
     /* Roll the propagate kernel's slots out in index order instead of in
-     * ascending step count K within each aligned chunk of 128 slots.
+     * ascending order key (the step count K; the 12D quadcopter's predicted
+     * step count) within each aligned chunk of 128 slots, longest quarter
+     * first.
      * Results are identical (every slot's outcome is independent of the
      * lane that computes it); only the time changes. */
     KPX_FLAG_NO_SLOT_ORDER = 4
@@ -550,8 +552,11 @@ typedef struct {
     size_t workspace_bytes;
     /* propagate order of the current iteration (written by the begin phase):
      * uint8[slot_cap rounded up to 128]; entry c * 128 + p is the offset in
-     * chunk c of the slot with the p-th smallest (K, offset); null when
-     * KPX_FLAG_NO_SLOT_ORDER is set */
+     * chunk c of the slot with the p-th smallest (key, offset), the key
+     * being the step count K (for the 12D quadcopter: K, or fewer steps when
+     * the velocity, extrapolated at the sampled thrust along the parent's
+     * body z axis, leaves its bounds); null when KPX_FLAG_NO_SLOT_ORDER is
+     * set */
     uint8_t* slot_order;
 } kpx_layout;
 

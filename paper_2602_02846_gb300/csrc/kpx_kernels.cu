@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(1024) k_grid_scan(DevParams P) {
 // In the loop body of a planner's graph (loop = 1) an iteration runs only
 // while iterations are owed (graph_pending > 0); otherwise every kernel of
 // the iteration is a no-op.
-// Every warp also sorts chunks of the iteration's slots by K for the
+// Every warp also sorts chunks of the iteration's slots by their order key
+// (order_chunk: K, or the quadcopter's predicted step count) for the
 // propagate kernel (slot_order); the slot count and lambda it uses are read
 // from counters begin_counters leaves alone (|V_A|, the iteration, the V_A
 // buffer), exactly as begin_counters derives them.

@@ -160,9 +160,10 @@ __device__ __forceinline__ bool begin_needs_snapshot(const DevParams& P, const k
 
 // ---------------------------------------------------------------------------
 // propagate order: the slots of each aligned ORDER_CHUNK-slot chunk sorted by
-// their step count K (one warp per chunk, a bitonic network over the warp's
-// registers and shuffles).  Only the lane that computes a slot changes, not
-// the slot's result.
+// an order key, their step count K or the quadcopter's predicted step count
+// (one warp per chunk, a bitonic network over the warp's registers and
+// shuffles).  Only the lane that computes a slot changes, not the slot's
+// result.
 // ---------------------------------------------------------------------------
 // Ascending sort of the 128 values v[e] of all lanes, element i = lane + 32 e.
 __device__ __forceinline__ void warp_sort128(uint32_t (&v)[4]) {
@@ -503,9 +504,10 @@ __device__ __forceinline__ void roll_candidate_coop(const DevParams& P, const Gr
 
 // Lane l of a warp takes position chunk * 32 + l of the slot sequence: the
 // slot itself, or with `order` (written by the begin kernel) the slot at that
-// position of its ORDER_CHUNK-slot chunk sorted by K, so that a warp's lanes
-// run similar step counts.  The slots past n_slots sort last in the final
-// chunk, so a position below n_slots always names a live slot.
+// position of its ORDER_CHUNK-slot chunk sorted by the order key (K, or the
+// quadcopter's predicted step count), so that a warp's lanes run similar
+// step counts.  The slots past n_slots sort last in the final chunk, so a
+// position below n_slots always names a live slot.
 template <int DYN, int INTEG, bool SYM = false>
 __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_slots, int lam, uint32_t iter,
                                                 const int32_t* va, bool early, int64_t chunk,
@@ -532,7 +534,7 @@ __device__ __forceinline__ void propagate_chunk(const DevParams& P, int64_t n_sl
 }
 
 // The propagate's work units: 32 slots each.  With the slots of each
-// 128-slot chunk sorted by K (ordered) they are handed out longest quarter
+// 128-slot chunk sorted by the order key (ordered) they are handed out longest quarter
 // first: unit q is quarter 3 - q / n128 of 128-slot chunk q % n128, so that
 // a launch ends on the short rollouts (a longest-first schedule); units past
 // n_slots are empty.  Otherwise unit q is slots [32 q, 32 q + 32).
